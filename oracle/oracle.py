@@ -1,0 +1,176 @@
+"""ctypes wrapper of the FP64 C oracle (``pd_oracle.c``).  TEST INFRASTRUCTURE.
+
+Every function here only marshals arguments; the arithmetic is in the C file,
+each C function citing the passage of the paper it follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pd_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libpd_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile pd_oracle.c into a shared library next to it (gcc, OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.or_rasterize.argtypes = [_dp, _dp, _i64p, ctypes.c_int, ctypes.c_int, _u32p, _u32p]
+            lib.or_cost.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.or_cost.restype = ctypes.c_double
+            lib.or_sinkhorn_w.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int,
+                                          ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp,
+                                          ctypes.POINTER(ctypes.c_int), _dp]
+            lib.or_sinkhorn_pd_batch.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, _u32p,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                 _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int), _dp]
+            lib.or_barycenter.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          _dp, _dp, _dp]
+            lib.or_kmeans.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_uint64, _i32p, _dp, _dp]
+            lib.or_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a, t):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+def rasterize(birth, death, offsets, d):
+    """Rasterise B diagrams (CSR: points offsets[b]..offsets[b+1]) on a d x d grid.
+    Returns (hist uint32 [B,d,d], mass uint32 [B])."""
+    birth = np.ascontiguousarray(birth, dtype=np.float64)
+    death = np.ascontiguousarray(death, dtype=np.float64)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    B = len(offsets) - 1
+    hist = np.zeros((B, d, d), dtype=np.uint32)
+    mass = np.zeros(B, dtype=np.uint32)
+    rc = _load().or_rasterize(_ptr(birth, _dp), _ptr(death, _dp), _ptr(offsets, _i64p), B, d,
+                              _ptr(hist, _u32p), _ptr(mass, _u32p))
+    if rc != 0:
+        raise ValueError("or_rasterize: invalid point (need finite 0 <= birth <= death <= 1)")
+    return hist, mass
+
+
+def cost(d, x, y):
+    """Entry C_xy of the augmented cost (index d*d is the Delta bin)."""
+    return float(_load().or_cost(d, int(x), int(y)))
+
+
+def augment(hA, hB):
+    """Prop. 1 augmentation of two histograms: a = (hA, |B|), b = (hB, |A|)."""
+    hA = np.asarray(hA, dtype=np.float64).ravel()
+    hB = np.asarray(hB, dtype=np.float64).ravel()
+    return np.concatenate([hA, [hB.sum()]]), np.concatenate([hB, [hA.sum()]])
+
+
+def sinkhorn_w(d, gamma, a, b, max_iter, tol, g_init=None):
+    """Log-domain FP64 Sinkhorn on the explicit augmented cost (weights a, b of
+    length d*d+1).  Returns a dict with cost, f, g, rmarg, cmarg, iters, err."""
+    n = d * d + 1
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    assert a.shape == (n,) and b.shape == (n,)
+    gi = None if g_init is None else np.ascontiguousarray(g_init, dtype=np.float64)
+    c = ctypes.c_double()
+    it = ctypes.c_int()
+    er = ctypes.c_double()
+    f = np.empty(n)
+    g = np.empty(n)
+    rm = np.empty(n)
+    cm = np.empty(n)
+    rc = _load().or_sinkhorn_w(d, gamma, _ptr(a, _dp), _ptr(b, _dp), int(max_iter), float(tol),
+                               _ptr(gi, _dp), ctypes.byref(c), _ptr(f, _dp), _ptr(g, _dp),
+                               _ptr(rm, _dp), _ptr(cm, _dp), ctypes.byref(it), ctypes.byref(er))
+    if rc != 0:
+        raise ValueError("or_sinkhorn_w: invalid weights (negative or unequal total mass)")
+    return dict(cost=c.value, f=f, g=g, rmarg=rm, cmarg=cm, iters=it.value, err=er.value)
+
+
+def sinkhorn_pd(d, gamma, hA, hB, max_iter, tol, g_init=None):
+    """Alg. 1 for one pair of d x d histograms (Prop. 1 augmentation)."""
+    a, b = augment(hA, hB)
+    return sinkhorn_w(d, gamma, a, b, max_iter, tol, g_init)
+
+
+def sinkhorn_pd_batch(d, gamma, hA, hB, max_iter, tol, want_potentials=False, want_marginals=False):
+    """Alg. 1 over P pairs (OpenMP over pairs).  hA, hB: uint32 [P,d,d]."""
+    hA = np.ascontiguousarray(hA, dtype=np.uint32)
+    hB = np.ascontiguousarray(hB, dtype=np.uint32)
+    P = hA.shape[0]
+    n = d * d + 1
+    cost_ = np.empty(P)
+    it = np.empty(P, dtype=np.int32)
+    er = np.empty(P)
+    f = np.empty((P, n)) if want_potentials else None
+    g = np.empty((P, n)) if want_potentials else None
+    rm = np.empty((P, n)) if want_marginals else None
+    cm = np.empty((P, n)) if want_marginals else None
+    rc = _load().or_sinkhorn_pd_batch(d, gamma, _ptr(hA, _u32p), _ptr(hB, _u32p), P, int(max_iter),
+                                      float(tol), _ptr(cost_, _dp), _ptr(f, _dp), _ptr(g, _dp),
+                                      _ptr(rm, _dp), _ptr(cm, _dp),
+                                      it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(er, _dp))
+    if rc != 0:
+        raise ValueError("or_sinkhorn_pd_batch failed")
+    return dict(cost=cost_, iters=it, err=er, f=f, g=g, rmarg=rm, cmarg=cm)
+
+
+def barycenter(d, gamma, hists, lam, outer_iters, max_iter, tol, z_init=None):
+    """Alg. 2.  hists: uint32 [N,d,d].  Returns (z [d,d], energy [outer_iters])."""
+    hists = np.ascontiguousarray(hists, dtype=np.uint32)
+    N = hists.shape[0]
+    zi = None if z_init is None else np.ascontiguousarray(z_init, dtype=np.float64).ravel()
+    z = np.empty(d * d)
+    e = np.empty(outer_iters)
+    rc = _load().or_barycenter(d, gamma, _ptr(hists, _u32p), N, float(lam), int(outer_iters),
+                               int(max_iter), float(tol), _ptr(zi, _dp), _ptr(z, _dp), _ptr(e, _dp))
+    if rc != 0:
+        raise ValueError("or_barycenter failed")
+    return z.reshape(d, d), e
+
+
+def kmeans(d, gamma, hists, k, lam, rounds, bary_steps, max_iter, tol, seed):
+    """k-means on diagrams.  Returns (assign [N], centroids [k,d,d], objective [rounds])."""
+    hists = np.ascontiguousarray(hists, dtype=np.uint32)
+    N = hists.shape[0]
+    assign = np.empty(N, dtype=np.int32)
+    cent = np.empty((k, d, d))
+    obj = np.empty(rounds)
+    rc = _load().or_kmeans(d, gamma, _ptr(hists, _u32p), N, k, float(lam), int(rounds),
+                           int(bary_steps), int(max_iter), float(tol), ctypes.c_uint64(seed),
+                           _ptr(assign, _i32p), _ptr(cent, _dp), _ptr(obj, _dp))
+    if rc != 0:
+        raise ValueError("or_kmeans failed")
+    return assign, cent, obj
