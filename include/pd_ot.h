@@ -1,0 +1,161 @@
+/*
+ * pd_ot.h -- C ABI of the GB300 (sm_103a) library for entropic optimal
+ * transport between persistence diagrams rasterised on a d x d grid plus one
+ * diagonal bin (Lacombe, Cuturi & Oudot, NeurIPS 2018).
+ *
+ * Conventions for every entry point
+ *   - Returns pd_status; PD_OK (0) on success.  No call aborts the process.
+ *     pd_last_error(ctx) gives a message for the last failing call on ctx
+ *     (owned by ctx, valid until the next call on ctx).
+ *   - Array arguments are DEVICE pointers unless their name ends in _host.
+ *     The caller owns every input and output buffer; the library never frees
+ *     them.  The library allocates only its own workspace, held by pd_ctx and
+ *     released by pd_ctx_destroy.
+ *   - Every call takes a CUDA stream (pd_stream is cudaStream_t; NULL is the
+ *     legacy default stream).  Work is enqueued on that stream; calls return
+ *     after enqueueing unless stated otherwise.  Calls that must inspect
+ *     device-side results on the host (convergence loops) synchronise the
+ *     stream and say so.
+ *   - Grid cell (i, j): i = birth index (row), j = death index (column),
+ *     0 <= i, j < d; flattened index x = i*d + j.  Index d*d is the Delta
+ *     (diagonal) bin.  Histograms are row-major uint32 [d][d].
+ *   - A pd_ctx must not be used by two host threads at once.
+ */
+#ifndef PD_OT_H
+#define PD_OT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* pd_stream; /* == cudaStream_t */
+typedef struct pd_ctx pd_ctx;
+typedef int pd_status;
+
+enum {
+    PD_OK = 0,
+    PD_ERR_INVALID = 1,   /* bad argument: d outside [2,256], gamma <= 0, bad point, NULL output ... */
+    PD_ERR_OOM = 2,       /* workspace allocation failed */
+    PD_ERR_CUDA = 3,      /* a CUDA runtime call failed (message in pd_last_error) */
+    PD_ERR_TIMEOUT = 4,   /* a bounded wait ran out */
+    PD_ERR_QUEUE_FULL = 5,/* serving queue has no free slot */
+    PD_NOT_CONVERGED = 6, /* per pair: max_iter reached before tol (not fatal) */
+    PD_PENDING = 7,       /* serving: result not ready yet */
+    PD_ERR_RANGE = 8      /* per pair: a scaling left the floating-point range even after absorption */
+};
+
+enum { PD_FP32 = 0, PD_BF16 = 1 };
+
+/* Version of this ABI (increments on incompatible change). */
+int pd_abi_version(void);
+
+/* Create a context bound to CUDA device `device` (makes it current for the
+ * calling thread).  *out receives the context. */
+pd_status pd_ctx_create(int device, pd_ctx** out);
+/* Release the context and its workspace.  Safe on NULL. */
+void pd_ctx_destroy(pd_ctx* ctx);
+/* Message of the last failing call on ctx ("" if none). */
+const char* pd_last_error(const pd_ctx* ctx);
+
+/*
+ * pd_rasterize -- Sec. 3 "Discretization": hist[b][i][j] = number of points
+ * of diagram b in grid cell (i, j), with i = floor(birth * d), j =
+ * floor(death * d) computed in IEEE FP64 and clamped to d-1 (the closed edge at
+ * 1 belongs to the last cell); mass[b] = number of points of diagram b.
+ *   birth, death : double [offsets[B]]  points in CSR order (device)
+ *   offsets      : int64  [B+1]         diagram b owns points offsets[b] .. offsets[b+1]-1 (device)
+ *   B, d         : number of diagrams, grid size (2 <= d <= 256)
+ *   hist         : uint32 [B][d][d]     output, overwritten (device)
+ *   mass         : uint32 [B]           output (device)
+ * Errors: PD_ERR_INVALID if B < 0, d outside [2,256], or any point is not a
+ * finite point of [0,1]^2 with birth <= death (checked on the device; this call
+ * then synchronises the stream to report it).
+ */
+pd_status pd_rasterize(pd_ctx* ctx, const double* birth, const double* death, const int64_t* offsets,
+                       int B, int d, uint32_t* hist, uint32_t* mass, pd_stream stream);
+
+/* Parameters of a batched Sinkhorn solve. */
+typedef struct {
+    double gamma;      /* entropic regularisation gamma > 0 (Eq. SinkhornMinimizationProblem) */
+    int d;             /* grid size, 2 <= d <= 256 */
+    int max_iter;      /* maximum number of Sinkhorn iterations (each = u-update then v-update), >= 1 */
+    double tol;        /* stop after iteration t if err_t / total mass <= tol (0 = run max_iter) */
+    int precision;     /* PD_FP32: CUDA-core FP32 GEMMs; PD_BF16: tcgen05 BF16 GEMMs, FP32 accumulate */
+    int refine_iters;  /* PD_BF16 only: FP32 iterations run after the BF16 phase stops (0 = none) */
+    double absorb_tau; /* re-absorb when |log(u~/a)| or |log(v~/b)| exceeds this (<= 0: default 20) */
+    int absorb_every;  /* also re-absorb every this many iterations (<= 0: default 64) */
+} pd_sinkhorn_params;
+
+/* Fill *p with defaults for (gamma, d): max_iter 20000, tol 1e-6, PD_FP32,
+ * refine_iters 0, absorb_tau 20, absorb_every 64. */
+void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, int d);
+
+/*
+ * pd_sinkhorn_batch -- Alg. 1: for each pair p, the entropic transport between
+ * the augmented histograms a = (histA[ia], massB[ib]) and b = (histB[ib],
+ * massA[ia]) (Prop. 1) with the squared-Euclidean grid cost in physical units
+ * on [0,1]^2 and cost (j-i)^2/(2 d^2) to the diagonal bin, by Sinkhorn
+ * iterations of Eq. (SinkhornMap) applied through the separable kernel of
+ * Prop. 1 (Sec. 3 "Convolutions").  Iteration t is the u-update then the
+ * v-update; err_t = sum_y |v_{t-1,y} (K^T u_t)_y - b_y| (the marginal error of
+ * Eq. Altschuler bounds, row side exact after the u-update) divided by the total
+ * mass; the loop stops after iteration t when err_t <= tol or t == max_iter.
+ * Potentials use P_xy = a_x b_y exp((f_x + g_y - C_xy)/gamma).
+ *   histA, massA : uint32 [NA][d][d], uint32 [NA]   (device)
+ *   histB, massB : uint32 [NB][d][d], uint32 [NB]   (device)
+ *   pairs        : int32 [P][2] (ia, ib) indices, or NULL meaning pair p = (p, p) (device)
+ *   P            : number of pairs (>= 0)
+ *   params       : host pointer
+ *   g_init       : double [P][d*d+1] initial g (warm start), or NULL for g = 0 (device)
+ * Outputs (device; only `cost` is required, others may be NULL):
+ *   cost     : double [P]          <P, C> by Prop. 2, reduced in FP64
+ *   row_marg : float  [P][d*d+1]   sum_y P_xy
+ *   col_marg : float  [P][d*d+1]   sum_x P_xy
+ *   f, g     : double [P][d*d+1]   potentials; entries whose kernel sum underflows are +inf
+ *   iters    : int32  [P]          iterations run
+ *   err      : float  [P]          last err_t (relative)
+ *   status   : int32  [P]          PD_OK, PD_NOT_CONVERGED or PD_ERR_RANGE
+ * Synchronises `stream` (the iteration loop checks convergence on the host).
+ * Errors: PD_ERR_INVALID (bad params / NULL cost / P < 0), PD_ERR_OOM, PD_ERR_CUDA.
+ */
+pd_status pd_sinkhorn_batch(pd_ctx* ctx, const uint32_t* histA, const uint32_t* massA,
+                            const uint32_t* histB, const uint32_t* massB, const int32_t* pairs, int P,
+                            const pd_sinkhorn_params* params, const double* g_init,
+                            double* cost, float* row_marg, float* col_marg, double* f, double* g,
+                            int32_t* iters, float* err, int32_t* status, pd_stream stream);
+
+
+/* Kernel classes recorded by the launch profiler. */
+enum {
+    PD_K_RASTER = 0,   /* rasteriser */
+    PD_K_SETUP = 1,    /* per-pair set-up of a Sinkhorn batch */
+    PD_K_LOGSTEP = 2,  /* exact log-domain first iteration */
+    PD_K_ABSORB = 3,   /* absorption / re-centring */
+    PD_K_ITER = 4,     /* linear-domain Sinkhorn iterations (the GEMM kernel) */
+    PD_K_FINALIZE = 5, /* transport cost (Prop. 2), marginals, potentials */
+    PD_K_COUNT = 16
+};
+
+/*
+ * pd_profile_enable -- start (enable != 0) or stop recording a pair of CUDA
+ * events around every kernel launch the library makes on ctx, on the stream
+ * the kernel is launched on; starting clears earlier records.  Library
+ * feature for tracing; no counterpart in the paper.
+ */
+pd_status pd_profile_enable(pd_ctx* ctx, int enable);
+
+/*
+ * pd_profile_read -- synchronise the recorded events and report, per kernel
+ * class k < PD_K_COUNT: ms_host[k] = summed launch durations (milliseconds),
+ * launches_host[k] = number of launches.  Host pointers of PD_K_COUNT
+ * entries; either may be NULL.
+ */
+pd_status pd_profile_read(pd_ctx* ctx, double* ms_host, int64_t* launches_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PD_OT_H */

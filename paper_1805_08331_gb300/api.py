@@ -1,0 +1,179 @@
+"""Thin Python binding of the C ABI in ``include/pd_ot.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``_build/libpdot.so``.  Tensors are PyTorch CUDA tensors (PyTorch is
+used for device memory and streams); their data pointers and the current
+stream are passed straight through.  If the library is missing, loading it
+raises -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+PD_OK, PD_ERR_INVALID, PD_ERR_OOM, PD_ERR_CUDA, PD_ERR_TIMEOUT, PD_ERR_QUEUE_FULL = 0, 1, 2, 3, 4, 5
+PD_NOT_CONVERGED, PD_PENDING, PD_ERR_RANGE = 6, 7, 8
+PD_FP32, PD_BF16 = 0, 1
+STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID", 2: "PD_ERR_OOM", 3: "PD_ERR_CUDA", 4: "PD_ERR_TIMEOUT",
+                5: "PD_ERR_QUEUE_FULL", 6: "PD_NOT_CONVERGED", 7: "PD_PENDING", 8: "PD_ERR_RANGE"}
+
+# Every symbol the header declares (checked by the ABI test).
+EXPORTED = ["pd_abi_version", "pd_ctx_create", "pd_ctx_destroy", "pd_last_error", "pd_rasterize",
+            "pd_sinkhorn_default_params", "pd_sinkhorn_batch", "pd_profile_enable", "pd_profile_read"]
+PD_K_RASTER, PD_K_SETUP, PD_K_LOGSTEP, PD_K_ABSORB, PD_K_ITER, PD_K_FINALIZE, PD_K_COUNT = 0, 1, 2, 3, 4, 5, 16
+KERNEL_NAMES = {0: "raster", 1: "setup", 2: "logstep", 3: "absorb", 4: "iter", 5: "finalize"}
+
+
+class PdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SinkhornParams(ctypes.Structure):
+    """Mirror of pd_sinkhorn_params."""
+    _fields_ = [("gamma", ctypes.c_double), ("d", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("tol", ctypes.c_double), ("precision", ctypes.c_int), ("refine_iters", ctypes.c_int),
+                ("absorb_tau", ctypes.c_double), ("absorb_every", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libpdot.so (optionally building it first).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise PdError(PD_ERR_CUDA, f"CUDA library not built: {path} (run __graft_entry__.build())")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        lib.pd_abi_version.restype = ctypes.c_int
+        lib.pd_ctx_create.argtypes = [ctypes.c_int, ctypes.POINTER(_vp)]
+        lib.pd_ctx_destroy.argtypes = [_vp]
+        lib.pd_ctx_destroy.restype = None
+        lib.pd_last_error.argtypes = [_vp]
+        lib.pd_last_error.restype = ctypes.c_char_p
+        lib.pd_rasterize.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        lib.pd_sinkhorn_default_params.argtypes = [ctypes.POINTER(SinkhornParams), ctypes.c_double, ctypes.c_int]
+        lib.pd_sinkhorn_default_params.restype = None
+        lib.pd_sinkhorn_batch.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(SinkhornParams),
+                                          _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        lib.pd_profile_enable.argtypes = [_vp, ctypes.c_int]
+        lib.pd_profile_read.argtypes = [_vp, _vp, _vp]
+        _lib = lib
+        return lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """Owns a pd_ctx (library workspace) bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = _vp()
+        st = self.lib.pd_ctx_create(int(device), ctypes.byref(h))
+        if st != PD_OK:
+            raise PdError(st, "pd_ctx_create failed")
+        self.handle = h
+        self.device = device
+
+    def last_error(self) -> str:
+        return self.lib.pd_last_error(self.handle).decode()
+
+    def check(self, st):
+        if st != PD_OK:
+            raise PdError(st, self.last_error())
+
+    def profile_enable(self, on: bool = True):
+        self.check(self.lib.pd_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self):
+        """{kernel class name: (total ms, launches)} of the recorded launches."""
+        ms = (ctypes.c_double * PD_K_COUNT)()
+        n = (ctypes.c_int64 * PD_K_COUNT)()
+        self.check(self.lib.pd_profile_read(self.handle, ctypes.cast(ms, _vp), ctypes.cast(n, _vp)))
+        return {KERNEL_NAMES.get(k, str(k)): (ms[k], n[k]) for k in range(PD_K_COUNT) if n[k] > 0}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.pd_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pd_sinkhorn_default_params(gamma: float, d: int, **kw) -> SinkhornParams:
+    p = SinkhornParams()
+    load().pd_sinkhorn_default_params(ctypes.byref(p), float(gamma), int(d))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def pd_rasterize(ctx: Context, birth, death, offsets, d: int, hist=None, mass=None, stream=None):
+    """Rasterise B diagrams given as CUDA tensors (float64 birth/death, int64
+    offsets [B+1]).  Returns (hist uint32 [B,d,d] as int32 storage, mass)."""
+    import torch
+    B = offsets.numel() - 1
+    dev = offsets.device
+    if hist is None:
+        hist = torch.empty((B, d, d), dtype=torch.int32, device=dev)
+    if mass is None:
+        mass = torch.empty((B,), dtype=torch.int32, device=dev)
+    ctx.check(ctx.lib.pd_rasterize(ctx.handle, _ptr(birth), _ptr(death), _ptr(offsets), int(B), int(d),
+                                   _ptr(hist), _ptr(mass), _stream(stream)))
+    return hist, mass
+
+
+def pd_sinkhorn_batch(ctx: Context, histA, massA, histB, massB, params: SinkhornParams, pairs=None, g_init=None,
+                      want_marginals=False, want_potentials=False, stream=None, out=None):
+    """Alg. 1 over P pairs.  Histograms are int32 CUDA tensors holding uint32
+    counts.  Returns a dict of CUDA tensors (cost, iters, err, status and, if
+    requested, row_marg, col_marg, f, g)."""
+    import torch
+    dev = histA.device
+    P = pairs.shape[0] if pairs is not None else histA.shape[0]
+    n = params.d * params.d + 1
+    o = dict(out or {})
+    o.setdefault("cost", torch.empty(P, dtype=torch.float64, device=dev))
+    o.setdefault("iters", torch.empty(P, dtype=torch.int32, device=dev))
+    o.setdefault("err", torch.empty(P, dtype=torch.float32, device=dev))
+    o.setdefault("status", torch.empty(P, dtype=torch.int32, device=dev))
+    if want_marginals:
+        o.setdefault("row_marg", torch.empty((P, n), dtype=torch.float32, device=dev))
+        o.setdefault("col_marg", torch.empty((P, n), dtype=torch.float32, device=dev))
+    if want_potentials:
+        o.setdefault("f", torch.empty((P, n), dtype=torch.float64, device=dev))
+        o.setdefault("g", torch.empty((P, n), dtype=torch.float64, device=dev))
+    ctx.check(ctx.lib.pd_sinkhorn_batch(
+        ctx.handle, _ptr(histA), _ptr(massA), _ptr(histB), _ptr(massB), _ptr(pairs), int(P), ctypes.byref(params),
+        _ptr(g_init), _ptr(o["cost"]), _ptr(o.get("row_marg")), _ptr(o.get("col_marg")), _ptr(o.get("f")),
+        _ptr(o.get("g")), _ptr(o["iters"]), _ptr(o["err"]), _ptr(o["status"]), _stream(stream)))
+    return o

@@ -1,0 +1,77 @@
+// pd_internal.h -- library-internal declarations (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// Per-pair scalar slots (double) of the Sinkhorn workspace.
+enum {
+    SC_FD = 0,   // absorbed Delta potential of the u side (log units, f_Delta/gamma part)
+    SC_GD,       // absorbed Delta potential of the v side
+    SC_UTD,      // residual scaling u~_Delta
+    SC_VTD,      // residual scaling v~_Delta
+    SC_DD,       // absorbed Delta-Delta kernel entry exp(FD + GD)
+    SC_AD,       // a_Delta = |B|
+    SC_BD,       // b_Delta = |A|
+    SC_TOTAL,    // total mass |A| + |B|
+    SC_ERR,      // last relative marginal error
+    SC_N
+};
+// Per-pair int slots.
+enum {
+    IC_NA = 0,   // support size of a on the grid
+    IC_NB,       // support size of b on the grid
+    IC_ITERS,    // iterations done
+    IC_STATUS,   // ST_*
+    IC_ABSORB,   // 1 = needs (re-)absorption before iterating
+    IC_FROMLIN,  // 1 = potentials must be rebuilt from the linear residuals
+    IC_RANGE,    // consecutive range failures
+    IC_SINCE,    // iterations since the last absorption
+    IC_N
+};
+enum { ST_ACTIVE = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_RANGE = 3, ST_INVALID = 4 };
+
+// Device-side view of the batched Sinkhorn workspace.  Every per-pair array is
+// stored pair-major with the stride given in the comment (dp = padded d, a
+// multiple of 64; n = d*d + 1).
+struct SkWS {
+    int d, dp, n, P;
+    double gamma;
+    // FP32 [P][dp*dp]
+    float *K1u, *K2u, *K1v, *K2v;   // absorbed separable kernel factors (u- and v-updates)
+    float *ut, *vt;                 // residual scalings on the grid (0 off support)
+    float *Wt, *Rt;                 // GEMM intermediate (transposed) and output scratch
+    float *KDu, *KDv;               // absorbed grid<->Delta kernel entries
+    float *am, *bm;                 // dense a, b on the grid (FP32)
+    // FP32 [P][dp]
+    float *rs_u, *cf_u, *rs_v, *cf_v;  // intermediate row scales / output column factors
+    // FP64 [P][dp]
+    double *ap, *bp, *al, *be;      // separable absorbed potentials: u side (alpha', beta'), v side (alpha, beta)
+    double *Au, *Bu, *Av, *Bv;      // intermediate shifts of the u- and v-updates
+    // FP64 [P][n]
+    double *phi, *psi;              // current log potentials f/gamma, g/gamma on the supports
+    double *sc;                     // [P][SC_N]
+    int *sa, *sb;                   // [P][dp*dp] support lists (row-major order)
+    int *ic;                        // [P][IC_N]
+    // inputs
+    const uint32_t *histA, *histB, *massA, *massB;
+    const int32_t* pairs;
+};
+
+cudaError_t pd_launch_raster(const double* birth, const double* death, const int64_t* offsets, int B,
+                             int d, int64_t npts, uint32_t* hist, uint32_t* mass, int* bad,
+                             cudaStream_t s);
+
+struct SkRun {
+    int max_iter;
+    double tol;
+    double tau;
+    int absorb_every;
+    double rel_thresh;   // relevance threshold (log) for the intermediate fits
+};
+
+cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s);
+cudaError_t sk_launch_logstep(const SkWS& w, SkRun r, cudaStream_t s);
+cudaError_t sk_launch_absorb(const SkWS& w, SkRun r, cudaStream_t s);
+cudaError_t sk_launch_iter_fp32(const SkWS& w, SkRun r, int n_inner, int* active_count, cudaStream_t s);
+cudaError_t sk_launch_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
+                               double* g, int32_t* iters, float* err, int32_t* status, cudaStream_t s);

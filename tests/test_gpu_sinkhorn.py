@@ -1,0 +1,130 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1805_08331_gb300 import api, inputs
+from gpu_util import dev, hists_to_gpu, masses, raster_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    api.load(build_if_missing=True)
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _solve(ctx, hA, hB, d, gamma, max_iter, tol, precision=api.PD_FP32, pairs=None, **kw):
+    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=max_iter, tol=tol, precision=precision)
+    out = api.pd_sinkhorn_batch(ctx, hists_to_gpu(hA), dev(masses(hA).view(np.int32)), hists_to_gpu(hB),
+                                dev(masses(hB).view(np.int32)), p, pairs=pairs, **kw)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+# --------------------------------------------------------------------------- rasteriser (bit-exact)
+@pytest.mark.parametrize("d", [2, 7, 32, 100, 128, 256])
+def test_raster_bit_exact(ctx, d):
+    b, t, o = inputs.random_diagrams(9, nmin=1, nmax=800, seed=d)
+    # edge points: on the diagonal, death = 1, cell edges, the origin
+    b = np.concatenate([b, [0.0, 0.5, 1.0, 0.25, 1 / d]])
+    t = np.concatenate([t, [0.0, 0.5, 1.0, 1.0, 2 / d]])
+    o = np.concatenate([o, [len(b)]])
+    hg, mg = raster_gpu(ctx, b, t, o, d)
+    ho, mo = oracle.rasterize(b, t, o, d)
+    assert np.array_equal(hg.cpu().numpy().view(np.uint32), ho)
+    assert np.array_equal(mg.cpu().numpy().view(np.uint32), mo)
+
+
+def test_raster_empty_diagrams_and_invalid(ctx):
+    b = np.array([0.1, 0.2]); t = np.array([0.3, 0.9]); o = np.array([0, 0, 2, 2])
+    hg, mg = raster_gpu(ctx, b, t, o, 16)
+    ho, mo = oracle.rasterize(b, t, o, 16)
+    assert np.array_equal(hg.cpu().numpy().view(np.uint32), ho) and list(mg.cpu().numpy()) == [0, 2, 0]
+    with pytest.raises(api.PdError) as e:
+        raster_gpu(ctx, np.array([0.5]), np.array([0.4]), np.array([0, 1]), 16)
+    assert e.value.status == api.PD_ERR_INVALID
+
+
+# --------------------------------------------------------------------------- Sinkhorn parity
+def test_config1_fp32_300_iterations(ctx):
+    """One pair of 20-point diagrams, d=32, gamma=1e-2, exactly 300 iterations."""
+    d, gamma = 32, 1e-2
+    b, t, o = inputs.random_diagrams(2, nmin=20, nmax=20, seed=0)
+    h, _ = oracle.rasterize(b, t, o, d)
+    r = oracle.sinkhorn_pd(d, gamma, h[0], h[1], 300, 0.0)
+    g = _solve(ctx, h[:1], h[1:], d, gamma, 300, 0.0, want_marginals=True, want_potentials=True)
+    assert g["iters"][0] == 300 and r["iters"] == 300
+    assert g["status"][0] == api.PD_NOT_CONVERGED
+    assert abs(g["cost"][0] - r["cost"]) <= 1e-6 * r["cost"]
+    assert abs(g["err"][0] - r["err"]) <= 1e-6 + 1e-3 * r["err"]
+    a, bb = oracle.augment(h[0], h[1])
+    assert np.allclose(g["row_marg"][0], r["rmarg"], rtol=2e-6, atol=1e-6)
+    assert np.allclose(g["col_marg"][0], r["cmarg"], rtol=2e-6, atol=1e-6)
+    ma, mb = a > 0, bb > 0
+    assert np.allclose(g["f"][0][ma], r["f"][ma], rtol=0, atol=gamma * 2e-5)
+    assert np.allclose(g["g"][0][mb], r["g"][mb], rtol=0, atol=gamma * 2e-5)
+
+
+@pytest.mark.parametrize("d,gamma", [(100, 1e-3), (128, 1e-3), (64, 5e-3)])
+def test_small_gamma_fixed_iterations(ctx, d, gamma):
+    """Paper-shaped pairs (50-500 points), log-stabilised small gamma, fixed 400
+    iterations on both sides: relative cost error <= 1e-6."""
+    b, t, o = inputs.random_diagrams(6, nmin=50, nmax=500, seed=d)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    ref = oracle.sinkhorn_pd_batch(d, gamma, hA, hB, 400, 0.0)
+    g = _solve(ctx, hA, hB, d, gamma, 400, 0.0)
+    assert np.all(g["iters"] == 400)
+    rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
+    assert rel.max() <= 1e-6, rel
+
+
+def test_small_gamma_converged(ctx):
+    """Stopping at relative marginal error 1e-6: costs agree with the converged
+    oracle within the stopping tolerance's effect."""
+    d, gamma = 100, 1e-3
+    b, t, o = inputs.random_diagrams(4, nmin=50, nmax=500, seed=1)
+    h, _ = oracle.rasterize(b, t, o, d)
+    ref = oracle.sinkhorn_pd_batch(d, gamma, h[0::2], h[1::2], 20000, 1e-6)
+    g = _solve(ctx, h[0::2], h[1::2], d, gamma, 20000, 1e-6)
+    assert np.all(g["status"] == api.PD_OK)
+    assert np.all(g["err"] <= 1e-6)
+    rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
+    assert rel.max() <= 5e-6, rel
+    assert np.all(np.abs(g["iters"] - ref["iters"]) <= 0.05 * ref["iters"] + 2)
+
+
+def test_pairs_index_and_edge_cases(ctx):
+    d, gamma = 32, 1e-2
+    b, t, o = inputs.random_diagrams(3, nmin=5, nmax=30, seed=3)
+    h, _ = oracle.rasterize(b, t, o, d)
+    empty = np.zeros((1, d, d), np.uint32)
+    one = np.zeros((1, d, d), np.uint32); one[0, 3, 20] = 2
+    H = np.concatenate([h, empty, one])                 # 0..2 random, 3 empty, 4 one cell
+    pairs = np.array([[0, 1], [1, 0], [2, 2], [0, 3], [3, 0], [3, 3], [4, 1], [4, 4]], dtype=np.int32)
+    g = _solve(ctx, H, H, d, gamma, 5000, 1e-9, pairs=dev(pairs))
+    for k, (i, j) in enumerate(pairs):
+        r = oracle.sinkhorn_pd(d, gamma, H[i], H[j], 5000, 1e-9)
+        assert abs(g["cost"][k] - r["cost"]) <= 2e-6 * max(r["cost"], 1e-12) + 1e-9, (k, g["cost"][k], r["cost"])
+    assert g["cost"][5] == 0.0 and g["status"][5] == api.PD_OK      # both empty
+    ii, jj = np.meshgrid(np.arange(d), np.arange(d), indexing="ij")
+    assert g["cost"][3] == pytest.approx(float((h[0] * ((jj - ii) / d) ** 2 / 2).sum()), rel=1e-6)
+
+
+def test_invalid_params(ctx):
+    h = np.zeros((1, 8, 8), np.uint32); h[0, 1, 2] = 1
+    for kw in (dict(gamma=-1.0), dict(d=300), dict(max_iter=0)):
+        p = api.pd_sinkhorn_default_params(1e-2, 8)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        with pytest.raises(api.PdError) as e:
+            api.pd_sinkhorn_batch(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), hists_to_gpu(h),
+                                  dev(masses(h).view(np.int32)), p)
+        assert e.value.status == api.PD_ERR_INVALID
