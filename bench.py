@@ -1,0 +1,400 @@
+"""Benchmark: batched Sinkhorn grid-cell updates/s on persistence-diagram pairs.
+
+Workload (default): 2048 pairs of synthetic diagrams, point counts log-uniform
+in [50, 500], birth ~ U[0,1), death = min(1, birth + Exp(mean 0.2)); grid
+d = 128 (the metric's grid); gamma = 1e-3 (log-stabilised); every pair runs
+until its relative marginal L1 error is <= 1e-6 (max 20000 iterations).
+
+One step = rasterise all diagrams + solve all pairs (Alg. 1) + transport cost
+(Prop. 2), inputs resident on the GPU.  value = sum over pairs of
+iterations * 2 (d^2 + 1) cell updates / time.  e2e repeats the step through
+the public API with the points in pinned host memory (H2D of the points and
+D2H of the costs inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp32|bf16] [--pairs P] [--d D]
+
+Under torchrun each rank solves its own batch (weak scaling, no data-path
+collective); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1805_08331_gb300 import inputs  # noqa: E402
+
+METRIC = "batched Sinkhorn grid-cell updates/s at d=128, fixed error vs FP64"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp32_dense", "bf16"])
+    ap.add_argument("--pairs", type=int, default=2048)
+    ap.add_argument("--d", type=int, default=128)
+    ap.add_argument("--gamma", type=float, default=1e-3)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-iter", type=int, default=20000)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-sample", type=int, default=16, help="pairs in the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--parity-sample", type=int, default=4, help="pairs checked against the oracle")
+    return ap.parse_args()
+
+
+def workload(args, rank):
+    """Points of 2*pairs diagrams (pair p = diagrams 2p, 2p+1)."""
+    b, t, o = inputs.random_diagrams(2 * args.pairs, nmin=50, nmax=500, exp_mean=0.2,
+                                     seed=args.seed + 1000 * rank)
+    return b, t, o
+
+
+def config_dict(args, precision):
+    return {"workload": f"{args.pairs} PD pairs, 50-500 points (log-uniform), birth~U[0,1), "
+                        f"death=min(1,birth+Exp(0.2)); d={args.d}; gamma={args.gamma:g} log-stabilised; "
+                        f"stop at relative marginal L1 error {args.tol:g}",
+            "pairs_per_gpu": args.pairs, "d": args.d, "gamma": args.gamma, "tol": args.tol,
+            "precision": precision, "l2": "flushed (512 MiB write) before every timed step"}
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, n in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- peaks
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            m = json.load(fh)
+        return m, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+FP32_LANES_PER_SM = 128
+MUFU_PER_SM = 16
+NUM_SMS = 152
+
+
+def fp32_peak_tflops(sm_mhz):
+    """CUDA-core FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x clock."""
+    return NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def mufu_peak_gexp(sm_mhz):
+    """Special-function-unit ex2 peak: 152 SMs x 16 ex2/clk x clock, in 1e9/s."""
+    return NUM_SMS * MUFU_PER_SM * sm_mhz * 1e6 / 1e9
+
+
+def lse_terms_per_iteration(hist, pairs, d):
+    """Log-sum-exp terms (one exponential each) of one iteration of the
+    log-domain engine for every pair: for each half-step, stage 1 has
+    nnz(in) x |columns of out| terms, stage 2 nnz(out) x |rows of in|, plus the
+    Delta terms."""
+    nz = hist.reshape(hist.shape[0], d, d) > 0
+    nnz = nz.reshape(nz.shape[0], -1).sum(1)
+    rows = nz.any(2).sum(1)
+    cols = nz.any(1).sum(1)
+    a, b = pairs[:, 0], pairs[:, 1]
+    u = nnz[b] * cols[a] + nnz[a] * rows[b] + nnz[a] + nnz[b] + 1
+    v = nnz[a] * cols[b] + nnz[b] * rows[a] + nnz[b] + nnz[a] + 1
+    return (u + v).astype(np.float64)
+
+
+# --------------------------------------------------------------------------- distributed helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- CPU baseline (oracle)
+def cpu_baseline(args, b, t, o, n_pairs):
+    import oracle
+    d = args.d
+    hist, _ = oracle.rasterize(b[:o[2 * n_pairs]], t[:o[2 * n_pairs]], o[:2 * n_pairs + 1], d)
+    t0 = time.perf_counter()
+    r = oracle.sinkhorn_pd_batch(d, args.gamma, hist[0::2], hist[1::2], args.max_iter, args.tol)
+    dt = time.perf_counter() - t0
+    cells = float(np.sum(r["iters"])) * 2 * (d * d + 1)
+    return {"value": cells / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {n_pairs} pairs of the workload solved to tol by the FP64 oracle "
+                      f"(OpenMP over pairs), {dt:.1f} s"}, r
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    import oracle
+    b, t, o = workload(args, 0)
+    n = max(1, min(args.cpu_sample // 2, args.pairs))
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not repeated on the CPU
+    times, cells = [], 0.0
+    for s in range(args.steps):
+        lo = (s * n) % max(1, args.pairs - n + 1)
+        sel = slice(2 * lo, 2 * (lo + n))
+        hist, _ = oracle.rasterize(b, t, o, args.d)
+        hA, hB = hist[sel][0::2], hist[sel][1::2]
+        t0 = time.perf_counter()
+        r = oracle.sinkhorn_pd_batch(args.d, args.gamma, hA, hB, args.max_iter, args.tol)
+        times.append(time.perf_counter() - t0)
+        cells += float(np.sum(r["iters"])) * 2 * (args.d * args.d + 1)
+    total = sum(times)
+    val = cells / total
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, "fp64 oracle"), "impl": "reference",
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"each step: {n} pairs of the workload solved to tol (OpenMP over pairs)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1805_08331_gb300 import api
+    api.load(build_if_missing=True)
+    ctx = api.Context(local)
+    precision = {"auto": api.PD_FP32, "fp32": api.PD_FP32, "fp32_dense": api.PD_FP32_DENSE,
+                 "bf16": api.PD_BF16}[args.precision]
+    pname = {api.PD_FP32: "fp32", api.PD_FP32_DENSE: "fp32", api.PD_BF16: "bf16"}[precision]
+    b, t, o = workload(args, rank)
+    d, P = args.d, args.pairs
+    params = api.pd_sinkhorn_default_params(args.gamma, d, max_iter=args.max_iter, tol=args.tol,
+                                            precision=precision)
+    db, dt_, do = torch.from_numpy(b).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(o).cuda()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    # pair p = (diagram 2p, diagram 2p+1), both read from the one rasterised batch
+    pairs = torch.arange(2 * P, dtype=torch.int32, device="cuda").view(P, 2).contiguous()
+
+    def step():
+        hist, mass = api.pd_rasterize(ctx, db, dt_, do, d)
+        return api.pd_sinkhorn_batch(ctx, hist, mass, hist, mass, params, pairs=pairs)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    hist0, _ = api.pd_rasterize(ctx, db, dt_, do, d)
+    terms = lse_terms_per_iteration(hist0.cpu().numpy(), pairs.cpu().numpy(), d)
+    barrier(ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile_enable(True)
+    ev = []
+    cells = 0.0
+    iters_in_iter_kernel = 0
+    lse_terms = 0.0
+    outs = None
+    torch.cuda.synchronize()
+    barrier(ws)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs = step()
+        e1.record(stream)
+        ev.append((e0, e1))
+        it = outs["iters"].cpu().numpy()
+        cells += float(it.sum()) * 2 * (d * d + 1)
+        iters_in_iter_kernel += int(np.maximum(it - 1, 0).sum())
+        lse_terms += float((it * terms).sum())
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    step_ms = [a.elapsed_time(bq) for a, bq in ev]
+    # the flush is excluded: each step is bracketed by its own events
+    my_ms = float(np.sum(step_ms))
+    tot_ms = max_over_ranks(my_ms, ws)
+    all_cells = sum_over_ranks(cells, ws)
+    value = all_cells / (tot_ms / 1e3)
+    status = outs["status"].cpu().numpy()
+    errs = outs["err"].cpu().numpy()
+
+    # ---- e2e through the public API with host buffers (pinned)
+    hb, ht, ho = (torch.from_numpy(x).pin_memory() for x in (b, t, o))
+    h2d = int(hb.numel() * 8 + ht.numel() * 8 + ho.numel() * 8)
+    d2h = int(P * 8)
+    e2e_cells, e2e_s = 0.0, 0.0
+    cost_host = torch.empty(P, dtype=torch.float64).pin_memory()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xb, xt, xo = hb.cuda(non_blocking=True), ht.cuda(non_blocking=True), ho.cuda(non_blocking=True)
+        hist, mass = api.pd_rasterize(ctx, xb, xt, xo, d)
+        out = api.pd_sinkhorn_batch(ctx, hist, mass, hist, mass, params, pairs=pairs)
+        cost_host.copy_(out["cost"], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+        e2e_cells += float(out["iters"].sum().item()) * 2 * (d * d + 1)
+    e2e_s = max_over_ranks(e2e_s, ws)
+    e2e_val = sum_over_ranks(e2e_cells, ws) / e2e_s
+
+    # ---- roofline of the dominant kernel (the iteration kernel)
+    pk, pk_kind = peaks()
+    iter_ms, iter_launches = prof.get("iter", (0.0, 0))
+    flops = iters_in_iter_kernel * 8.0 * d ** 3          # two d^3-MAC GEMMs per half-step
+    if precision == api.PD_BF16:
+        peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+        bound, unit, kname = "tensor", "TFLOP/s", "sk_iter (tcgen05 BF16 separable GEMMs)"
+        achieved = flops / (iter_ms / 1e3) / 1e12 if iter_ms > 0 else 0.0
+        src = f"{pk_kind} bf16_tflops_sustained"
+    elif precision == api.PD_FP32_DENSE:
+        peak = fp32_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+        bound, unit, kname = "alu", "TFLOP/s", "sk_iter_fp32_kernel (CUDA-core FP32 separable GEMMs)"
+        achieved = flops / (iter_ms / 1e3) / 1e12 if iter_ms > 0 else 0.0
+        src = f"{pk_kind} sm_max_mhz x 152 SMs x 128 FP32 lanes x 2"
+    else:
+        peak = mufu_peak_gexp(pk.get("sm_max_mhz", 2070.0))
+        bound, unit, kname = "alu", "Gexp/s", "sk_lse_iter_kernel (log-domain separable Sinkhorn)"
+        achieved = lse_terms / (iter_ms / 1e3) / 1e9 if iter_ms > 0 else 0.0
+        src = f"{pk_kind} sm_max_mhz x 152 SMs x 16 MUFU ex2/clk (one exponential per log-sum-exp term)"
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak if peak else None, "traffic": None, "kernel": kname, "peak_source": src,
+            "launches": iter_launches, "kernel_ms": iter_ms,
+            "share_of_step": iter_ms / my_ms if my_ms else None}
+    launches = int(sum(n for _, n in prof.values()))
+
+    # ---- parity sample and CPU baseline (rank 0 only)
+    cpu = None
+    parity = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n = max(1, min(args.cpu_sample, P))
+        cpu, ref = cpu_baseline(args, b, t, o, n)
+        k = min(args.parity_sample, n)
+        c_gpu = outs["cost"].cpu().numpy()[:k]
+        rel = np.abs(c_gpu - ref["cost"][:k]) / ref["cost"][:k]
+        parity = {"pairs_checked": int(k), "max_rel_cost_err_vs_fp64": float(rel.max())}
+    ctx.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": pname, "data": "synthetic",
+                "config": config_dict(args, pname), "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clk, "parity": parity,
+                "status_counts": {str(int(s)): int((status == s).sum()) for s in np.unique(status)},
+                "max_err": float(errs.max())}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -47,7 +47,14 @@ enum {
     PD_ERR_RANGE = 8      /* per pair: a scaling left the floating-point range even after absorption */
 };
 
-enum { PD_FP32 = 0, PD_BF16 = 1 };
+/* Engines of pd_sinkhorn_batch:
+ *   PD_FP32       exact log-domain separable evaluation (Prop. 1 in the log semiring) on the
+ *                 histogram supports, FP32 double-float arithmetic, FP64 potentials; any gamma.
+ *   PD_BF16       absorbed-potential linear-domain separable GEMMs on the tensor cores (tcgen05,
+ *                 BF16 operands, FP32 accumulation), then FP32 refinement by the PD_FP32 engine.
+ *   PD_FP32_DENSE absorbed-potential linear-domain separable GEMMs on the CUDA cores (FP32),
+ *                 one pair per CTA: the plain dense form. */
+enum { PD_FP32 = 0, PD_BF16 = 1, PD_FP32_DENSE = 2 };
 
 /* Version of this ABI (increments on incompatible change). */
 int pd_abi_version(void);
@@ -83,14 +90,17 @@ typedef struct {
     int d;             /* grid size, 2 <= d <= 256 */
     int max_iter;      /* maximum number of Sinkhorn iterations (each = u-update then v-update), >= 1 */
     double tol;        /* stop after iteration t if err_t / total mass <= tol (0 = run max_iter) */
-    int precision;     /* PD_FP32: CUDA-core FP32 GEMMs; PD_BF16: tcgen05 BF16 GEMMs, FP32 accumulate */
+    int precision;     /* engine: PD_FP32, PD_BF16 or PD_FP32_DENSE (see above) */
     int refine_iters;  /* PD_BF16 only: FP32 iterations run after the BF16 phase stops (0 = none) */
     double absorb_tau; /* re-absorb when |log(u~/a)| or |log(v~/b)| exceeds this (<= 0: default 20) */
     int absorb_every;  /* also re-absorb every this many iterations (<= 0: default 64) */
+    double rel_log_thresh; /* a term counts as relevant to an output when it is within exp(rel_log_thresh)
+                              of the output's sum; the absorbed representation keeps every relevant
+                              term in range (>= 0: default, -21 for PD_FP32 and -14 for PD_BF16) */
 } pd_sinkhorn_params;
 
 /* Fill *p with defaults for (gamma, d): max_iter 20000, tol 1e-6, PD_FP32,
- * refine_iters 0, absorb_tau 20, absorb_every 64. */
+ * refine_iters 0, absorb_tau 20, absorb_every 64, rel_log_thresh 0 (default). */
 void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, int d);
 
 /*

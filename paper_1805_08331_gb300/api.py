@@ -16,7 +16,7 @@ from . import build as _build
 
 PD_OK, PD_ERR_INVALID, PD_ERR_OOM, PD_ERR_CUDA, PD_ERR_TIMEOUT, PD_ERR_QUEUE_FULL = 0, 1, 2, 3, 4, 5
 PD_NOT_CONVERGED, PD_PENDING, PD_ERR_RANGE = 6, 7, 8
-PD_FP32, PD_BF16 = 0, 1
+PD_FP32, PD_BF16, PD_FP32_DENSE = 0, 1, 2
 STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID", 2: "PD_ERR_OOM", 3: "PD_ERR_CUDA", 4: "PD_ERR_TIMEOUT",
                 5: "PD_ERR_QUEUE_FULL", 6: "PD_NOT_CONVERGED", 7: "PD_PENDING", 8: "PD_ERR_RANGE"}
 
@@ -37,7 +37,7 @@ class SinkhornParams(ctypes.Structure):
     """Mirror of pd_sinkhorn_params."""
     _fields_ = [("gamma", ctypes.c_double), ("d", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int), ("refine_iters", ctypes.c_int),
-                ("absorb_tau", ctypes.c_double), ("absorb_every", ctypes.c_int)]
+                ("absorb_tau", ctypes.c_double), ("absorb_every", ctypes.c_int), ("rel_log_thresh", ctypes.c_double)]
 
 
 _lib = None

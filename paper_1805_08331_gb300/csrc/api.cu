@@ -5,12 +5,11 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <cmath>
 
 #include "pd_internal.h"
 #include "../../include/pd_ot.h"
 
-cudaError_t sk_set_aux(double* L64, int* rpa, int* rpb, int* cpa, int* cpb, int* cia, int* cib, float* ctab,
-                       cudaStream_t s);
 
 struct pd_ctx {
     int device = 0;
@@ -149,14 +148,14 @@ extern "C" void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, 
     p->refine_iters = 0;
     p->absorb_tau = 20.0;
     p->absorb_every = 64;
+    p->rel_log_thresh = 0.0;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Carve the workspace for P pairs at padded size dp; returns bytes needed when
 // base == nullptr.
-static size_t carve(char* base, int P, int d, int dp, double gamma, SkWS* w, double** L64, int** rpa, int** rpb,
-                    int** cpa, int** cpb, int** cia, int** cib, float** ctab, int** counter) {
+static size_t carve(char* base, int P, int d, int dp, double gamma, SkWS* w, int** counter) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* { char* r = base ? base + off : nullptr; off += align256(bytes); return r; };
     const size_t M = (size_t)dp * dp, n = M + 1;
@@ -174,14 +173,16 @@ static size_t carve(char* base, int P, int d, int dp, double gamma, SkWS* w, dou
     t.sa = (int*)take(sizeof(int) * M * P);
     t.sb = (int*)take(sizeof(int) * M * P);
     t.ic = (int*)take(sizeof(int) * IC_N * P);
-    *L64 = (double*)take(sizeof(double) * 2 * M * P);
-    *rpa = (int*)take(sizeof(int) * (dp + 1) * P);
-    *rpb = (int*)take(sizeof(int) * (dp + 1) * P);
-    *cpa = (int*)take(sizeof(int) * (dp + 1) * P);
-    *cpb = (int*)take(sizeof(int) * (dp + 1) * P);
-    *cia = (int*)take(sizeof(int) * M * P);
-    *cib = (int*)take(sizeof(int) * M * P);
-    *ctab = (float*)take(sizeof(float) * 2 * dp);
+    t.L64 = (double*)take(sizeof(double) * 2 * M * P);
+    t.la = (double*)take(sizeof(double) * M * P);
+    t.lb = (double*)take(sizeof(double) * M * P);
+    t.rpa = (int*)take(sizeof(int) * (dp + 1) * P);
+    t.rpb = (int*)take(sizeof(int) * (dp + 1) * P);
+    t.cpa = (int*)take(sizeof(int) * (dp + 1) * P);
+    t.cpb = (int*)take(sizeof(int) * (dp + 1) * P);
+    t.cia = (int*)take(sizeof(int) * M * P);
+    t.cib = (int*)take(sizeof(int) * M * P);
+    t.ctab = (float*)take(sizeof(float) * 5 * dp);
     *counter = (int*)take(sizeof(int) * 4);
     if (w) *w = t;
     return off;
@@ -200,7 +201,7 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     if (!(prm->gamma > 0) || !std::isfinite(prm->gamma)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: gamma must be > 0");
     if (prm->max_iter < 1) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: max_iter must be >= 1");
     if (!(prm->tol >= 0)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: tol must be >= 0");
-    if (prm->precision != PD_FP32 && prm->precision != PD_BF16)
+    if (prm->precision != PD_FP32 && prm->precision != PD_FP32_DENSE)
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: unknown precision %d", prm->precision);
     if (P < 0) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: P < 0");
     if (P == 0) return PD_OK;
@@ -209,8 +210,8 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     CUDA_TRY(c, cudaSetDevice(c->device));
     const int dp = ((d + 63) / 64) * 64;
     SkWS w;
-    double* L64; int *rpa, *rpb, *cpa, *cpb, *cia, *cib, *counter; float* ctab;
-    size_t need = carve(nullptr, P, d, dp, prm->gamma, nullptr, &L64, &rpa, &rpb, &cpa, &cpb, &cia, &cib, &ctab, &counter);
+    int* counter;
+    size_t need = carve(nullptr, P, d, dp, prm->gamma, nullptr, &counter);
     if (need > c->ws_bytes) {
         CUDA_TRY(c, cudaStreamSynchronize(s));
         if (c->ws) cudaFree(c->ws);
@@ -222,26 +223,51 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         }
         c->ws_bytes = need;
     }
-    carve((char*)c->ws, P, d, dp, prm->gamma, &w, &L64, &rpa, &rpb, &cpa, &cpb, &cia, &cib, &ctab, &counter);
+    carve((char*)c->ws, P, d, dp, prm->gamma, &w, &counter);
     w.histA = histA; w.histB = histB; w.massA = massA; w.massB = massB; w.pairs = pairs;
-    // c_m/gamma for m = 0..dp-1, split into FP32 hi + lo parts
-    std::vector<float> tab(2 * dp);
+    // Cost tables for m = 0..dp-1 (physical units, z = m/d): c_m/gamma = z^2/gamma and
+    // cD_m/gamma = z^2/(2 gamma), each split into FP32 hi + lo words; log c_m = 2 log z.
+    std::vector<float> tab(5 * dp);
     for (int m = 0; m < dp; ++m) {
         double z = (double)m / d;
-        double v = z * z / prm->gamma;
-        float hi = (float)v;
+        double v = z * z / prm->gamma, v2 = 0.5 * z * z / prm->gamma;
+        float hi = (float)v, hi2 = (float)v2;
         tab[m] = hi;
         tab[dp + m] = (float)(v - (double)hi);
+        tab[2 * dp + m] = hi2;
+        tab[3 * dp + m] = (float)(v2 - (double)hi2);
+        tab[4 * dp + m] = m == 0 ? -INFINITY : (float)(2.0 * std::log(z));
     }
-    CUDA_TRY(c, cudaMemcpyAsync(ctab, tab.data(), sizeof(float) * 2 * dp, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(c, sk_set_aux(L64, rpa, rpb, cpa, cpb, cia, cib, ctab, s));
+    CUDA_TRY(c, cudaMemcpyAsync(w.ctab, tab.data(), sizeof(float) * 5 * dp, cudaMemcpyHostToDevice, s));
     SkRun r;
     r.max_iter = prm->max_iter;
     r.tol = prm->tol;
     r.tau = prm->absorb_tau > 0 ? prm->absorb_tau : 20.0;
     r.absorb_every = prm->absorb_every > 0 ? prm->absorb_every : 64;
-    r.rel_thresh = -21.0;
+    r.rel_thresh = prm->rel_log_thresh < 0 ? prm->rel_log_thresh : (prm->precision == PD_BF16 ? -14.0 : -21.0);
     { ProfScope ps(c, PD_K_SETUP, s); CUDA_TRY(c, sk_launch_setup(w, g_init, s)); }
+    if (prm->precision == PD_FP32) {
+        // exact log-domain engine: no absorption, iterate until every pair stops
+        const int n_inner = 64;
+        const int max_rounds = prm->max_iter / n_inner + 2;
+        bool any_big = true;
+        for (int round = 0; round < max_rounds; ++round) {
+            CUDA_TRY(c, cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
+            { ProfScope ps(c, PD_K_ITER, s); CUDA_TRY(c, sk_launch_lse_smem(w, r, n_inner, counter, counter + 1, s)); }
+            if (any_big) {   // pairs whose supports do not fit on chip
+                ProfScope ps(c, PD_K_ITER, s);
+                CUDA_TRY(c, sk_launch_lse_iter(w, r, n_inner, counter, s));
+            }
+            CUDA_TRY(c, cudaMemcpyAsync(c->hflag, counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            if (round == 0) any_big = c->hflag[1] > 0;
+            if (c->hflag[0] == 0) break;
+        }
+        { ProfScope ps(c, PD_K_FINALIZE, s);
+          CUDA_TRY(c, sk_launch_lse_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, s)); }
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        return PD_OK;
+    }
     { ProfScope ps(c, PD_K_LOGSTEP, s); CUDA_TRY(c, sk_launch_logstep(w, r, s)); }
     const int max_rounds = prm->max_iter + 8;
     for (int round = 0; round < max_rounds; ++round) {

@@ -14,6 +14,7 @@ enum {
     SC_BD,       // b_Delta = |A|
     SC_TOTAL,    // total mass |A| + |B|
     SC_ERR,      // last relative marginal error
+    SC_TAU,      // residual threshold that triggers the next absorption
     SC_N
 };
 // Per-pair int slots.
@@ -26,6 +27,7 @@ enum {
     IC_FROMLIN,  // 1 = potentials must be rebuilt from the linear residuals
     IC_RANGE,    // consecutive range failures
     IC_SINCE,    // iterations since the last absorption
+    IC_BIG,      // 1 = supports too large for the on-chip log-domain kernel
     IC_N
 };
 enum { ST_ACTIVE = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_RANGE = 3, ST_INVALID = 4 };
@@ -52,6 +54,12 @@ struct SkWS {
     double *sc;                     // [P][SC_N]
     int *sa, *sb;                   // [P][dp*dp] support lists (row-major order)
     int *ic;                        // [P][IC_N]
+    // auxiliary per-pair arrays
+    double* L64;                    // [P][2*dp*dp] FP64 scratch
+    double *la, *lb;                // [P][dp*dp] log a, log b on the supports (FP64)
+    int *rpa, *rpb, *cpa, *cpb;     // [P][dp+1] row / column pointers of the support lists
+    int *cia, *cib;                 // [P][dp*dp] row indices of the column-major support lists
+    float* ctab;                    // [2*dp] hi / lo FP32 split of c_m/gamma, m = 0..dp-1
     // inputs
     const uint32_t *histA, *histB, *massA, *massB;
     const int32_t* pairs;
@@ -73,5 +81,10 @@ cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s)
 cudaError_t sk_launch_logstep(const SkWS& w, SkRun r, cudaStream_t s);
 cudaError_t sk_launch_absorb(const SkWS& w, SkRun r, cudaStream_t s);
 cudaError_t sk_launch_iter_fp32(const SkWS& w, SkRun r, int n_inner, int* active_count, cudaStream_t s);
+cudaError_t sk_launch_lse_iter(const SkWS& w, SkRun r, int n_inner, int* active_count, cudaStream_t s);
+cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count,
+                               cudaStream_t s);
+cudaError_t sk_launch_lse_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
+                                   double* g, int32_t* iters, float* err, int32_t* status, cudaStream_t s);
 cudaError_t sk_launch_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
                                double* g, int32_t* iters, float* err, int32_t* status, cudaStream_t s);

