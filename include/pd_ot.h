@@ -165,6 +165,41 @@ pd_status pd_profile_enable(pd_ctx* ctx, int enable);
  */
 pd_status pd_profile_read(pd_ctx* ctx, double* ms_host, int64_t* launches_host);
 
+/*
+ * pd_sinkhorn_batch_noalloc -- the PD_FP32 solve of pd_sinkhorn_batch without
+ * any memory allocation.  (A library feature; the paper has no counterpart.)
+ *
+ * For callers that must not allocate device memory: code that runs while a
+ * stream is being captured into a CUDA graph (cudaMalloc is not allowed
+ * there), applications that hand all device memory to their own pool
+ * allocator and forbid libraries from calling cudaMalloc / cudaFree (which also
+ * synchronise the device), and latency-critical serving threads that cannot
+ * afford an allocation's implicit synchronisation.  It takes no pd_ctx (a
+ * context allocates) and calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *
+ * Its workspace is a fixed 16 MiB array in device memory that every GPU that
+ * loads this library holds until the process exits.  That bounds the batch: the
+ * pairs must fit in 16 MiB of workspace, about 9 pairs at d = 100..128 and 35
+ * pairs at d <= 64; a larger P returns PD_ERR_INVALID.  params->precision must
+ * be PD_FP32.  Arguments, outputs and results are those of pd_sinkhorn_batch,
+ * computed on the current CUDA device.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (each
+ * call initialises everything it reads), so calls whose GPU work overlaps --
+ * on two streams, or from two host threads -- race and corrupt each other's
+ * results; serialise them.  Synchronises `stream`.
+ * Errors: PD_ERR_INVALID (bad params, NULL input/cost, P too large for the
+ * array), PD_ERR_CUDA.
+ */
+pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint32_t* massA,
+                                    const uint32_t* histB, const uint32_t* massB, const int32_t* pairs, int P,
+                                    const pd_sinkhorn_params* params, const double* g_init,
+                                    double* cost, float* row_marg, float* col_marg, double* f, double* g,
+                                    int32_t* iters, float* err, int32_t* status, pd_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID", 2: "PD_ERR_OOM", 3: "PD_ERR_CUD
 
 # Every symbol the header declares (checked by the ABI test).
 EXPORTED = ["pd_abi_version", "pd_ctx_create", "pd_ctx_destroy", "pd_last_error", "pd_rasterize",
-            "pd_sinkhorn_default_params", "pd_sinkhorn_batch", "pd_profile_enable", "pd_profile_read"]
+            "pd_sinkhorn_default_params", "pd_sinkhorn_batch", "pd_profile_enable", "pd_profile_read",
+            "pd_sinkhorn_batch_noalloc"]
 PD_K_RASTER, PD_K_SETUP, PD_K_LOGSTEP, PD_K_ABSORB, PD_K_ITER, PD_K_FINALIZE, PD_K_COUNT = 0, 1, 2, 3, 4, 5, 16
 KERNEL_NAMES = {0: "raster", 1: "setup", 2: "logstep", 3: "absorb", 4: "iter", 5: "finalize"}
 
@@ -72,6 +73,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.pd_sinkhorn_default_params.restype = None
         lib.pd_sinkhorn_batch.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(SinkhornParams),
                                           _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        lib.pd_sinkhorn_batch_noalloc.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                                  ctypes.POINTER(SinkhornParams), _vp, _vp, _vp, _vp, _vp, _vp,
+                                                  _vp, _vp, _vp, _vp]
         lib.pd_profile_enable.argtypes = [_vp, ctypes.c_int]
         lib.pd_profile_read.argtypes = [_vp, _vp, _vp]
         _lib = lib
@@ -176,4 +180,22 @@ def pd_sinkhorn_batch(ctx: Context, histA, massA, histB, massB, params: Sinkhorn
         ctx.handle, _ptr(histA), _ptr(massA), _ptr(histB), _ptr(massB), _ptr(pairs), int(P), ctypes.byref(params),
         _ptr(g_init), _ptr(o["cost"]), _ptr(o.get("row_marg")), _ptr(o.get("col_marg")), _ptr(o.get("f")),
         _ptr(o.get("g")), _ptr(o["iters"]), _ptr(o["err"]), _ptr(o["status"]), _stream(stream)))
+    return o
+
+
+def pd_sinkhorn_batch_noalloc(histA, massA, histB, massB, params: SinkhornParams, pairs=None, g_init=None,
+                              out=None, stream=None):
+    """The allocation-free solve (see include/pd_ot.h): same arguments as
+    pd_sinkhorn_batch but no context; output tensors must be supplied in `out`
+    (cost, iters, err, status; optional row_marg, col_marg, f, g) by callers
+    that cannot allocate.  Raises PdError on a non-PD_OK status."""
+    lib = load()
+    P = pairs.shape[0] if pairs is not None else histA.shape[0]
+    o = dict(out)
+    st = lib.pd_sinkhorn_batch_noalloc(
+        _ptr(histA), _ptr(massA), _ptr(histB), _ptr(massB), _ptr(pairs), int(P), ctypes.byref(params),
+        _ptr(g_init), _ptr(o["cost"]), _ptr(o.get("row_marg")), _ptr(o.get("col_marg")), _ptr(o.get("f")),
+        _ptr(o.get("g")), _ptr(o["iters"]), _ptr(o["err"]), _ptr(o["status"]), _stream(stream))
+    if st != PD_OK:
+        raise PdError(st, "pd_sinkhorn_batch_noalloc failed")
     return o

@@ -283,3 +283,85 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return PD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of pd_sinkhorn_batch (PD_FP32 engine only).
+//
+// Its workspace is the file-scope device array below instead of memory from
+// cudaMalloc: every GPU that loads this library reserves it for the lifetime
+// of the process.  Host code cannot use the array's name as a device address
+// (in host code it names a host-side stand-in), so the device address is
+// obtained once per device with cudaGetSymbolAddress and cached.
+#define PD_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define PD_NOALLOC_MAX_DEVICES 64
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PD_NOALLOC_SCRATCH_BYTES];
+static void* g_noalloc_addr[PD_NOALLOC_MAX_DEVICES];
+
+extern "C" pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint32_t* massA,
+                                               const uint32_t* histB, const uint32_t* massB,
+                                               const int32_t* pairs, int P, const pd_sinkhorn_params* prm,
+                                               const double* g_init, double* cost, float* row_marg,
+                                               float* col_marg, double* f, double* g, int32_t* iters,
+                                               float* err, int32_t* status, pd_stream stream) {
+    if (!prm) return PD_ERR_INVALID;
+    const int d = prm->d;
+    if (d < 2 || d > 256 || !(prm->gamma > 0) || !std::isfinite(prm->gamma) || prm->max_iter < 1 ||
+        !(prm->tol >= 0) || prm->precision != PD_FP32 || P < 0)
+        return PD_ERR_INVALID;
+    if (P == 0) return PD_OK;
+    if (!cost || !histA || !histB || !massA || !massB) return PD_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= PD_NOALLOC_MAX_DEVICES) return PD_ERR_CUDA;
+    // one-time set-up on this device: device address of the static scratch array
+    if (!g_noalloc_addr[dev]) {
+        void* a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_noalloc_scratch) != cudaSuccess || !a) return PD_ERR_CUDA;
+        g_noalloc_addr[dev] = a;
+    }
+    const int dp = ((d + 63) / 64) * 64;
+    int* counter = nullptr;
+    if (carve(nullptr, P, d, dp, prm->gamma, nullptr, &counter) > PD_NOALLOC_SCRATCH_BYTES)
+        return PD_ERR_INVALID;   // this many pairs at this d do not fit in the static scratch
+    SkWS w;
+    carve((char*)g_noalloc_addr[dev], P, d, dp, prm->gamma, &w, &counter);
+    w.histA = histA; w.histB = histB; w.massA = massA; w.massB = massB; w.pairs = pairs;
+    float tab[5 * 256];
+    for (int m = 0; m < dp; ++m) {
+        double z = (double)m / d;
+        double v = z * z / prm->gamma, v2 = 0.5 * z * z / prm->gamma;
+        float hi = (float)v, hi2 = (float)v2;
+        tab[m] = hi;
+        tab[dp + m] = (float)(v - (double)hi);
+        tab[2 * dp + m] = hi2;
+        tab[3 * dp + m] = (float)(v2 - (double)hi2);
+        tab[4 * dp + m] = m == 0 ? -INFINITY : (float)(2.0 * std::log(z));
+    }
+    if (cudaMemcpyAsync(w.ctab, tab, sizeof(float) * 5 * dp, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return PD_ERR_CUDA;
+    SkRun r;
+    r.max_iter = prm->max_iter;
+    r.tol = prm->tol;
+    r.tau = 20.0;
+    r.absorb_every = 64;
+    r.rel_thresh = -21.0;
+    if (sk_launch_setup(w, g_init, s) != cudaSuccess) return PD_ERR_CUDA;
+    const int n_inner = 64;
+    const int max_rounds = prm->max_iter / n_inner + 2;
+    int hcount[2] = {0, 0};
+    bool any_big = true;
+    for (int round = 0; round < max_rounds; ++round) {
+        if (cudaMemsetAsync(counter, 0, 2 * sizeof(int), s) != cudaSuccess) return PD_ERR_CUDA;
+        if (sk_launch_lse_smem(w, r, n_inner, counter, counter + 1, s) != cudaSuccess) return PD_ERR_CUDA;
+        if (any_big && sk_launch_lse_iter(w, r, n_inner, counter, s) != cudaSuccess) return PD_ERR_CUDA;
+        if (cudaMemcpyAsync(hcount, counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return PD_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return PD_ERR_CUDA;
+        if (round == 0) any_big = hcount[1] > 0;
+        if (hcount[0] == 0) break;
+    }
+    if (sk_launch_lse_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, s) != cudaSuccess)
+        return PD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PD_ERR_CUDA;
+    return PD_OK;
+}
