@@ -448,7 +448,7 @@ cudaError_t sk_launch_lse_finalize(const SkWS& w, double* cost, float* row_marg,
 // the input h.  Global memory is read at the start of the launch and written
 // at its end only.  Pairs that do not fit are marked and left to the
 // global-memory kernel above.
-#define LSE_SM_THREADS 512
+#define LSE_SM_THREADS 768
 
 struct SideS {
     int n;                 // support size
@@ -488,20 +488,44 @@ __device__ void sm_stage1(const SideS& in, const SideS& out, const float* Hh, co
         const int r = e / out.nc, c = e - r * out.nc;
         const int k = in.rows[r], j = out.cols[c];
         const int q0 = in.rp[k], q1 = in.rp[k + 1];
-        float m = -INFINITY;
-        for (int q = q0; q < q1; ++q) {
-            int mm = abs(j - in.cell[q] % dp);
-            df v = df_sub({Hh[q], Hl[q]}, chi[mm], clo[mm]);
-            m = fmaxf(m, v.hi);
-        }
-        Kahan s;
-        for (int q = q0; q < q1; ++q) {
-            int mm = abs(j - in.cell[q] % dp);
-            df v = df_sub({Hh[q], Hl[q]}, chi[mm], clo[mm]);
-            s.add(expf((v.hi - m) + v.lo));
+        float m, tot;
+        if (q1 - q0 <= 8) {
+            // the row's arguments, formed once (double-float), then max and sum from registers
+            float vh[8], vl[8];
+            m = -INFINITY;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (q0 + u < q1) {
+                    const int q = q0 + u, mm = abs(j - in.cell[q] % dp);
+                    df v = df_sub({Hh[q], Hl[q]}, chi[mm], clo[mm]);
+                    vh[u] = v.hi; vl[u] = v.lo;
+                    m = fmaxf(m, v.hi);
+                } else {
+                    vh[u] = -INFINITY; vl[u] = 0.f;
+                }
+            }
+            Kahan s;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (q0 + u < q1) s.add(expf((vh[u] - m) + vl[u]));
+            tot = s.s - s.c;
+        } else {
+            m = -INFINITY;
+            for (int q = q0; q < q1; ++q) {
+                int mm = abs(j - in.cell[q] % dp);
+                df v = df_sub({Hh[q], Hl[q]}, chi[mm], clo[mm]);
+                m = fmaxf(m, v.hi);
+            }
+            Kahan s;
+            for (int q = q0; q < q1; ++q) {
+                int mm = abs(j - in.cell[q] % dp);
+                df v = df_sub({Hh[q], Hl[q]}, chi[mm], clo[mm]);
+                s.add(expf((v.hi - m) + v.lo));
+            }
+            tot = s.s - s.c;
         }
         Lh[r * ld + c] = m;
-        Ll[r * ld + c] = log_acc(s.s - s.c);
+        Ll[r * ld + c] = log_acc(tot);
     }
     __syncthreads();
 }
@@ -521,29 +545,49 @@ __device__ double sm_halfstep(SideS& in, SideS& out, float* Hh, float* Hl, float
     sm_stage1(in, out, Hh, Hl, Lh, Ll, ld, chi, clo, dp);
     const df hD = df_from(in.lD + in.potD);
     double err = 0.0;
-    for (int e = wid; e < out.n; e += nw) {
-        const int cell = out.cell[e], i = cell / dp, j = cell - i * dp, c = out.colpos[j];
-        const int mmD = abs(j - i);
-        float m = -INFINITY;
-        for (int r = lane; r < in.nr; r += 32) {
-            int mm = abs(i - in.rows[r]);
-            df v = df_sub({Lh[r * ld + c], Ll[r * ld + c]}, chi[mm], clo[mm]);
-            m = fmaxf(m, v.hi);
+    // warp per non-empty output row i; lane holds rows r = lane + 32u of the input (u < 8)
+    for (int rr = wid; rr < out.nr; rr += nw) {
+        const int i = out.rows[rr];
+        float kh[8], kl[8];
+        int roff[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int r = lane + 32 * u;
+            if (r < in.nr) {
+                const int mm = abs(i - in.rows[r]);
+                kh[u] = chi[mm]; kl[u] = clo[mm]; roff[u] = r * ld;
+            } else {
+                kh[u] = 0.f; kl[u] = 0.f; roff[u] = -1;
+            }
         }
-        df vD = df_sub(hD, chi2[mmD], clo2[mmD]);
-        m = fmaxf(warp_max(m), vD.hi);
-        Kahan s;
-        for (int r = lane; r < in.nr; r += 32) {
-            int mm = abs(i - in.rows[r]);
-            df v = df_sub({Lh[r * ld + c], Ll[r * ld + c]}, chi[mm], clo[mm]);
-            s.add(expf((v.hi - m) + v.lo));
-        }
-        float tot = warp_sum(s.s - s.c);
-        if (hD.hi > -INFINITY) tot += expf((vD.hi - m) + vD.lo);
-        if (lane == 0) {
-            double nv = -((double)m + (double)log_acc(tot));
-            if (want_err) err += (double)(out.w[e] * fabsf(expm1f((float)(out.pot[e] - nv))));
-            out.pot[e] = nv;
+        for (int e = out.rp[i]; e < out.rp[i + 1]; ++e) {
+            const int cell = out.cell[e], j = cell - i * dp, c = out.colpos[j];
+            const int mmD = abs(j - i);
+            float vh[8], vl[8];
+            float m = -INFINITY;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (roff[u] >= 0) {
+                    df v = df_sub({Lh[roff[u] + c], Ll[roff[u] + c]}, kh[u], kl[u]);
+                    vh[u] = v.hi; vl[u] = v.lo;
+                    m = fmaxf(m, v.hi);
+                } else {
+                    vh[u] = -INFINITY; vl[u] = 0.f;
+                }
+            }
+            df vD = df_sub(hD, chi2[mmD], clo2[mmD]);
+            m = fmaxf(warp_max(m), vD.hi);
+            Kahan s;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (roff[u] >= 0) s.add(expf((vh[u] - m) + vl[u]));
+            float tot = warp_sum(s.s - s.c);
+            if (hD.hi > -INFINITY) tot += expf((vD.hi - m) + vD.lo);
+            if (lane == 0) {
+                double nv = -((double)m + (double)log_acc(tot));
+                if (want_err) err += (double)(out.w[e] * fabsf(expm1f((float)(out.pot[e] - nv))));
+                out.pot[e] = nv;
+            }
         }
     }
     // Delta output
