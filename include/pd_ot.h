@@ -138,6 +138,45 @@ pd_status pd_sinkhorn_batch(pd_ctx* ctx, const uint32_t* histA, const uint32_t* 
                             int32_t* iters, float* err, int32_t* status, pd_stream stream);
 
 
+/*
+ * pd_barycenter -- Alg. 2 (smoothed barycenter).  z starts as z_init, or, when
+ * z_init is NULL, as the uniform measure above the diagonal (every cell j >= i
+ * gets mean_i |D_i| / (d(d+1)/2)).  Each of the outer_iters steps solves the N
+ * pairs (z + R a_i, a_i + R z) with the PD_FP32 engine (warm-started from the
+ * previous step's g_i, the first step cold) and applies the multiplicative
+ * update z <- z exp(-lambda grad) where z > 0, with the gradient of the
+ * smoothed energy (the gradient proposition of Sec. 4) averaged over i:
+ *   grad(x) = mean_i [ gamma log z(x) + f_i(x) + gamma log|z| + g_i(Delta) ].
+ *   hist, mass  : uint32 [N][d][d], uint32 [N] (device)
+ *   params      : inner Sinkhorn parameters (precision must be PD_FP32)
+ *   lambda      : step size (> 0); outer_iters >= 0
+ *   z_init      : double [d*d] or NULL (device); z_out: double [d*d] (device)
+ *   energy      : double [outer_iters] or NULL: mean transport cost of step t's
+ *                 plans, (1/N) sum_i <P_i, C> (the energy of z_t) (device)
+ * Synchronises `stream`.  Errors: PD_ERR_INVALID, PD_ERR_OOM, PD_ERR_CUDA.
+ */
+pd_status pd_barycenter(pd_ctx* ctx, const uint32_t* hist, const uint32_t* mass, int N,
+                        const pd_sinkhorn_params* params, double lambda, int outer_iters,
+                        const double* z_init, double* z_out, double* energy, pd_stream stream);
+
+/*
+ * pd_kmeans -- k-means on persistence diagrams (Sec. 5): centroids start as k
+ * distinct input histograms drawn by splitmix64(seed) (draw r mod N, repeats
+ * skipped).  Each round assigns every diagram n to argmin_c <P, C> of the pair
+ * (a_n + R z_c, z_c + R a_n) (cold-started PD_FP32 solves; ties go to the lowest
+ * c), then moves every non-empty cluster's centroid by bary_steps steps of
+ * Alg. 2 over its members (the first step cold, the others warm-started); an
+ * empty cluster keeps its centroid.
+ *   hist, mass : uint32 [N][d][d], uint32 [N] (device); 1 <= k <= N
+ *   assign     : int32 [N] (device, output: assignment of the last round)
+ *   centroids  : double [k][d*d] (device, output)
+ *   objective  : double [rounds] or NULL (device): sum_n min_c cost at each round
+ * Synchronises `stream`.  Errors: PD_ERR_INVALID, PD_ERR_OOM, PD_ERR_CUDA.
+ */
+pd_status pd_kmeans(pd_ctx* ctx, const uint32_t* hist, const uint32_t* mass, int N, int k,
+                    const pd_sinkhorn_params* params, double lambda, int rounds, int bary_steps,
+                    uint64_t seed, int32_t* assign, double* centroids, double* objective, pd_stream stream);
+
 /* Kernel classes recorded by the launch profiler. */
 enum {
     PD_K_RASTER = 0,   /* rasteriser */

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID", 2: "PD_ERR_OOM", 3: "PD_ERR_CUD
 # Every symbol the header declares (checked by the ABI test).
 EXPORTED = ["pd_abi_version", "pd_ctx_create", "pd_ctx_destroy", "pd_last_error", "pd_rasterize",
             "pd_sinkhorn_default_params", "pd_sinkhorn_batch", "pd_profile_enable", "pd_profile_read",
-            "pd_sinkhorn_batch_noalloc"]
+            "pd_sinkhorn_batch_noalloc", "pd_barycenter", "pd_kmeans"]
 PD_K_RASTER, PD_K_SETUP, PD_K_LOGSTEP, PD_K_ABSORB, PD_K_ITER, PD_K_FINALIZE, PD_K_COUNT = 0, 1, 2, 3, 4, 5, 16
 KERNEL_NAMES = {0: "raster", 1: "setup", 2: "logstep", 3: "absorb", 4: "iter", 5: "finalize"}
 
@@ -76,6 +76,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.pd_sinkhorn_batch_noalloc.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int,
                                                   ctypes.POINTER(SinkhornParams), _vp, _vp, _vp, _vp, _vp, _vp,
                                                   _vp, _vp, _vp, _vp]
+        lib.pd_barycenter.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(SinkhornParams), ctypes.c_double,
+                                      ctypes.c_int, _vp, _vp, _vp, _vp]
+        lib.pd_kmeans.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SinkhornParams),
+                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _vp, _vp, _vp, _vp]
         lib.pd_profile_enable.argtypes = [_vp, ctypes.c_int]
         lib.pd_profile_read.argtypes = [_vp, _vp, _vp]
         _lib = lib
@@ -181,6 +185,34 @@ def pd_sinkhorn_batch(ctx: Context, histA, massA, histB, massB, params: Sinkhorn
         _ptr(g_init), _ptr(o["cost"]), _ptr(o.get("row_marg")), _ptr(o.get("col_marg")), _ptr(o.get("f")),
         _ptr(o.get("g")), _ptr(o["iters"]), _ptr(o["err"]), _ptr(o["status"]), _stream(stream)))
     return o
+
+
+def pd_barycenter(ctx: Context, hist, mass, params: SinkhornParams, lam: float, outer_iters: int, z_init=None,
+                  stream=None):
+    """Alg. 2 on N histograms (int32 CUDA tensors holding uint32 counts).
+    Returns (z [d,d] float64 CUDA tensor, energy [outer_iters] float64)."""
+    import torch
+    d = params.d
+    z = torch.empty((d, d), dtype=torch.float64, device=hist.device)
+    e = torch.empty(max(outer_iters, 1), dtype=torch.float64, device=hist.device)
+    ctx.check(ctx.lib.pd_barycenter(ctx.handle, _ptr(hist), _ptr(mass), int(hist.shape[0]), ctypes.byref(params),
+                                    float(lam), int(outer_iters), _ptr(z_init), _ptr(z), _ptr(e), _stream(stream)))
+    return z, e[:outer_iters]
+
+
+def pd_kmeans(ctx: Context, hist, mass, k: int, params: SinkhornParams, lam: float, rounds: int, bary_steps: int,
+              seed: int = 0, stream=None):
+    """k-means on N histograms.  Returns (assign [N] int32, centroids [k,d,d]
+    float64, objective [rounds] float64) as CUDA tensors."""
+    import torch
+    d, N = params.d, int(hist.shape[0])
+    assign = torch.empty(N, dtype=torch.int32, device=hist.device)
+    cent = torch.empty((k, d, d), dtype=torch.float64, device=hist.device)
+    obj = torch.empty(max(rounds, 1), dtype=torch.float64, device=hist.device)
+    ctx.check(ctx.lib.pd_kmeans(ctx.handle, _ptr(hist), _ptr(mass), N, int(k), ctypes.byref(params), float(lam),
+                                int(rounds), int(bary_steps), ctypes.c_uint64(seed), _ptr(assign), _ptr(cent),
+                                _ptr(obj), _stream(stream)))
+    return assign, cent, obj[:rounds]
 
 
 def pd_sinkhorn_batch_noalloc(histA, massA, histB, massB, params: SinkhornParams, pairs=None, g_init=None,

@@ -16,6 +16,8 @@ struct pd_ctx {
     std::string err;
     void* ws = nullptr;        // Sinkhorn workspace
     size_t ws_bytes = 0;
+    void* ws2 = nullptr;       // outer-loop buffers (barycenter, k-means)
+    size_t ws2_bytes = 0;
     int* dflag = nullptr;      // small device scratch (error flags, counters)
     int* hflag = nullptr;      // pinned host mirror
     // launch profiler
@@ -79,6 +81,7 @@ extern "C" void pd_ctx_destroy(pd_ctx* c) {
     for (auto& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->ws) cudaFree(c->ws);
+    if (c->ws2) cudaFree(c->ws2);
     if (c->dflag) cudaFree(c->dflag);
     if (c->hflag) cudaFreeHost(c->hflag);
     delete c;
@@ -188,6 +191,78 @@ static size_t carve(char* base, int P, int d, int dp, double gamma, SkWS* w, int
     return off;
 }
 
+
+// Cost tables for m = 0..dp-1 (physical units, z = m/d): c_m/gamma = z^2/gamma and
+// cD_m/gamma = z^2/(2 gamma), each split into FP32 hi + lo words; log c_m = 2 log z.
+static cudaError_t upload_cost_tables(const SkWS& w, double gamma, cudaStream_t s) {
+    const int dp = w.dp, d = w.d;
+    std::vector<float> tab(5 * dp);
+    for (int m = 0; m < dp; ++m) {
+        double z = (double)m / d;
+        double v = z * z / gamma, v2 = 0.5 * z * z / gamma;
+        float hi = (float)v, hi2 = (float)v2;
+        tab[m] = hi;
+        tab[dp + m] = (float)(v - (double)hi);
+        tab[2 * dp + m] = hi2;
+        tab[3 * dp + m] = (float)(v2 - (double)hi2);
+        tab[4 * dp + m] = m == 0 ? -INFINITY : (float)(2.0 * std::log(z));
+    }
+    return cudaMemcpyAsync(w.ctab, tab.data(), sizeof(float) * 5 * dp, cudaMemcpyHostToDevice, s);
+}
+
+static SkRun make_run(const pd_sinkhorn_params* prm) {
+    SkRun r;
+    r.max_iter = prm->max_iter;
+    r.tol = prm->tol;
+    r.tau = prm->absorb_tau > 0 ? prm->absorb_tau : 20.0;
+    r.absorb_every = prm->absorb_every > 0 ? prm->absorb_every : 64;
+    r.rel_thresh = prm->rel_log_thresh < 0 ? prm->rel_log_thresh : (prm->precision == PD_BF16 ? -14.0 : -21.0);
+    r.pot_support_only = 0;
+    return r;
+}
+
+// Grow-only device buffer owned by the context.
+static pd_status ensure_buffer(pd_ctx* c, void** buf, size_t* have, size_t need, cudaStream_t s) {
+    if (need <= *have) return PD_OK;
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc(buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PD_ERR_OOM, "cannot allocate %zu bytes of workspace", need);
+    }
+    *have = need;
+    return PD_OK;
+}
+
+// The PD_FP32 (log-domain) solve of the pairs described by w, on stream s:
+// set-up, iteration rounds until every pair stops, finalize.  Synchronises s
+// once per round (convergence check).
+static pd_status lse_solve(pd_ctx* c, SkWS& w, SkRun r, const double* g_init, double* cost, float* row_marg,
+                           float* col_marg, double* f, double* g, int32_t* iters, float* err, int32_t* status,
+                           int* counter, cudaStream_t s) {
+    { ProfScope ps(c, PD_K_SETUP, s); CUDA_TRY(c, sk_launch_setup(w, g_init, s)); }
+    const int n_inner = 64;
+    const int max_rounds = r.max_iter / n_inner + 2;
+    bool any_big = true;
+    for (int round = 0; round < max_rounds; ++round) {
+        CUDA_TRY(c, cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
+        { ProfScope ps(c, PD_K_ITER, s); CUDA_TRY(c, sk_launch_lse_smem(w, r, n_inner, counter, counter + 1, s)); }
+        if (any_big) {   // pairs whose supports do not fit on chip
+            ProfScope ps(c, PD_K_ITER, s);
+            CUDA_TRY(c, sk_launch_lse_iter(w, r, n_inner, counter, s));
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(c->hflag, counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (round == 0) any_big = c->hflag[1] > 0;
+        if (c->hflag[0] == 0) break;
+    }
+    { ProfScope ps(c, PD_K_FINALIZE, s);
+      CUDA_TRY(c, sk_launch_lse_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, r.pot_support_only, s)); }
+    return PD_OK;
+}
+
 extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const uint32_t* massA, const uint32_t* histB,
                                        const uint32_t* massB, const int32_t* pairs, int P,
                                        const pd_sinkhorn_params* prm, const double* g_init, double* cost,
@@ -225,49 +300,15 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     }
     carve((char*)c->ws, P, d, dp, prm->gamma, &w, &counter);
     w.histA = histA; w.histB = histB; w.massA = massA; w.massB = massB; w.pairs = pairs;
-    // Cost tables for m = 0..dp-1 (physical units, z = m/d): c_m/gamma = z^2/gamma and
-    // cD_m/gamma = z^2/(2 gamma), each split into FP32 hi + lo words; log c_m = 2 log z.
-    std::vector<float> tab(5 * dp);
-    for (int m = 0; m < dp; ++m) {
-        double z = (double)m / d;
-        double v = z * z / prm->gamma, v2 = 0.5 * z * z / prm->gamma;
-        float hi = (float)v, hi2 = (float)v2;
-        tab[m] = hi;
-        tab[dp + m] = (float)(v - (double)hi);
-        tab[2 * dp + m] = hi2;
-        tab[3 * dp + m] = (float)(v2 - (double)hi2);
-        tab[4 * dp + m] = m == 0 ? -INFINITY : (float)(2.0 * std::log(z));
-    }
-    CUDA_TRY(c, cudaMemcpyAsync(w.ctab, tab.data(), sizeof(float) * 5 * dp, cudaMemcpyHostToDevice, s));
-    SkRun r;
-    r.max_iter = prm->max_iter;
-    r.tol = prm->tol;
-    r.tau = prm->absorb_tau > 0 ? prm->absorb_tau : 20.0;
-    r.absorb_every = prm->absorb_every > 0 ? prm->absorb_every : 64;
-    r.rel_thresh = prm->rel_log_thresh < 0 ? prm->rel_log_thresh : (prm->precision == PD_BF16 ? -14.0 : -21.0);
-    { ProfScope ps(c, PD_K_SETUP, s); CUDA_TRY(c, sk_launch_setup(w, g_init, s)); }
+    CUDA_TRY(c, upload_cost_tables(w, prm->gamma, s));
+    SkRun r = make_run(prm);
     if (prm->precision == PD_FP32) {
-        // exact log-domain engine: no absorption, iterate until every pair stops
-        const int n_inner = 64;
-        const int max_rounds = prm->max_iter / n_inner + 2;
-        bool any_big = true;
-        for (int round = 0; round < max_rounds; ++round) {
-            CUDA_TRY(c, cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
-            { ProfScope ps(c, PD_K_ITER, s); CUDA_TRY(c, sk_launch_lse_smem(w, r, n_inner, counter, counter + 1, s)); }
-            if (any_big) {   // pairs whose supports do not fit on chip
-                ProfScope ps(c, PD_K_ITER, s);
-                CUDA_TRY(c, sk_launch_lse_iter(w, r, n_inner, counter, s));
-            }
-            CUDA_TRY(c, cudaMemcpyAsync(c->hflag, counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(c, cudaStreamSynchronize(s));
-            if (round == 0) any_big = c->hflag[1] > 0;
-            if (c->hflag[0] == 0) break;
-        }
-        { ProfScope ps(c, PD_K_FINALIZE, s);
-          CUDA_TRY(c, sk_launch_lse_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, s)); }
+        pd_status st = lse_solve(c, w, r, g_init, cost, row_marg, col_marg, f, g, iters, err, status, counter, s);
+        if (st != PD_OK) return st;
         CUDA_TRY(c, cudaStreamSynchronize(s));
         return PD_OK;
     }
+    { ProfScope ps(c, PD_K_SETUP, s); CUDA_TRY(c, sk_launch_setup(w, g_init, s)); }
     { ProfScope ps(c, PD_K_LOGSTEP, s); CUDA_TRY(c, sk_launch_logstep(w, r, s)); }
     const int max_rounds = prm->max_iter + 8;
     for (int round = 0; round < max_rounds; ++round) {
@@ -280,6 +321,177 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     }
     { ProfScope ps(c, PD_K_ABSORB, s); CUDA_TRY(c, sk_launch_absorb(w, r, s)); }   // pairs that finished inside the log step
     { ProfScope ps(c, PD_K_FINALIZE, s); CUDA_TRY(c, sk_launch_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, s)); }
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Outer loops: barycenter (Alg. 2) and k-means (Sec. 5).
+
+static pd_status check_params(pd_ctx* c, const pd_sinkhorn_params* prm, const char* who) {
+    if (!prm) return fail(c, PD_ERR_INVALID, "%s: NULL params", who);
+    if (prm->d < 2 || prm->d > 256) return fail(c, PD_ERR_INVALID, "%s: d must be in [2,256]", who);
+    if (!(prm->gamma > 0) || !std::isfinite(prm->gamma)) return fail(c, PD_ERR_INVALID, "%s: gamma must be > 0", who);
+    if (prm->max_iter < 1) return fail(c, PD_ERR_INVALID, "%s: max_iter must be >= 1", who);
+    if (!(prm->tol >= 0)) return fail(c, PD_ERR_INVALID, "%s: tol must be >= 0", who);
+    if (prm->precision != PD_FP32) return fail(c, PD_ERR_INVALID, "%s: only PD_FP32 is supported", who);
+    return PD_OK;
+}
+
+// Carve a Sinkhorn workspace for P pairs in c->ws.
+static pd_status sinkhorn_ws(pd_ctx* c, int P, const pd_sinkhorn_params* prm, SkWS* w, int** counter,
+                             cudaStream_t s) {
+    const int d = prm->d, dp = ((d + 63) / 64) * 64;
+    size_t need = carve(nullptr, P, d, dp, prm->gamma, nullptr, counter);
+    pd_status st = ensure_buffer(c, &c->ws, &c->ws_bytes, need, s);
+    if (st != PD_OK) return st;
+    carve((char*)c->ws, P, d, dp, prm->gamma, w, counter);
+    CUDA_TRY(c, upload_cost_tables(*w, prm->gamma, s));
+    return PD_OK;
+}
+
+// Sub-allocator over c->ws2.
+struct Arena {
+    char* base; size_t off;
+    template <class T> T* take(size_t n) { T* r = (T*)(base ? base + off : nullptr); off += (n * sizeof(T) + 255) & ~size_t(255); return r; }
+};
+
+extern "C" pd_status pd_barycenter(pd_ctx* c, const uint32_t* hist, const uint32_t* mass, int N,
+                                   const pd_sinkhorn_params* prm, double lambda, int outer_iters,
+                                   const double* z_init, double* z_out, double* energy, pd_stream stream) {
+    if (!c) return PD_ERR_INVALID;
+    c->err.clear();
+    pd_status st = check_params(c, prm, "pd_barycenter");
+    if (st != PD_OK) return st;
+    if (N < 1 || !hist || !mass || !z_out) return fail(c, PD_ERR_INVALID, "pd_barycenter: need N >= 1, hist, mass, z_out");
+    if (!(lambda > 0) || outer_iters < 0) return fail(c, PD_ERR_INVALID, "pd_barycenter: need lambda > 0, outer_iters >= 0");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const int d = prm->d, D = d * d, n1 = D + 1;
+    Arena a{nullptr, 0};
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            st = ensure_buffer(c, &c->ws2, &c->ws2_bytes, a.off, s);
+            if (st != PD_OK) return st;
+            a = Arena{(char*)c->ws2, 0};
+        }
+        a.take<double>(D); a.take<double>(1); a.take<double>((size_t)N * n1); a.take<double>((size_t)N * n1);
+        a.take<double>(N); a.take<int32_t>(2 * (size_t)N); a.take<int32_t>(N); a.take<float>(N); a.take<int32_t>(N);
+        if (pass == 0) continue;
+    }
+    a.off = 0;
+    double* z = a.take<double>(D);
+    double* zmass = a.take<double>(1);
+    double* f = a.take<double>((size_t)N * n1);
+    double* g = a.take<double>((size_t)N * n1);
+    double* cost = a.take<double>(N);
+    int32_t* pairs = a.take<int32_t>(2 * (size_t)N);
+    int32_t* iters = a.take<int32_t>(N);
+    float* err = a.take<float>(N);
+    int32_t* status = a.take<int32_t>(N);
+    SkWS w;
+    int* counter;
+    st = sinkhorn_ws(c, N, prm, &w, &counter, s);
+    if (st != PD_OK) return st;
+    if (z_init) CUDA_TRY(c, cudaMemcpyAsync(z, z_init, sizeof(double) * D, cudaMemcpyDeviceToDevice, s));
+    else CUDA_TRY(c, outer_bary_init_uniform(z, mass, N, d, s));
+    CUDA_TRY(c, outer_owner_pairs(nullptr, N, pairs, s));
+    SkRun r = make_run(prm);
+    r.pot_support_only = 1;
+    for (int t = 0; t < outer_iters; ++t) {
+        CUDA_TRY(c, outer_measure_mass(z, 1, d, zmass, s));
+        w.histA = nullptr; w.massA = nullptr; w.wA = z;            // a side: z + R a_i
+        w.histB = hist; w.massB = mass; w.wB = nullptr;            // b side: a_i + R z
+        w.pairs = pairs;
+        st = lse_solve(c, w, r, t > 0 ? g : nullptr, cost, nullptr, nullptr, f, g, iters, err, status, counter, s);
+        if (st != PD_OK) return st;
+        if (energy) CUDA_TRY(c, outer_mean(cost, N, energy + t, s));
+        CUDA_TRY(c, outer_bary_step(z, zmass, f, g, nullptr, N, 1, d, prm->gamma, lambda, s));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(z_out, z, sizeof(double) * D, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+// splitmix64 (Steele, Lea & Flood, OOPSLA 2014).
+static uint64_t splitmix64_next(uint64_t* st) {
+    uint64_t z = (*st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+extern "C" pd_status pd_kmeans(pd_ctx* c, const uint32_t* hist, const uint32_t* mass, int N, int k,
+                               const pd_sinkhorn_params* prm, double lambda, int rounds, int bary_steps,
+                               uint64_t seed, int32_t* assign, double* centroids, double* objective,
+                               pd_stream stream) {
+    if (!c) return PD_ERR_INVALID;
+    c->err.clear();
+    pd_status st = check_params(c, prm, "pd_kmeans");
+    if (st != PD_OK) return st;
+    if (N < 1 || k < 1 || k > N || !hist || !mass || !assign || !centroids)
+        return fail(c, PD_ERR_INVALID, "pd_kmeans: need 1 <= k <= N and non-NULL hist, mass, assign, centroids");
+    if (!(lambda > 0) || rounds < 0 || bary_steps < 0)
+        return fail(c, PD_ERR_INVALID, "pd_kmeans: need lambda > 0, rounds >= 0, bary_steps >= 0");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const int d = prm->d, D = d * d, n1 = D + 1;
+    const size_t NK = (size_t)N * k;
+    Arena a{nullptr, 0};
+    auto layout = [&](Arena& ar, double** zmass, double** f, double** g, double** cost, int32_t** pairs,
+                      int32_t** iters, float** err, int32_t** status, int32_t** idx) {
+        *zmass = ar.take<double>(k); *f = ar.take<double>((size_t)N * n1); *g = ar.take<double>((size_t)N * n1);
+        *cost = ar.take<double>(NK); *pairs = ar.take<int32_t>(2 * NK); *iters = ar.take<int32_t>(NK);
+        *err = ar.take<float>(NK); *status = ar.take<int32_t>(NK); *idx = ar.take<int32_t>(k);
+    };
+    double *zmass, *f, *g, *cost; int32_t *pairs, *iters, *status, *idx; float* err;
+    layout(a, &zmass, &f, &g, &cost, &pairs, &iters, &err, &status, &idx);
+    st = ensure_buffer(c, &c->ws2, &c->ws2_bytes, a.off, s);
+    if (st != PD_OK) return st;
+    a = Arena{(char*)c->ws2, 0};
+    layout(a, &zmass, &f, &g, &cost, &pairs, &iters, &err, &status, &idx);
+    // seeding: k distinct histograms drawn by splitmix64(seed), draw r mod N, repeats skipped
+    std::vector<int32_t> chosen;
+    uint64_t stt = seed;
+    while ((int)chosen.size() < k) {
+        int r0 = (int)(splitmix64_next(&stt) % (uint64_t)N);
+        if (std::find(chosen.begin(), chosen.end(), r0) == chosen.end()) chosen.push_back(r0);
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(idx, chosen.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, outer_km_seed(hist, idx, k, d, centroids, s));
+    SkWS w;
+    int* counter;
+    st = sinkhorn_ws(c, (int)std::max(NK, (size_t)N), prm, &w, &counter, s);
+    if (st != PD_OK) return st;
+    SkRun r = make_run(prm);
+    for (int rd = 0; rd < rounds; ++rd) {
+        // assignment: pairs (a_n + R z_c, z_c + R a_n) for every n, c
+        CUDA_TRY(c, outer_km_pairs(N, k, pairs, s));
+        SkWS wa = w;
+        wa.P = (int)NK;
+        wa.histA = hist; wa.massA = mass; wa.wA = nullptr;
+        wa.histB = nullptr; wa.massB = nullptr; wa.wB = centroids;
+        wa.pairs = pairs;
+        r.pot_support_only = 0;
+        st = lse_solve(c, wa, r, nullptr, cost, nullptr, nullptr, nullptr, nullptr, iters, err, status, counter, s);
+        if (st != PD_OK) return st;
+        CUDA_TRY(c, outer_km_assign(cost, N, k, assign, objective ? objective + rd : nullptr, s));
+        // centroid update: bary_steps steps of Alg. 2 per cluster, all clusters batched
+        CUDA_TRY(c, outer_owner_pairs(assign, N, pairs, s));
+        SkWS wb = w;
+        wb.P = N;
+        wb.histA = nullptr; wb.massA = nullptr; wb.wA = centroids;
+        wb.histB = hist; wb.massB = mass; wb.wB = nullptr;
+        wb.pairs = pairs;
+        r.pot_support_only = 1;
+        for (int st2 = 0; st2 < bary_steps; ++st2) {
+            CUDA_TRY(c, outer_measure_mass(centroids, k, d, zmass, s));
+            st = lse_solve(c, wb, r, st2 > 0 ? g : nullptr, cost, nullptr, nullptr, f, g, iters, err, status, counter, s);
+            if (st != PD_OK) return st;
+            CUDA_TRY(c, outer_bary_step(centroids, zmass, f, g, assign, N, k, d, prm->gamma, lambda, s));
+        }
+    }
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return PD_OK;
 }
@@ -360,7 +572,7 @@ extern "C" pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint
         if (round == 0) any_big = hcount[1] > 0;
         if (hcount[0] == 0) break;
     }
-    if (sk_launch_lse_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, s) != cudaSuccess)
+    if (sk_launch_lse_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, 0, s) != cudaSuccess)
         return PD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return PD_ERR_CUDA;
     return PD_OK;

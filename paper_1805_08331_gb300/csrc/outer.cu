@@ -1,0 +1,158 @@
+// outer.cu -- kernels of the barycenter (Alg. 2) and k-means (Sec. 5) loops.
+//
+// Both loops run batched Sinkhorn solves (Alg. 1) between a real-valued
+// measure z (barycenter / centroid) and integer histograms a_i, as the pairs
+// (z + R a_i, a_i + R z) of Alg. 2, and then apply the gradient of the
+// smoothed energy (the gradient proposition of Sec. 4):
+//     grad(x) = gamma log u_i(x) + gamma log v_i(Delta),  summed over i,
+// where u_i = z exp(f_i/gamma) on the z side and v_i(Delta) = |z| exp(g_i(Delta)/gamma)
+// (R^T maps the Delta value to a constant on the grid), so
+//     gamma log u_i(x) + gamma log v_i(Delta) = gamma log z(x) + f_i(x) + gamma log|z| + g_i(Delta).
+// The gradient is averaged over the diagrams (the energy is the mean) and the
+// multiplicative update of Alg. 2, z <- z exp(-lambda grad), is applied where
+// z > 0.  Sums over diagrams are FP64 in a fixed order (deterministic).
+#include "pd_common.cuh"
+#include <stdint.h>
+
+// z = uniform measure above the diagonal: every cell with j >= i gets
+// (mean histogram mass) / (d (d+1) / 2).
+__global__ void bary_init_uniform_kernel(double* __restrict__ z, const uint32_t* __restrict__ mass, int N, int d) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s += (double)mass[i];
+    s = block_sum(s, sh);
+    const double per = (s / N) / (d * (d + 1) / 2.0);
+    for (int x = threadIdx.x; x < d * d; x += blockDim.x) z[x] = ((x % d) >= (x / d)) ? per : 0.0;
+}
+
+// |z_c| for every measure c (one block per measure).
+__global__ void measure_mass_kernel(const double* __restrict__ z, int d, double* __restrict__ out) {
+    __shared__ double sh[32];
+    const double* zc = z + (size_t)blockIdx.x * d * d;
+    double s = 0.0;
+    for (int x = threadIdx.x; x < d * d; x += blockDim.x) s += zc[x];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// Multiplicative gradient step for k measures at once.  Diagram n belongs to
+// measure owner[n] (owner == NULL: all to measure 0); f, g are the potentials of
+// the pair (z_owner[n] + R a_n, a_n + R z_owner[n]) with n = d*d+1 entries per pair.
+// One thread per (measure c, cell x).
+__global__ void bary_step_kernel(double* __restrict__ z, const double* __restrict__ zmass,
+                                 const double* __restrict__ f, const double* __restrict__ g,
+                                 const int32_t* __restrict__ owner, int N, int k, int d, double gamma,
+                                 double lambda) {
+    const int D = d * d, n1 = D + 1;
+    const int64_t tot = (int64_t)k * D;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / D), x = (int)(e % D);
+        double* zc = z + (size_t)c * D;
+        const double zx = zc[x];
+        if (!(zx > 0.0)) continue;
+        const double base = gamma * log(zx) + gamma * log(zmass[c]);
+        double s = 0.0;
+        int m = 0;
+        for (int i = 0; i < N; ++i) {
+            if (owner && owner[i] != c) continue;
+            s += base + f[(size_t)i * n1 + x] + g[(size_t)i * n1 + D];
+            ++m;
+        }
+        if (m > 0) zc[x] = zx * exp(-lambda * (s / m));
+    }
+}
+
+// energy[slot] = mean of cost[0..N)  (one block, fixed order).
+__global__ void mean_kernel(const double* __restrict__ cost, int N, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s += cost[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) *out = s / N;
+}
+
+// k-means assignment: assign[n] = argmin_c cost[n*k + c] (ties -> lowest c);
+// objective = sum_n min_c cost (one block, fixed order).
+__global__ void km_assign_kernel(const double* __restrict__ cost, int N, int k, int32_t* __restrict__ assign,
+                                 double* __restrict__ objective) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        int best = 0;
+        double bv = cost[(size_t)n * k];
+        for (int c = 1; c < k; ++c) {
+            double v = cost[(size_t)n * k + c];
+            if (v < bv) { bv = v; best = c; }
+        }
+        assign[n] = best;
+        s += bv;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0 && objective) *objective = s;
+}
+
+// centroid c <- histogram idx[c] as real weights.
+__global__ void km_seed_kernel(const uint32_t* __restrict__ hist, const int32_t* __restrict__ idx, int k, int d,
+                               double* __restrict__ z) {
+    const int D = d * d;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * D;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / D), x = (int)(e % D);
+        z[e] = (double)hist[(size_t)idx[c] * D + x];
+    }
+}
+
+// pairs for the assignment batch: p = n*k + c -> (n, c)
+__global__ void km_pairs_kernel(int N, int k, int32_t* __restrict__ pairs) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < (int64_t)N * k;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        pairs[2 * p] = (int32_t)(p / k);
+        pairs[2 * p + 1] = (int32_t)(p % k);
+    }
+}
+
+// pairs for the centroid batch: p = n -> (owner[n], n)   (owner NULL: (0, n))
+__global__ void owner_pairs_kernel(const int32_t* __restrict__ owner, int N, int32_t* __restrict__ pairs) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+        pairs[2 * p] = owner ? owner[p] : 0;
+        pairs[2 * p + 1] = p;
+    }
+}
+
+// ---------------------------------------------------------------------------
+cudaError_t outer_bary_init_uniform(double* z, const uint32_t* mass, int N, int d, cudaStream_t s) {
+    bary_init_uniform_kernel<<<1, 1024, 0, s>>>(z, mass, N, d);
+    return cudaGetLastError();
+}
+cudaError_t outer_measure_mass(const double* z, int k, int d, double* out, cudaStream_t s) {
+    measure_mass_kernel<<<k, 512, 0, s>>>(z, d, out);
+    return cudaGetLastError();
+}
+cudaError_t outer_bary_step(double* z, const double* zmass, const double* f, const double* g, const int32_t* owner,
+                            int N, int k, int d, double gamma, double lambda, cudaStream_t s) {
+    int64_t tot = (int64_t)k * d * d;
+    int blocks = (int)((tot + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    bary_step_kernel<<<blocks, 256, 0, s>>>(z, zmass, f, g, owner, N, k, d, gamma, lambda);
+    return cudaGetLastError();
+}
+cudaError_t outer_mean(const double* cost, int N, double* out, cudaStream_t s) {
+    mean_kernel<<<1, 1024, 0, s>>>(cost, N, out);
+    return cudaGetLastError();
+}
+cudaError_t outer_km_assign(const double* cost, int N, int k, int32_t* assign, double* objective, cudaStream_t s) {
+    km_assign_kernel<<<1, 1024, 0, s>>>(cost, N, k, assign, objective);
+    return cudaGetLastError();
+}
+cudaError_t outer_km_seed(const uint32_t* hist, const int32_t* idx, int k, int d, double* z, cudaStream_t s) {
+    km_seed_kernel<<<152, 256, 0, s>>>(hist, idx, k, d, z);
+    return cudaGetLastError();
+}
+cudaError_t outer_km_pairs(int N, int k, int32_t* pairs, cudaStream_t s) {
+    km_pairs_kernel<<<152, 256, 0, s>>>(N, k, pairs);
+    return cudaGetLastError();
+}
+cudaError_t outer_owner_pairs(const int32_t* owner, int N, int32_t* pairs, cudaStream_t s) {
+    owner_pairs_kernel<<<(N + 255) / 256, 256, 0, s>>>(owner, N, pairs);
+    return cudaGetLastError();
+}

@@ -60,8 +60,10 @@ struct SkWS {
     int *rpa, *rpb, *cpa, *cpb;     // [P][dp+1] row / column pointers of the support lists
     int *cia, *cib;                 // [P][dp*dp] row indices of the column-major support lists
     float* ctab;                    // [2*dp] hi / lo FP32 split of c_m/gamma, m = 0..dp-1
-    // inputs
+    // inputs: integer histograms (histA/massA, histB/massB) or, when wA / wB is
+    // non-NULL, real-valued weights [N][d*d] for that side (its mass is their sum)
     const uint32_t *histA, *histB, *massA, *massB;
+    const double *wA, *wB;
     const int32_t* pairs;
 };
 
@@ -75,6 +77,7 @@ struct SkRun {
     double tau;
     int absorb_every;
     double rel_thresh;   // relevance threshold (log) for the intermediate fits
+    int pot_support_only; // finalize: potentials on the supports and Delta only
 };
 
 cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s);
@@ -85,6 +88,17 @@ cudaError_t sk_launch_lse_iter(const SkWS& w, SkRun r, int n_inner, int* active_
 cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count,
                                cudaStream_t s);
 cudaError_t sk_launch_lse_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
-                                   double* g, int32_t* iters, float* err, int32_t* status, cudaStream_t s);
+                                   double* g, int32_t* iters, float* err, int32_t* status, int pot_support_only,
+                                   cudaStream_t s);
+// outer loops (outer.cu)
+cudaError_t outer_bary_init_uniform(double* z, const uint32_t* mass, int N, int d, cudaStream_t s);
+cudaError_t outer_measure_mass(const double* z, int k, int d, double* out, cudaStream_t s);
+cudaError_t outer_bary_step(double* z, const double* zmass, const double* f, const double* g, const int32_t* owner,
+                            int N, int k, int d, double gamma, double lambda, cudaStream_t s);
+cudaError_t outer_mean(const double* cost, int N, double* out, cudaStream_t s);
+cudaError_t outer_km_assign(const double* cost, int N, int k, int32_t* assign, double* objective, cudaStream_t s);
+cudaError_t outer_km_seed(const uint32_t* hist, const int32_t* idx, int k, int d, double* z, cudaStream_t s);
+cudaError_t outer_km_pairs(int N, int k, int32_t* pairs, cudaStream_t s);
+cudaError_t outer_owner_pairs(const int32_t* owner, int N, int32_t* pairs, cudaStream_t s);
 cudaError_t sk_launch_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
                                double* g, int32_t* iters, float* err, int32_t* status, cudaStream_t s);

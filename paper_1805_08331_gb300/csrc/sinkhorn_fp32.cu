@@ -133,32 +133,40 @@ __device__ void build_lists(const float* m, int d, int dp, int* list, int* rowpt
 
 __global__ void __launch_bounds__(T_CTA) sk_setup_kernel(SkWS w, const double* __restrict__ g_init) {
     __shared__ int sh[64];
+    __shared__ double shd[32];
     const int p = blockIdx.x, t = threadIdx.x;
     PairPtrs q = pair_ptrs(w, p);
     const int d = w.d, dp = w.dp;
     int ia = w.pairs ? w.pairs[2 * p] : p, ib = w.pairs ? w.pairs[2 * p + 1] : p;
-    const uint32_t* hA = w.histA + (size_t)ia * d * d;
-    const uint32_t* hB = w.histB + (size_t)ib * d * d;
-    unsigned long long sA = 0, sB = 0;
+    const uint32_t* hA = w.histA ? w.histA + (size_t)ia * d * d : nullptr;
+    const uint32_t* hB = w.histB ? w.histB + (size_t)ib * d * d : nullptr;
+    const double* rA = w.wA ? w.wA + (size_t)ia * d * d : nullptr;
+    const double* rB = w.wB ? w.wB + (size_t)ib * d * d : nullptr;
+    double sA = 0, sB = 0;
     for (int c = t; c < dp * dp; c += blockDim.x) {
         int i = c / dp, j = c % dp;
-        float va = 0.f, vb = 0.f;
-        if (i < d && j < d) { va = (float)hA[i * d + j]; vb = (float)hB[i * d + j]; sA += hA[i * d + j]; sB += hB[i * d + j]; }
-        q.am[c] = va; q.bm[c] = vb; q.ut[c] = 0.f; q.vt[c] = 0.f;
-        q.la[c] = va > 0.f ? log((double)va) : -INFINITY;
-        q.lb[c] = vb > 0.f ? log((double)vb) : -INFINITY;
+        double va = 0.0, vb = 0.0;
+        if (i < d && j < d) {
+            va = rA ? rA[i * d + j] : (double)hA[i * d + j];
+            vb = rB ? rB[i * d + j] : (double)hB[i * d + j];
+            if (!(va >= 0.0)) va = 0.0;   // negative / NaN weights are treated as 0 (validated on the host)
+            if (!(vb >= 0.0)) vb = 0.0;
+            sA += va; sB += vb;
+        }
+        q.am[c] = (float)va; q.bm[c] = (float)vb; q.ut[c] = 0.f; q.vt[c] = 0.f;
+        q.la[c] = va > 0.0 ? log(va) : -INFINITY;
+        q.lb[c] = vb > 0.0 ? log(vb) : -INFINITY;
     }
-    __shared__ unsigned long long shl[32];
-    sA = block_sum(sA, shl);
-    sB = block_sum(sB, shl);
+    sA = block_sum(sA, shd);
+    sB = block_sum(sB, shd);
     __syncthreads();
     build_lists(q.am, d, dp, q.sa, q.rpa, q.cpa, q.cia, &q.ic[IC_NA], sh);
     build_lists(q.bm, d, dp, q.sb, q.rpb, q.cpb, q.cib, &q.ic[IC_NB], sh);
-    const double nA = (double)w.massA[ia], nB = (double)w.massB[ib];
+    const double nA = rA ? sA : (double)w.massA[ia], nB = rB ? sB : (double)w.massB[ib];
     for (int x = t; x < w.n; x += blockDim.x) { q.phi[x] = 0.0; q.psi[x] = 0.0; }
     __syncthreads();
     if (g_init) {
-        const double* gi = g_init + (size_t)p * w.n;
+        const double* gi = g_init + (size_t)p * (d * d + 1);
         for (int c = t; c < d * d; c += blockDim.x) {
             int i = c / d, j = c % d;
             q.psi[i * dp + j] = gi[c] / w.gamma;   // psi stored at padded index for grid cells
@@ -170,11 +178,12 @@ __global__ void __launch_bounds__(T_CTA) sk_setup_kernel(SkWS w, const double* _
         q.sc[SC_AD] = nB; q.sc[SC_BD] = nA; q.sc[SC_TOTAL] = nA + nB; q.sc[SC_ERR] = INFINITY;
         q.ic[IC_ITERS] = 0; q.ic[IC_ABSORB] = 1; q.ic[IC_FROMLIN] = 0; q.ic[IC_RANGE] = 0; q.ic[IC_BIG] = 0;
         int st = ST_ACTIVE;
-        if ((double)sA != nA || (double)sB != nB) st = ST_INVALID;
+        if ((!rA && sA != nA) || (!rB && sB != nB)) st = ST_INVALID;
         else if (nA + nB == 0) { st = ST_CONVERGED; q.sc[SC_ERR] = 0; }
         q.ic[IC_STATUS] = st;
     }
 }
+
 // phi/psi address grid cells by the padded index i*dp + j and hold dp*dp + 1
 // entries (w.n = dp*dp + 1); the Delta entry is index n - 1.
 

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_finalize_kernel(SkWS w, double* 
                                                                 double* __restrict__ fo, double* __restrict__ go,
                                                                 int32_t* __restrict__ iters_o,
                                                                 float* __restrict__ err_o,
-                                                                int32_t* __restrict__ status_o) {
+                                                                int32_t* __restrict__ status_o, int pso) {
     __shared__ int rows[256], cols[256], nrc[2];
     __shared__ double shd[32];
     const int p = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
@@ -331,10 +331,11 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_finalize_kernel(SkWS w, double* 
     // per output cell (all grid cells when f is requested, else the a-support)
     const df hDb = df_from(lBD + psiD);
     double cs = 0.0, rowD = 0.0;
-    const int nx = fo ? d * d : na;
+    const bool allx = fo && !pso;
+    const int nx = allx ? d * d : na;
     for (int e = wid; e < nx; e += nw) {
         int i, j;
-        if (fo) { i = e / d; j = e % d; } else { int c = q.sa[e]; i = c / dp; j = c % dp; }
+        if (allx) { i = e / d; j = e % d; } else { int c = q.sa[e]; i = c / dp; j = c % dp; }
         const int c = i * dp + j, mmD = abs(j - i);
         // -log (K v)_x  (phi' of the final v)
         double phip = lse_stage2_cell(ua, chi, clo, i, j, d, dp, rows, nr, hDb, chi2[mmD], clo2[mmD]);
@@ -368,12 +369,12 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_finalize_kernel(SkWS w, double* 
                 rowD += exp(lu + lBD + psiD - cd / gamma);
                 if (row_marg) row_marg[(size_t)p * n_out + i * d + j] = (float)exp(lu - phip);
             }
-        } else if (lane == 0 && row_marg && fo) {
+        } else if (lane == 0 && row_marg && allx) {
             row_marg[(size_t)p * n_out + i * d + j] = 0.f;
         }
         if (lane == 0 && fo) fo[(size_t)p * n_out + i * d + j] = gamma * (ina ? q.phi[c] : phip);
     }
-    if (row_marg && !fo) {
+    if (row_marg && !allx) {
         for (int x = t; x < d * d; x += blockDim.x) {
             int c = (x / d) * dp + x % d;
             if (!(q.am[c] > 0.f)) row_marg[(size_t)p * n_out + x] = 0.f;
@@ -415,7 +416,7 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_finalize_kernel(SkWS w, double* 
         for (int e = wid; e < d * d; e += nw) {
             const int k = e / d, l = e % d, c = k * dp + l, mmD = abs(l - k);
             const bool inb = q.bm[c] > 0.f;
-            if (!inb && !go) continue;
+            if (!inb && (!go || pso)) continue;
             double psip = lse_stage2_cell(va, chi, clo, k, l, d, dp, rows, nr2, hDa, chi2[mmD], clo2[mmD]);
             if (lane == 0) {
                 if (col_marg) col_marg[(size_t)p * n_out + e] = inb ? (float)exp(q.lb[c] + q.psi[c] - psip) : 0.f;
@@ -434,9 +435,9 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_finalize_kernel(SkWS w, double* 
 }
 
 cudaError_t sk_launch_lse_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
-                                   double* g, int32_t* iters, float* err, int32_t* status, cudaStream_t s) {
+                                   double* g, int32_t* iters, float* err, int32_t* status, int pso, cudaStream_t s) {
     if (w.P == 0) return cudaSuccess;
-    sk_lse_finalize_kernel<<<w.P, T_CTA, 0, s>>>(w, cost, row_marg, col_marg, f, g, iters, err, status);
+    sk_lse_finalize_kernel<<<w.P, T_CTA, 0, s>>>(w, cost, row_marg, col_marg, f, g, iters, err, status, pso);
     return cudaGetLastError();
 }
 
