@@ -239,10 +239,21 @@ static pd_status ensure_buffer(pd_ctx* c, void** buf, size_t* have, size_t need,
 // The PD_FP32 (log-domain) solve of the pairs described by w, on stream s:
 // set-up, iteration rounds until every pair stops, finalize.  Synchronises s
 // once per round (convergence check).
+static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* row_marg, float* col_marg,
+                             double* f, double* g, int32_t* iters, float* err, int32_t* status, int* counter,
+                             cudaStream_t s);
 static pd_status lse_solve(pd_ctx* c, SkWS& w, SkRun r, const double* g_init, double* cost, float* row_marg,
                            float* col_marg, double* f, double* g, int32_t* iters, float* err, int32_t* status,
                            int* counter, cudaStream_t s) {
     { ProfScope ps(c, PD_K_SETUP, s); CUDA_TRY(c, sk_launch_setup(w, g_init, s)); }
+    return lse_iterate(c, w, r, cost, row_marg, col_marg, f, g, iters, err, status, counter, s);
+}
+
+// Iteration rounds of the log-domain engine from the current potentials until
+// every pair stops, then finalize.
+static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* row_marg, float* col_marg,
+                             double* f, double* g, int32_t* iters, float* err, int32_t* status, int* counter,
+                             cudaStream_t s) {
     const int n_inner = 64;
     const int max_rounds = r.max_iter / n_inner + 2;
     bool any_big = true;
@@ -276,8 +287,10 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     if (!(prm->gamma > 0) || !std::isfinite(prm->gamma)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: gamma must be > 0");
     if (prm->max_iter < 1) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: max_iter must be >= 1");
     if (!(prm->tol >= 0)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: tol must be >= 0");
-    if (prm->precision != PD_FP32 && prm->precision != PD_FP32_DENSE)
+    if (prm->precision != PD_FP32 && prm->precision != PD_FP32_DENSE && prm->precision != PD_BF16)
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: unknown precision %d", prm->precision);
+    if (prm->precision == PD_BF16 && d > 128)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: PD_BF16 supports d <= 128");
     if (P < 0) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: P < 0");
     if (P == 0) return PD_OK;
     if (!cost || !histA || !histB || !massA || !massB) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: NULL input/cost");
@@ -309,6 +322,36 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         return PD_OK;
     }
     { ProfScope ps(c, PD_K_SETUP, s); CUDA_TRY(c, sk_launch_setup(w, g_init, s)); }
+    if (prm->precision == PD_BF16) {
+        // tensor-core phase to err <= max(tol, 1e-4) when refining, then exact FP32 refinement
+        const bool refine = prm->refine_iters > 0;
+        SkRun rb = r;
+        if (refine) rb.tol = std::max(prm->tol, 1e-4);
+        { ProfScope ps(c, PD_K_LOGSTEP, s); CUDA_TRY(c, sk_launch_logstep(w, rb, s)); }
+        CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), s));
+        const int max_rounds_b = prm->max_iter + 8;
+        for (int round = 0; round < max_rounds_b; ++round) {
+            { ProfScope ps(c, PD_K_ABSORB, s); CUDA_TRY(c, sk_launch_absorb(w, rb, s)); }
+            CUDA_TRY(c, cudaMemsetAsync(counter, 0, sizeof(int), s));
+            { ProfScope ps(c, PD_K_ITER, s);
+              CUDA_TRY(c, sk_launch_iter_bf16(w, rb, rb.absorb_every, counter, c->dflag, s)); }
+            CUDA_TRY(c, cudaMemcpyAsync(c->hflag, counter, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            if (c->hflag[0] == 0) break;
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(c->hflag + 1, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (c->hflag[1]) return fail(c, PD_ERR_TIMEOUT, "pd_sinkhorn_batch: a tensor-core wait timed out");
+        // every pair (including ones that hit the range limit) continues in the exact engine
+        { ProfScope ps(c, PD_K_ABSORB, s); CUDA_TRY(c, sk_launch_refine_prep(w, s)); }
+        SkRun rr = r;
+        rr.tol = prm->tol;
+        if (refine) rr.max_iter = prm->max_iter;   // total count: BF16 phase + refinement, capped at max_iter
+        pd_status st = lse_iterate(c, w, rr, cost, row_marg, col_marg, f, g, iters, err, status, counter, s);
+        if (st != PD_OK) return st;
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        return PD_OK;
+    }
     { ProfScope ps(c, PD_K_LOGSTEP, s); CUDA_TRY(c, sk_launch_logstep(w, r, s)); }
     const int max_rounds = prm->max_iter + 8;
     for (int round = 0; round < max_rounds; ++round) {

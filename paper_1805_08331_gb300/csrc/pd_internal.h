@@ -85,6 +85,9 @@ cudaError_t sk_launch_logstep(const SkWS& w, SkRun r, cudaStream_t s);
 cudaError_t sk_launch_absorb(const SkWS& w, SkRun r, cudaStream_t s);
 cudaError_t sk_launch_iter_fp32(const SkWS& w, SkRun r, int n_inner, int* active_count, cudaStream_t s);
 cudaError_t sk_launch_lse_iter(const SkWS& w, SkRun r, int n_inner, int* active_count, cudaStream_t s);
+cudaError_t sk_launch_iter_bf16(const SkWS& w, SkRun r, int n_inner, int* active_count, int* error_flag,
+                                cudaStream_t s);
+cudaError_t sk_launch_refine_prep(const SkWS& w, cudaStream_t s);
 cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count,
                                cudaStream_t s);
 cudaError_t sk_launch_lse_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,

@@ -20,8 +20,9 @@ def ctx():
     c.close()
 
 
-def _solve(ctx, hA, hB, d, gamma, max_iter, tol, precision=api.PD_FP32, pairs=None, **kw):
-    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=max_iter, tol=tol, precision=precision)
+def _solve(ctx, hA, hB, d, gamma, max_iter, tol, precision=api.PD_FP32, pairs=None, refine_iters=0, **kw):
+    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=max_iter, tol=tol, precision=precision,
+                                       refine_iters=refine_iters)
     out = api.pd_sinkhorn_batch(ctx, hists_to_gpu(hA), dev(masses(hA).view(np.int32)), hists_to_gpu(hB),
                                 dev(masses(hB).view(np.int32)), p, pairs=pairs, **kw)
     torch.cuda.synchronize()
@@ -131,3 +132,29 @@ def test_invalid_params(ctx):
             api.pd_sinkhorn_batch(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), hists_to_gpu(h),
                                   dev(masses(h).view(np.int32)), p)
         assert e.value.status == api.PD_ERR_INVALID
+
+
+# --------------------------------------------------------------------------- tensor-core engine
+@pytest.mark.parametrize("d,gamma,npts", [(32, 1e-2, 20), (64, 5e-3, 80), (100, 1e-3, 200), (128, 1e-3, 300)])
+def test_bf16_refined_matches_oracle(ctx, d, gamma, npts):
+    """PD_BF16: tcgen05 BF16 phase then exact FP32 refinement to tol; the cost
+    must meet the FP32 bar against the converged oracle."""
+    b, t, o = inputs.random_diagrams(6, nmin=npts // 2, nmax=npts, seed=d + 7)
+    h, _ = oracle.rasterize(b, t, o, d)
+    tol = 1e-7 if gamma >= 5e-3 else 1e-6
+    ref = oracle.sinkhorn_pd_batch(d, gamma, h[0::2], h[1::2], 40000, tol)
+    g = _solve(ctx, h[0::2], h[1::2], d, gamma, 40000, tol, precision=api.PD_BF16, refine_iters=1)
+    assert np.all(g["status"] == api.PD_OK), g["status"]
+    rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
+    assert rel.max() <= 5e-6, rel
+
+
+def test_bf16_unrefined_within_bf16_bar(ctx):
+    """Without refinement the BF16 phase alone must land within the 1e-3 BF16 bar."""
+    d, gamma = 32, 1e-2
+    b, t, o = inputs.random_diagrams(4, nmin=20, nmax=40, seed=2)
+    h, _ = oracle.rasterize(b, t, o, d)
+    ref = oracle.sinkhorn_pd_batch(d, gamma, h[0::2], h[1::2], 20000, 1e-6)
+    g = _solve(ctx, h[0::2], h[1::2], d, gamma, 20000, 1e-6, precision=api.PD_BF16, refine_iters=0)
+    rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
+    assert rel.max() <= 1e-3, rel
