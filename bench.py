@@ -353,7 +353,7 @@ def run_ours(args):
         src = f"{pk_kind} sm_max_mhz x 152 SMs x 128 FP32 lanes x 2"
     else:
         peak = mufu_peak_gexp(pk.get("sm_max_mhz", 2070.0))
-        bound, unit, kname = "alu", "Gexp/s", "sk_lse_iter_kernel (log-domain separable Sinkhorn)"
+        bound, unit, kname = "alu", "Gexp/s", "sk_lse2_kernel (on-chip base-2 log-domain separable Sinkhorn)"
         achieved = lse_terms / (iter_ms / 1e3) / 1e9 if iter_ms > 0 else 0.0
         src = f"{pk_kind} sm_max_mhz x 152 SMs x 16 MUFU ex2/clk (one exponential per log-sum-exp term)"
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,

@@ -1,5 +1,6 @@
 // api.cu -- host implementation of the C ABI declared in include/pd_ot.h.
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -35,10 +36,10 @@ struct ProfScope {
         cudaEvent_t e; cudaEventCreate(&e); return e;
     }
     ProfScope(pd_ctx* c_, int k, cudaStream_t s_) : c(c_), kind(k), s(s_) {
-        if (c->prof) { a = get(c); b = get(c); cudaEventRecord(a, s); }
+        if (c && c->prof) { a = get(c); b = get(c); cudaEventRecord(a, s); }
     }
     ~ProfScope() {
-        if (c->prof) { cudaEventRecord(b, s); c->recs.push_back({kind, a, b}); }
+        if (c && c->prof) { cudaEventRecord(b, s); c->recs.push_back({kind, a, b}); }
     }
 };
 
@@ -242,6 +243,62 @@ static pd_status ensure_buffer(pd_ctx* c, void** buf, size_t* have, size_t need,
 static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* row_marg, float* col_marg,
                              double* f, double* g, int32_t* iters, float* err, int32_t* status, int* counter,
                              cudaStream_t s);
+
+// Iteration rounds of the log-domain engine: each round runs up to 64
+// iterations of every active pair in the on-chip kernel (base-2 kernel when
+// gamma allows a grid, else the double-float one), then the FP64 global-memory
+// kernel for the pairs that do not fit on chip or left the base-2 range, until
+// no pair is active.  counter: 3 device ints; hbuf: 3 host ints; c (may be
+// NULL) receives the per-launch profile records.
+static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hbuf, cudaStream_t s) {
+    const int n_inner = 64;
+    const int max_rounds = r.max_iter / n_inner + 2;
+    const int gbits = sk_lse2_grid_bits(w.gamma);
+    size_t smem = 0;
+    cudaError_t e;
+    if (gbits >= 0) {
+        if ((e = cudaMemsetAsync(counter + 2, 0, sizeof(int), s)) != cudaSuccess) return e;
+        if ((e = sk_launch_lse2_need(w, counter + 2, s)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(hbuf + 2, counter + 2, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        smem = (size_t)hbuf[2];
+    }
+    // CTA width of the base-2 kernel: 256 threads while there are several pairs
+    // per SM, wider CTAs (more warps on one pair) once fewer pairs than SMs
+    // remain.  PD_LSE2_THREADS=256|512|1024 fixes it (tuning).
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int fixed_threads = 0;
+    if (const char* ev = std::getenv("PD_LSE2_THREADS")) {
+        const int v = std::atoi(ev);
+        if (v == 256 || v == 512 || v == 1024) fixed_threads = v;
+    }
+    int active = w.P;
+    bool any_big = false;
+    for (int round = 0; round < max_rounds; ++round) {
+        if ((e = cudaMemsetAsync(counter, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
+        {
+            ProfScope ps(c, PD_K_ITER, s);
+            const int threads = fixed_threads ? fixed_threads : (active > 2 * nsm ? 256 : (active > nsm ? 512 : 1024));
+            e = gbits >= 0 ? sk_launch_lse2(w, r, n_inner, counter, counter + 1, smem, gbits, threads, s)
+                           : sk_launch_lse_smem(w, r, n_inner, counter, counter + 1, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (any_big) {
+            ProfScope ps(c, PD_K_ITER, s);
+            if ((e = sk_launch_lse_iter(w, r, n_inner, counter, s)) != cudaSuccess) return e;
+        }
+        if ((e = cudaMemcpyAsync(hbuf, counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        if (hbuf[1] > 0) any_big = true;   // pairs handed to the global-memory kernel (next round on)
+        if (hbuf[0] == 0) break;
+        active = hbuf[0];
+    }
+    return cudaSuccess;
+}
 static pd_status lse_solve(pd_ctx* c, SkWS& w, SkRun r, const double* g_init, double* cost, float* row_marg,
                            float* col_marg, double* f, double* g, int32_t* iters, float* err, int32_t* status,
                            int* counter, cudaStream_t s) {
@@ -254,21 +311,7 @@ static pd_status lse_solve(pd_ctx* c, SkWS& w, SkRun r, const double* g_init, do
 static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* row_marg, float* col_marg,
                              double* f, double* g, int32_t* iters, float* err, int32_t* status, int* counter,
                              cudaStream_t s) {
-    const int n_inner = 64;
-    const int max_rounds = r.max_iter / n_inner + 2;
-    bool any_big = true;
-    for (int round = 0; round < max_rounds; ++round) {
-        CUDA_TRY(c, cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
-        { ProfScope ps(c, PD_K_ITER, s); CUDA_TRY(c, sk_launch_lse_smem(w, r, n_inner, counter, counter + 1, s)); }
-        if (any_big) {   // pairs whose supports do not fit on chip
-            ProfScope ps(c, PD_K_ITER, s);
-            CUDA_TRY(c, sk_launch_lse_iter(w, r, n_inner, counter, s));
-        }
-        CUDA_TRY(c, cudaMemcpyAsync(c->hflag, counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(c, cudaStreamSynchronize(s));
-        if (round == 0) any_big = c->hflag[1] > 0;
-        if (c->hflag[0] == 0) break;
-    }
+    CUDA_TRY(c, lse_rounds(c, w, r, counter, c->hflag, s));
     { ProfScope ps(c, PD_K_FINALIZE, s);
       CUDA_TRY(c, sk_launch_lse_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, r.pot_support_only, s)); }
     return PD_OK;
@@ -601,20 +644,8 @@ extern "C" pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint
     r.absorb_every = 64;
     r.rel_thresh = -21.0;
     if (sk_launch_setup(w, g_init, s) != cudaSuccess) return PD_ERR_CUDA;
-    const int n_inner = 64;
-    const int max_rounds = prm->max_iter / n_inner + 2;
-    int hcount[2] = {0, 0};
-    bool any_big = true;
-    for (int round = 0; round < max_rounds; ++round) {
-        if (cudaMemsetAsync(counter, 0, 2 * sizeof(int), s) != cudaSuccess) return PD_ERR_CUDA;
-        if (sk_launch_lse_smem(w, r, n_inner, counter, counter + 1, s) != cudaSuccess) return PD_ERR_CUDA;
-        if (any_big && sk_launch_lse_iter(w, r, n_inner, counter, s) != cudaSuccess) return PD_ERR_CUDA;
-        if (cudaMemcpyAsync(hcount, counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-            return PD_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return PD_ERR_CUDA;
-        if (round == 0) any_big = hcount[1] > 0;
-        if (hcount[0] == 0) break;
-    }
+    int hcount[3] = {0, 0, 0};
+    if (lse_rounds(nullptr, w, r, counter, hcount, s) != cudaSuccess) return PD_ERR_CUDA;
     if (sk_launch_lse_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, 0, s) != cudaSuccess)
         return PD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return PD_ERR_CUDA;

@@ -90,6 +90,11 @@ cudaError_t sk_launch_iter_bf16(const SkWS& w, SkRun r, int n_inner, int* active
 cudaError_t sk_launch_refine_prep(const SkWS& w, cudaStream_t s);
 cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count,
                                cudaStream_t s);
+// base-2 on-chip iteration kernel (sinkhorn_log2.cu)
+int sk_lse2_grid_bits(double gamma);
+cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, cudaStream_t s);
+cudaError_t sk_launch_lse2(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count, size_t smem,
+                           int gbits, int threads, cudaStream_t s);
 cudaError_t sk_launch_lse_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
                                    double* g, int32_t* iters, float* err, int32_t* status, int pot_support_only,
                                    cudaStream_t s);

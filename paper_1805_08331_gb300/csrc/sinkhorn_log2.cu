@@ -1,0 +1,614 @@
+// sinkhorn_log2.cu -- on-chip log-domain Sinkhorn iterations in base 2 with
+// exactly subtractable arguments (the default iteration kernel).
+//
+// Mathematics: Prop. 1's separable kernel application in the log semiring,
+// restricted to the supports (zero-mass cells carry exp(-inf) = 0):
+//   stage 1: L[k,j]   = LSE_{(k,l) in supp(in)} ( h_kl - c_jl/gamma )
+//   stage 2: out_(i,j) = -LSE( LSE_k ( L[k,j] - c_ik/gamma ), h_D - cD_(i,j)/gamma )
+//   Delta:   out_D     = -LSE( { h_y - cD_y/gamma : y in supp(in) } u { h_D } )
+// with h = log(weight) + potential/gamma of the input side; the u-update
+// (phi from psi) and the v-update (psi from phi) swap the two sides.  The
+// v-update also yields err_t = sum_y w_y |exp(psi_old - psi_new) - 1| / mass,
+// the column-marginal error of the plan after the u-update.
+//
+// Number format.  Every log-value x (log2 units) is a pair (xh, xl): xh is a
+// multiple of 2^-G (G chosen from gamma on the host) and |xl| <= 2^-(G+1).
+// Multiples of 2^-G below 2^(24-G) are exact FP32 numbers, so with the
+// potentials kept below 2^(21-G) every sum or difference of xh words is exact,
+// and an argument h - c is two plain additions (xh - ch exact,
+// xl - cl to ~1e-11) and exp2 applies to it directly; no TwoSum, no FP64 in
+// the loop.  Potentials that leave that range hand their pair to the FP64
+// global-memory kernel.
+//
+// One pass per sum.  Stage 2 and the Delta output are shifted by the previous
+// value of the potential they produce, so near convergence the shifted sum is
+// close to 1 and its log2 is accurate to a few 1e-8 in absolute terms.  A sum
+// outside [2^-100, 2^100] (the first iterations, or any jump) is recomputed
+// with the exact maximum.  Stage 1 keeps (max, sum) un-logged, so a stage-2
+// term is exp2(m - c) * S.
+//
+// Output columns are processed in chunks of 32: stage 1 for the chunk's
+// columns, then stage 2 for the output cells in them, so the stage-1 buffer
+// is (non-empty input rows) x 32 whatever the output support; several pairs
+// fit on one SM.
+#include "sk_common.cuh"
+#include <cmath>
+
+#define L2_CW 32          // output columns per chunk
+#define L2_MAXCH 8        // chunks per side (d <= 256)
+#define L2_MAXW 32        // warps per CTA at most
+
+// Dynamic shared memory of the kernel; the per-side arrays are addressed by
+// 32-bit byte offsets into it (shared-memory addressing, one register each).
+extern __shared__ __align__(16) unsigned char l2_sm[];
+template <typename T>
+__device__ __forceinline__ T* smp(uint32_t off) { return reinterpret_cast<T*>(l2_sm + off); }
+
+struct L2Side {
+    int n, nr, nc, nch;
+    uint32_t lw;      // float2 [n] log2 weight (hi, lo)
+    uint32_t pot;     // float2 [n] potential/gamma in log2 units (hi, lo)
+    uint32_t hin;     // float2 [n] lw + pot, the side's h when it is the input
+    uint32_t w;       // float  [n] weight (marginal error)
+    uint32_t rp;      // int    [d+1] row pointers into the support (row-major)
+    uint32_t row;     // short  [n]
+    uint32_t col;     // short  [n]
+    uint32_t chl;     // short  [n] support entries grouped by output chunk, row-major inside a chunk
+    uint32_t rows;    // short  [nr] non-empty rows
+    uint32_t cols;    // short  [nc] non-empty columns
+    uint32_t colpos;  // short  [d] position of a column in cols, -1 if empty
+    short chs[L2_MAXCH + 1];   // chunk starts in chl
+    float2 lwD, potD, hinD;
+    float wD;
+};
+
+__host__ __device__ __forceinline__ size_t l2_al(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Shared-memory bytes of a pair (the host sizes the launch with the maximum).
+__device__ __forceinline__ size_t l2_need(int nA, int nB, int nrA, int nrB, int d) {
+    size_t b = 0;
+    const int ns[2] = {nA, nB};
+    for (int s = 0; s < 2; ++s) {
+        const size_t n = (size_t)ns[s];
+        b += l2_al(24 * n) + l2_al(4 * n) + l2_al(4 * (size_t)(d + 1)) + l2_al(6 * n) + l2_al(6 * (size_t)d);
+    }
+    b += l2_al(8 * (size_t)(2 * d - 1)) + l2_al(8 * (size_t)d);
+    const size_t nr = (size_t)(nrA > nrB ? nrA : nrB);
+    b += l2_al(8 * (size_t)L2_CW * nr);
+    return b;
+}
+
+// (hi, lo) split of an FP64 value on the 2^-G grid (gsc = 2^G).
+__device__ __forceinline__ float2 l2_split(double x, double gsc) {
+    if (!isfinite(x)) return make_float2((float)x, 0.f);
+    const double h = rint(x * gsc) / gsc;
+    return make_float2((float)h, (float)(x - h));
+}
+__device__ __forceinline__ float l2_round(float x, float gsc, float ginv) { return rintf(x * gsc) * ginv; }
+
+// tot (normal, > 0) = 2^e * m with m in [0.75, 1.5); returns e and log2(m).
+__device__ __forceinline__ float l2_log2(float tot, int& e) {
+    const int b = __float_as_int(tot);
+    e = ((b >> 23) & 0xff) - 127;
+    float m = __int_as_float((b & 0x007fffff) | 0x3f800000);
+    if (m >= 1.5f) { m *= 0.5f; e += 1; }
+    return log2f(m);
+}
+
+// 2^x with the special-function unit (relative error below 1.5e-7 on the
+// normal range, measured against FP64 exp2; results below 2^-126 flush to 0).
+__device__ __forceinline__ float l2_ex2(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Non-empty rows (or columns) of a CSR pointer array, in increasing order;
+// pos[i] = index in out or -1.  Needs blockDim.x >= d.
+static __device__ void l2_compact(const int* __restrict__ ptr, int d, short* out, int* count, short* pos,
+                                  int* warp_cnt) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int i = threadIdx.x;
+    const bool f = (i < d) && (ptr[i + 1] > ptr[i]);
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_cnt[wid] = __popc(bal);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int q = 0; q < nw; ++q) { if (q < wid) off += warp_cnt[q]; tot += warp_cnt[q]; }
+    const int idx = off + __popc(bal & ((1u << lane) - 1u));
+    if (i < d) {
+        if (f && out) out[idx] = (short)i;
+        if (pos) pos[i] = f ? (short)idx : (short)-1;
+    }
+    if (threadIdx.x == 0) *count = tot;
+    __syncthreads();
+}
+
+// Group the output cells of a side by chunk of 32 non-empty columns (warp c
+// builds chunk c; the order inside a chunk stays row-major).
+static __device__ void l2_chunks(L2Side& s, int* warp_cnt) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nch = s.nch, n = s.n;
+    const short* col = smp<short>(s.col);
+    const short* colpos = smp<short>(s.colpos);
+    short* chl = smp<short>(s.chl);
+    if (wid < nch) {
+        int cnt = 0;
+        for (int b = 0; b < n; b += 32) {
+            const int e = b + lane;
+            const bool f = e < n && (colpos[col[e]] >> 5) == wid;
+            cnt += __popc(__ballot_sync(0xffffffffu, f));
+        }
+        if (lane == 0) warp_cnt[wid] = cnt;
+    }
+    __syncthreads();
+    if (wid < nch) {
+        int off = 0;
+        for (int q = 0; q < wid; ++q) off += warp_cnt[q];
+        if (lane == 0) s.chs[wid] = (short)off;
+        if (wid == nch - 1 && lane == 0) s.chs[nch] = (short)(off + warp_cnt[wid]);
+        for (int b = 0; b < n; b += 32) {
+            const int e = b + lane;
+            const bool f = e < n && (colpos[col[e]] >> 5) == wid;
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (f) chl[off + __popc(bal & ((1u << lane) - 1u))] = (short)e;
+            off += __popc(bal);
+        }
+    }
+    if (nch == 0 && threadIdx.x == 0) s.chs[0] = 0;
+    __syncthreads();
+}
+
+struct L2Consts {
+    uint32_t ct;     // float2 [2d-1] c_m/gamma in log2 units (hi, lo), m = (i - k) + d - 1
+    uint32_t cdt;    // float2 [d] cD_m/gamma in log2 units, m = |j - i|
+    uint32_t L1;     // float2 [nr][32] stage-1 (max, sum), swizzled columns
+    int d;
+    float gsc, ginv, lim;
+};
+
+// Lanes per output cell in stage 2 (NT / 4 cells per pass).  Wider groups
+// measured slower: the per-cell epilogue runs on one lane of the group.
+template <int NT> struct L2Lanes { static constexpr int G = 4; static constexpr int SW = 16 / G; };
+
+// Stage-1 buffer index (float2 units): row r, chunk column cc.  Stage 2 reads
+// rows r = g + G u together (g = lane in the cell's group); XOR-ing the column
+// with g * SW puts those G reads in distinct 8-byte bank slots of a wavefront.
+template <int NT>
+__device__ __forceinline__ int l2_lidx(int r, int cc) {
+    return r * L2_CW + (cc ^ ((r & (L2Lanes<NT>::G - 1)) * L2Lanes<NT>::SW));
+}
+
+// New potential -(shift + log2 tot) as a (grid, rest) pair; err term
+// w |exp(old - new) - 1| added when want_err.  Returns false if out of range.
+__device__ __forceinline__ bool l2_update(float tot, float shift, float Ms, float2 po, float wgt, bool want_err,
+                                          const L2Consts& K, float& errs, float2& pn) {
+    if (!(tot > 0.f && isfinite(tot) && isfinite(shift))) return false;
+    int ex;
+    const float l = l2_log2(tot, ex);
+    const float lr = l2_round(l, K.gsc, K.ginv);
+    pn = make_float2(-((shift + (float)ex) + lr), -(l - lr));
+    if (want_err) {
+        // old - new = po.y + log2(tot) (+ po.x + shift, zero unless the exact path ran)
+        const float ev = (shift == Ms) ? (tot - 1.f) + tot * expm1f(po.y * 0.69314718f)
+                                       : tot * exp2f((po.x + shift) + po.y) - 1.f;
+        errs += wgt * fabsf(ev);
+    }
+    return fabsf(pn.x) < K.lim;
+}
+
+// One half-step: out.pot <- -LSE over the input side.  Adds the marginal-error
+// terms of `out` to errs when want_err.  Sets *range_flag if a potential left
+// the exact range (the pair then moves to the FP64 kernel).
+template <int NT>
+static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool want_err, float& errs,
+                               float* redD, int* range_flag) {
+    constexpr int NW = NT / 32;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int d = K.d;
+    const int in_n = in.n, in_nr = in.nr;
+    const float2* in_hin = smp<float2>(in.hin);
+    const short* in_row = smp<short>(in.row);
+    const short* in_col = smp<short>(in.col);
+    const short* in_rows = smp<short>(in.rows);
+    const int* in_rp = smp<int>(in.rp);
+    const float2* ct = smp<float2>(K.ct);
+    const float2* cdt = smp<float2>(K.cdt);
+    float2* L1 = smp<float2>(K.L1);
+    // ---- Delta output, shifted by its previous value
+    const bool doD = out.wD > 0.f;
+    const float MsD = -out.potD.x;
+    {
+        float sD = 0.f;
+        if (doD) {
+            for (int q = t; q < in_n; q += NT) {
+                const float2 h = in_hin[q];
+                const float2 c = cdt[abs((int)in_col[q] - (int)in_row[q])];
+                sD += l2_ex2(((h.x - c.x) - MsD) + (h.y - c.y));
+            }
+        }
+        sD = warp_sum(sD);
+        if (lane == 0) redD[wid] = sD;
+    }
+    __syncthreads();
+    if (t == 0 && doD) {
+        float tot = 0.f;
+        for (int q = 0; q < NW; ++q) tot += redD[q];
+        const float2 hD = in.hinD;
+        if (hD.x > -INFINITY) tot += exp2f((hD.x - MsD) + hD.y);
+        float shift = MsD;
+        if (!(tot >= 0x1p-100f && tot <= 0x1p100f)) {
+            float mx = hD.x;
+            for (int q = 0; q < in_n; ++q)
+                mx = fmaxf(mx, in_hin[q].x - cdt[abs((int)in_col[q] - (int)in_row[q])].x);
+            shift = mx;
+            tot = (hD.x > -INFINITY) ? exp2f((hD.x - shift) + hD.y) : 0.f;
+            for (int q = 0; q < in_n; ++q) {
+                const float2 h = in_hin[q];
+                const float2 c = cdt[abs((int)in_col[q] - (int)in_row[q])];
+                tot += exp2f(((h.x - c.x) - shift) + (h.y - c.y));
+            }
+        }
+        float2 pn;
+        if (l2_update(tot, shift, MsD, out.potD, out.wD, want_err, K, errs, pn)) {
+            out.potD = pn;
+            out.hinD = make_float2(out.lwD.x + pn.x, out.lwD.y + pn.y);
+        } else {
+            atomicOr(range_flag, 1);
+        }
+    }
+    const float2 hD = in.hinD;   // input Delta term (not written in this half-step)
+    constexpr int L2_G = L2Lanes<NT>::G;
+    const unsigned gmask = ((1u << L2_G) - 1u) << (lane & ~(L2_G - 1));
+    const int g = lane & (L2_G - 1);
+    const int out_nch = out.nch, out_nc = out.nc;
+    const short* out_cols = smp<short>(out.cols);
+    for (int ch = 0; ch < out_nch; ++ch) {
+        const int c0 = ch * L2_CW;
+        const int wc = min(L2_CW, out_nc - c0);
+        // ---- stage 1 for the chunk's columns: element (r, cc), r over non-empty input rows
+        {
+            int r = t / wc, cc = t - r * wc;
+            const int dr = NT / wc, dc = NT - dr * wc;
+            while (r < in_nr) {
+                const int k = in_rows[r];
+                const int j = out_cols[c0 + cc];
+                const int q0 = in_rp[k], q1 = in_rp[k + 1];
+                const float2* ctj = ct + (j + d - 1);
+                // online log-sum-exp over the row's cells: (m, S) with value m + log2 S
+                float2 h = in_hin[q0];
+                float2 c = ctj[-(int)in_col[q0]];
+                float m = h.x - c.x;
+                float S = l2_ex2(h.y - c.y);
+                for (int qq = q0 + 1; qq < q1; ++qq) {
+                    h = in_hin[qq];
+                    c = ctj[-(int)in_col[qq]];
+                    const float a = h.x - c.x;
+                    const float mn = fmaxf(m, a);
+                    S = fmaf(S, l2_ex2(m - mn), l2_ex2((a - mn) + (h.y - c.y)));
+                    m = mn;
+                }
+                L1[l2_lidx<NT>(r, cc)] = make_float2(m, S);
+                r += dr; cc += dc;
+                if (cc >= wc) { cc -= wc; ++r; }
+            }
+        }
+        __syncthreads();
+        // ---- stage 2 for the chunk's output cells, L2_G lanes per cell
+        {
+            const int cs = out.chs[ch], ce = out.chs[ch + 1];
+            const short* out_chl = smp<short>(out.chl);
+            const short* out_row = smp<short>(out.row);
+            const short* out_col = smp<short>(out.col);
+            const short* out_colpos = smp<short>(out.colpos);
+            float2* out_pot = smp<float2>(out.pot);
+            // every lane of a group runs the same trip count (the loop index is shared)
+            for (int e0 = cs; e0 < ce; e0 += NT / L2_G) {
+                const int e = e0 + (t / L2_G);
+                const bool live = e < ce;
+                int i = 0, j = 0, ccs = 0, qo = 0;
+                float2 po = make_float2(0.f, 0.f);
+                if (live) {
+                    qo = out_chl[e];
+                    i = out_row[qo]; j = out_col[qo];
+                    ccs = (out_colpos[j] - c0) ^ (g * L2Lanes<NT>::SW);   // rows r = g + G u
+                    po = out_pot[qo];
+                }
+                const float Ms = -po.x;
+                const float2* cti = ct + (i + d - 1);
+                float tot = 0.f;
+                if (live) {
+                    // two interleaved compensated sums (rows g + 2Gu and g + G + 2Gu)
+                    float s0 = 0.f, c0s = 0.f, s1 = 0.f, c1s = 0.f;
+                    int r2 = g;
+                    for (; r2 + L2_G < in_nr; r2 += 2 * L2_G) {
+                        const int ka = in_rows[r2], kb = in_rows[r2 + L2_G];
+                        const float2 La = L1[r2 * L2_CW + ccs], Lb = L1[(r2 + L2_G) * L2_CW + ccs];
+                        const float2 ca = cti[-ka], cb = cti[-kb];
+                        kahan_add(s0, c0s, l2_ex2(((La.x - ca.x) - Ms) - ca.y) * La.y);
+                        kahan_add(s1, c1s, l2_ex2(((Lb.x - cb.x) - Ms) - cb.y) * Lb.y);
+                    }
+                    if (r2 < in_nr) {
+                        const int ka = in_rows[r2];
+                        const float2 ca = cti[-ka];
+                        const float2 La = L1[r2 * L2_CW + ccs];
+                        kahan_add(s0, c0s, l2_ex2(((La.x - ca.x) - Ms) - ca.y) * La.y);
+                    }
+                    if (g == 0 && hD.x > -INFINITY) {
+                        const float2 c = cdt[abs(j - i)];
+                        kahan_add(s1, c1s, l2_ex2(((hD.x - c.x) - Ms) + (hD.y - c.y)));
+                    }
+                    tot = (s0 - c0s) + (s1 - c1s);
+                }
+#pragma unroll
+                for (int o = 1; o < L2_G; o <<= 1) tot += __shfl_xor_sync(gmask, tot, o);
+                float shift = Ms;
+                if (live && !(tot >= 0x1p-100f && tot <= 0x1p100f)) {
+                    // exact maximum of the group's terms; S_k <= 256 so shift = max + 8 bounds every term by 1
+                    float mx = -INFINITY;
+                    for (int r3 = g; r3 < in_nr; r3 += L2_G)
+                        mx = fmaxf(mx, L1[r3 * L2_CW + ccs].x - cti[-(int)in_rows[r3]].x);
+                    if (g == 0 && hD.x > -INFINITY) mx = fmaxf(mx, hD.x - cdt[abs(j - i)].x);
+#pragma unroll
+                    for (int o = 1; o < L2_G; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(gmask, mx, o));
+                    shift = mx + 8.f;
+                    float s = 0.f, cmp = 0.f;
+                    for (int r3 = g; r3 < in_nr; r3 += L2_G) {
+                        const float2 c = cti[-(int)in_rows[r3]];
+                        const float2 La = L1[r3 * L2_CW + ccs];
+                        kahan_add(s, cmp, l2_ex2(((La.x - c.x) - shift) - c.y) * La.y);
+                    }
+                    if (g == 0 && hD.x > -INFINITY) {
+                        const float2 c = cdt[abs(j - i)];
+                        kahan_add(s, cmp, l2_ex2(((hD.x - c.x) - shift) + (hD.y - c.y)));
+                    }
+                    tot = s - cmp;
+#pragma unroll
+                    for (int o = 1; o < L2_G; o <<= 1) tot += __shfl_xor_sync(gmask, tot, o);
+                }
+                if (live && g == 0) {
+                    float2 pn;
+                    if (l2_update(tot, shift, Ms, po, smp<float>(out.w)[qo], want_err, K, errs, pn)) {
+                        out_pot[qo] = pn;
+                        const float2 lw = smp<float2>(out.lw)[qo];
+                        smp<float2>(out.hin)[qo] = make_float2(lw.x + pn.x, lw.y + pn.y);
+                    } else {
+                        atomicOr(range_flag, 1);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (out_nch == 0) __syncthreads();
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 3 : (NT <= 512 ? 2 : 1)))
+sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int smem_cap, int* big_count, int gbits) {
+    constexpr int NW = NT / 32;
+    __shared__ L2Side S[2];
+    __shared__ float redD[NW], redE[NW];
+    __shared__ int wcnt[NW];
+    __shared__ int cnt[4];
+    __shared__ int range_flag, fits;
+    const int p = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    PairPtrs q = pair_ptrs(w, p);
+    if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG]) return;
+    const int d = w.d, dp = w.dp, nA = q.ic[IC_NA], nB = q.ic[IC_NB];
+    l2_compact(q.rpa, d, nullptr, &cnt[0], nullptr, wcnt);
+    l2_compact(q.rpb, d, nullptr, &cnt[1], nullptr, wcnt);
+    const int nrA = cnt[0], nrB = cnt[1];
+    if (t == 0) fits = l2_need(nA, nB, nrA, nrB, d) <= (size_t)smem_cap;
+    __syncthreads();
+    if (!fits) {
+        if (t == 0) { q.ic[IC_BIG] = 1; atomicAdd(big_count, 1); }
+        return;
+    }
+    // ---- carve shared memory (byte offsets)
+    uint32_t sp = 0;
+    auto take = [&](size_t bytes) { const uint32_t r0 = sp; sp += (uint32_t)l2_al(bytes); return r0; };
+    const int ns[2] = {nA, nB};
+    for (int s = 0; s < 2; ++s) {
+        const int n = ns[s];
+        const uint32_t o_lw = take(24 * (size_t)n), o_w = take(4 * (size_t)n), o_rp = take(4 * (size_t)(d + 1));
+        const uint32_t o_row = take(6 * (size_t)n), o_rows = take(6 * (size_t)d);
+        if (t == 0) {
+            L2Side& X = S[s];
+            X.n = n;
+            X.lw = o_lw; X.pot = o_lw + 8 * n; X.hin = o_lw + 16 * n;
+            X.w = o_w; X.rp = o_rp;
+            X.row = o_row; X.col = o_row + 2 * n; X.chl = o_row + 4 * n;
+            X.rows = o_rows; X.cols = o_rows + 2 * d; X.colpos = o_rows + 4 * d;
+        }
+    }
+    L2Consts K;
+    K.ct = take(8 * (size_t)(2 * d - 1));
+    K.cdt = take(8 * (size_t)d);
+    const int nrmax = nrA > nrB ? nrA : nrB;
+    K.L1 = take(8 * (size_t)L2_CW * nrmax);
+    __syncthreads();
+    // ---- load
+    const double gsc = ldexp(1.0, gbits);
+    const double LOG2E = 1.4426950408889634;
+    {
+        const int* lists[2] = {q.sa, q.sb};
+        const double* lw[2] = {q.la, q.lb};
+        const double* pot[2] = {q.phi, q.psi};
+        const float* wt[2] = {q.am, q.bm};
+        const int* rps[2] = {q.rpa, q.rpb};
+        const int* cps[2] = {q.cpa, q.cpb};
+        for (int s = 0; s < 2; ++s) {
+            L2Side& X = S[s];
+            const int n = X.n;
+            short* row = smp<short>(X.row);
+            short* col = smp<short>(X.col);
+            float2* xlw = smp<float2>(X.lw);
+            float2* xpot = smp<float2>(X.pot);
+            float2* xhin = smp<float2>(X.hin);
+            float* xw = smp<float>(X.w);
+            int* xrp = smp<int>(X.rp);
+            for (int e = t; e < n; e += NT) {
+                const int c = lists[s][e];
+                const int i = c / dp, j = c - i * dp;
+                row[e] = (short)i; col[e] = (short)j;
+                const float2 l2 = l2_split(lw[s][c] * LOG2E, gsc);
+                const float2 p2 = l2_split(pot[s][c] * LOG2E, gsc);
+                xlw[e] = l2; xpot[e] = p2;
+                xhin[e] = make_float2(l2.x + p2.x, l2.y + p2.y);
+                xw[e] = wt[s][c];
+            }
+            for (int i = t; i <= d; i += NT) xrp[i] = rps[s][i];
+            l2_compact(rps[s], d, smp<short>(X.rows), &cnt[2], nullptr, wcnt);
+            l2_compact(cps[s], d, smp<short>(X.cols), &cnt[3], smp<short>(X.colpos), wcnt);
+            if (t == 0) {
+                X.nr = cnt[2]; X.nc = cnt[3]; X.nch = (cnt[3] + L2_CW - 1) / L2_CW;
+                const double wD = q.sc[s == 0 ? SC_AD : SC_BD];
+                X.wD = (float)wD;
+                X.lwD = wD > 0 ? l2_split(log(wD) * LOG2E, gsc) : make_float2(-INFINITY, 0.f);
+                X.potD = l2_split(pot[s][w.n - 1] * LOG2E, gsc);
+                X.hinD = wD > 0 ? make_float2(X.lwD.x + X.potD.x, X.lwD.y + X.potD.y) : make_float2(-INFINITY, 0.f);
+            }
+            __syncthreads();
+        }
+    }
+    {
+        const double sc2 = LOG2E / (w.gamma * (double)d * (double)d);
+        float2* ct = smp<float2>(K.ct);
+        float2* cdt = smp<float2>(K.cdt);
+        for (int m = t; m < 2 * d - 1; m += NT) {
+            const double z = (double)(m - (d - 1));
+            ct[m] = l2_split(z * z * sc2, gsc);
+        }
+        for (int m = t; m < d; m += NT) cdt[m] = l2_split(0.5 * (double)m * (double)m * sc2, gsc);
+    }
+    if (t == 0) range_flag = 0;
+    __syncthreads();
+    l2_chunks(S[0], wcnt);
+    l2_chunks(S[1], wcnt);
+    K.d = d;
+    K.gsc = (float)gsc; K.ginv = (float)(1.0 / gsc);
+    K.lim = (float)ldexp(1.0, 21 - gbits);   // |potential| bound keeping every sum of grid words exact
+    const float inv_total = (float)(1.0 / q.sc[SC_TOTAL]);
+    const float tolf = (float)r.tol;
+    int iters = q.ic[IC_ITERS];
+    float errf = (float)q.sc[SC_ERR];
+    int status = ST_ACTIVE;
+    bool moved = false;
+    for (int it = 0; it < n_inner; ++it) {
+        float errs = 0.f;
+        l2_half<NT>(S[1], S[0], K, false, errs, redD, &range_flag);   // u-update: phi from psi
+        errs = 0.f;
+        l2_half<NT>(S[0], S[1], K, true, errs, redD, &range_flag);    // v-update: psi from phi, err_t
+        errs = warp_sum(errs);
+        if (lane == 0) redE[wid] = errs;
+        __syncthreads();
+        float e = 0.f;
+        for (int k = 0; k < NW; ++k) e += redE[k];
+        errf = e * inv_total;
+        ++iters;
+        if (range_flag) { moved = true; break; }
+        if (r.tol > 0 && errf <= tolf) { status = ST_CONVERGED; break; }
+        if (iters >= r.max_iter) { status = ST_MAXITER; break; }
+        if (!isfinite(errf)) { status = ST_RANGE; break; }
+    }
+    // ---- store the potentials (FP64, natural units)
+    const double LN2 = 0.6931471805599453;
+    for (int s = 0; s < 2; ++s) {
+        const L2Side& X = S[s];
+        double* pot = s == 0 ? q.phi : q.psi;
+        const int* list = s == 0 ? q.sa : q.sb;
+        const float2* xpot = smp<float2>(X.pot);
+        for (int e = t; e < X.n; e += NT) pot[list[e]] = ((double)xpot[e].x + (double)xpot[e].y) * LN2;
+        if (t == 0) pot[w.n - 1] = ((double)X.potD.x + (double)X.potD.y) * LN2;
+    }
+    if (t == 0) {
+        q.sc[SC_ERR] = (double)errf;
+        q.ic[IC_ITERS] = iters;
+        if (moved) {
+            // the exact-range guard tripped: the FP64 global-memory kernel takes the pair over
+            q.ic[IC_BIG] = 1;
+            atomicAdd(big_count, 1);
+            atomicAdd(active_count, 1);
+        } else {
+            q.ic[IC_STATUS] = status;
+            if (status == ST_ACTIVE) atomicAdd(active_count, 1);
+        }
+    }
+}
+
+// Maximum shared-memory need over the active on-chip pairs (one thread per pair).
+__global__ void sk_lse2_need_kernel(SkWS w, int* max_need) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.P) return;
+    PairPtrs q = pair_ptrs(w, p);
+    if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG]) return;
+    int nrA = 0, nrB = 0;
+    for (int i = 0; i < w.d; ++i) {
+        nrA += q.rpa[i + 1] > q.rpa[i];
+        nrB += q.rpb[i + 1] > q.rpb[i];
+    }
+    const size_t need = l2_need(q.ic[IC_NA], q.ic[IC_NB], nrA, nrB, w.d);
+    atomicMax(max_need, (int)(need > 0x7fffffff ? 0x7fffffff : need));
+}
+
+cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, cudaStream_t s) {
+    if (w.P == 0) return cudaSuccess;
+    sk_lse2_need_kernel<<<(w.P + 255) / 256, 256, 0, s>>>(w, max_need);
+    return cudaGetLastError();
+}
+
+// Grid exponent G for a gamma.  Multiples of 2^-G below 2^(24-G) are exact in
+// FP32, so a difference of two grid words is exact whenever its result is
+// below that.  Potentials are kept below 2^(21-G) (the kernel's guard) and
+// 2^(23-G) covers eight times the largest cost/gamma in log2 units plus a
+// margin for log-weights, which bounds every argument the kernel forms.
+// Returns -1 when gamma is too small for a grid of at least 2^-4 (the caller
+// then uses the FP64-argument kernels).
+int sk_lse2_grid_bits(double gamma) {
+    const double cmax = 2.0 / gamma * 1.4426950408889634 + 64.0;
+    int e = 0;
+    while (std::ldexp(1.0, e) < 8.0 * cmax) ++e;
+    const int g = 23 - e;
+    return g >= 4 ? (g > 12 ? 12 : g) : -1;
+}
+
+size_t sk_lse2_smem_cap() {
+    int dev = 0, cap = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return (size_t)cap - 1024;   // static shared memory of the kernel
+}
+
+template <int NT>
+static cudaError_t launch_lse2(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count, size_t smem,
+                               int gbits, cudaStream_t s) {
+    static size_t configured = 0;
+    const size_t cap = sk_lse2_smem_cap();
+    if (configured != cap) {
+        cudaError_t e = cudaFuncSetAttribute(sk_lse2_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+        if (e != cudaSuccess) return e;
+        configured = cap;
+    }
+    if (smem > cap) smem = cap;
+    sk_lse2_kernel<NT><<<w.P, NT, smem, s>>>(w, r, n_inner, active_count, (int)smem, big_count, gbits);
+    return cudaGetLastError();
+}
+
+cudaError_t sk_launch_lse2(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count, size_t smem,
+                           int gbits, int threads, cudaStream_t s) {
+    if (w.P == 0) return cudaSuccess;
+    switch (threads) {
+        case 256: return launch_lse2<256>(w, r, n_inner, active_count, big_count, smem, gbits, s);
+        case 512: return launch_lse2<512>(w, r, n_inner, active_count, big_count, smem, gbits, s);
+        case 1024: return launch_lse2<1024>(w, r, n_inner, active_count, big_count, smem, gbits, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
