@@ -177,6 +177,95 @@ pd_status pd_kmeans(pd_ctx* ctx, const uint32_t* hist, const uint32_t* mass, int
                     const pd_sinkhorn_params* params, double lambda, int rounds, int bary_steps,
                     uint64_t seed, int32_t* assign, double* centroids, double* objective, pd_stream stream);
 
+/*
+ * Serving (pd_serve_*): a request loop with continuous batching for
+ * distance and nearest-centroid queries.  The paper has no serving component;
+ * the queries are the uses of the distance that Sec. 5 makes (pairwise
+ * distances between diagrams, assignment of a diagram to the nearest of k
+ * centroids), each answered by a PD_FP32 solve of Alg. 1.
+ *
+ * A server owns one pool of pair slots per grid size d in {32, 64, 128, 256};
+ * a slot is the device workspace of one Sinkhorn pair.  A worker thread runs
+ * scheduling rounds: it admits queued queries in FIFO order (per d) while their
+ * pairs fit in free slots (distance: 1 pair, nearest: one pair per resident
+ * centroid of that d), rasterises and sets them up, runs inner_iters
+ * iterations of every active pair of every pool (one launch per pool, pools on
+ * their own streams, so the work of all admitted queries overlaps on the
+ * device), then finalises the pairs that stopped and releases their slots.
+ * Queries that arrive while others are on the GPU join at the next round.
+ * Centroids stay resident in device memory; with warm_start, the solve of a
+ * query against centroid c starts from the centroid-side potential g of the
+ * last finished solve against c (its support entries and Delta).
+ *
+ * All entry points are thread-safe.  Points are host arrays, copied at submit.
+ */
+typedef struct pd_server pd_server;
+
+typedef struct {
+    double gamma;          /* entropic regularisation of every solve (> 0) */
+    double tol;            /* relative marginal tolerance of every solve (>= 0) */
+    int max_iter;          /* iterations per solve at most (>= 1) */
+    int inner_iters;       /* iterations per scheduling round (<= 0: 32) */
+    int slots[4];          /* pair slots for d = 32, 64, 128, 256; 0: from max_hbm_bytes;
+                              < 0: no pool for that d (its queries are refused) */
+    size_t max_hbm_bytes;  /* device memory shared equally by the pools whose slots[] is 0
+                              (0: half of the free device memory at creation) */
+    int queue_capacity;    /* queries submitted and not yet polled at most (<= 0: 65536) */
+    int warm_start;        /* 1: nearest-centroid solves start from the last g of that centroid */
+} pd_serve_config;
+
+enum { PD_Q_DISTANCE = 0, PD_Q_NEAREST = 1 };
+
+typedef struct {
+    int kind;                  /* PD_Q_DISTANCE or PD_Q_NEAREST */
+    int d;                     /* 32, 64, 128 or 256 */
+    const double* birth_a_host;/* diagram A: n_a points (host, copied at submit) */
+    const double* death_a_host;
+    int n_a;
+    const double* birth_b_host;/* diagram B (PD_Q_DISTANCE only) */
+    const double* death_b_host;
+    int n_b;
+} pd_query;
+
+typedef struct {
+    pd_status status;    /* PD_OK; PD_NOT_CONVERGED if a solve hit max_iter; PD_ERR_* on failure */
+    double cost;         /* distance: <P, C> of (A, B); nearest: <P, C> to the nearest centroid */
+    int centroid;        /* nearest: index of the nearest centroid (ties: lowest); distance: -1 */
+    int iters;           /* largest iteration count over the query's solves */
+    double latency_ms;   /* submit to completion, host steady clock */
+} pd_result;
+
+/* Default configuration: gamma 5e-3, tol 1e-4, max_iter 5000, inner_iters 32,
+ * slots from half the free memory, queue_capacity 65536, warm_start 1. */
+void pd_serve_default_config(pd_serve_config* cfg);
+/* Create a server on ctx's device (ctx must outlive the server; the server
+ * does not use ctx's workspace).  Allocates the slot pools.
+ * Errors: PD_ERR_INVALID (bad config), PD_ERR_OOM, PD_ERR_CUDA. */
+pd_status pd_serve_create(pd_ctx* ctx, const pd_serve_config* cfg, pd_server** out);
+/* Make z (double [k][d*d], device, non-negative weights) the resident centroids
+ * of grid size d (copied; replaces earlier ones and their warm potentials).
+ * Errors: PD_ERR_INVALID if d is not a pool size, k < 1, k exceeds the pool's
+ * slots, or a query of size d is in flight; PD_ERR_OOM; PD_ERR_CUDA. */
+pd_status pd_serve_load_centroids(pd_server* sv, int d, const double* z, int k);
+/* Queue a query; *ticket identifies it.  Points must be finite with
+ * 0 <= birth <= death <= 1 (checked here).  Errors: PD_ERR_INVALID (bad query,
+ * no centroids loaded for a nearest query), PD_ERR_QUEUE_FULL, PD_ERR_CUDA (the
+ * server stopped after a device error). */
+pd_status pd_serve_submit(pd_server* sv, const pd_query* q, uint64_t* ticket);
+/* Result of a ticket: PD_PENDING while it runs; otherwise the query's status,
+ * with *out filled, and the ticket is released.  PD_ERR_INVALID for an unknown
+ * ticket. */
+pd_status pd_serve_poll(pd_server* sv, uint64_t ticket, pd_result* out);
+/* As pd_serve_poll, but waits up to timeout_ms (< 0: without limit) for the
+ * result; PD_PENDING if it is still running then. */
+pd_status pd_serve_wait(pd_server* sv, uint64_t ticket, pd_result* out, double timeout_ms);
+/* Host-side fault injection for tests: the next scheduling round fails as if
+ * a CUDA call had failed, without touching the device.  The server then
+ * fails every admitted and queued query with PD_ERR_CUDA and refuses new ones. */
+pd_status pd_serve_inject_failure(pd_server* sv);
+/* Stop the worker, drop unfinished queries, release the pools.  Safe on NULL. */
+void pd_serve_destroy(pd_server* sv);
+
 /* Kernel classes recorded by the launch profiler. */
 enum {
     PD_K_RASTER = 0,   /* rasteriser */

@@ -23,7 +23,11 @@ STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID", 2: "PD_ERR_OOM", 3: "PD_ERR_CUD
 # Every symbol the header declares (checked by the ABI test).
 EXPORTED = ["pd_abi_version", "pd_ctx_create", "pd_ctx_destroy", "pd_last_error", "pd_rasterize",
             "pd_sinkhorn_default_params", "pd_sinkhorn_batch", "pd_profile_enable", "pd_profile_read",
-            "pd_sinkhorn_batch_noalloc", "pd_barycenter", "pd_kmeans"]
+            "pd_sinkhorn_batch_noalloc", "pd_barycenter", "pd_kmeans", "pd_serve_default_config",
+            "pd_serve_create", "pd_serve_load_centroids", "pd_serve_submit", "pd_serve_poll", "pd_serve_wait",
+            "pd_serve_inject_failure", "pd_serve_destroy"]
+PD_Q_DISTANCE, PD_Q_NEAREST = 0, 1
+SERVE_D = (32, 64, 128, 256)
 PD_K_RASTER, PD_K_SETUP, PD_K_LOGSTEP, PD_K_ABSORB, PD_K_ITER, PD_K_FINALIZE, PD_K_COUNT = 0, 1, 2, 3, 4, 5, 16
 KERNEL_NAMES = {0: "raster", 1: "setup", 2: "logstep", 3: "absorb", 4: "iter", 5: "finalize"}
 
@@ -39,6 +43,26 @@ class SinkhornParams(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("d", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int), ("refine_iters", ctypes.c_int),
                 ("absorb_tau", ctypes.c_double), ("absorb_every", ctypes.c_int), ("rel_log_thresh", ctypes.c_double)]
+
+
+class ServeConfig(ctypes.Structure):
+    """Mirror of pd_serve_config."""
+    _fields_ = [("gamma", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("inner_iters", ctypes.c_int), ("slots", ctypes.c_int * 4), ("max_hbm_bytes", ctypes.c_size_t),
+                ("queue_capacity", ctypes.c_int), ("warm_start", ctypes.c_int)]
+
+
+class Query(ctypes.Structure):
+    """Mirror of pd_query."""
+    _fields_ = [("kind", ctypes.c_int), ("d", ctypes.c_int),
+                ("birth_a_host", ctypes.c_void_p), ("death_a_host", ctypes.c_void_p), ("n_a", ctypes.c_int),
+                ("birth_b_host", ctypes.c_void_p), ("death_b_host", ctypes.c_void_p), ("n_b", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    """Mirror of pd_result."""
+    _fields_ = [("status", ctypes.c_int), ("cost", ctypes.c_double), ("centroid", ctypes.c_int),
+                ("iters", ctypes.c_int), ("latency_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -80,6 +104,16 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                       ctypes.c_int, _vp, _vp, _vp, _vp]
         lib.pd_kmeans.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SinkhornParams),
                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _vp, _vp, _vp, _vp]
+        lib.pd_serve_default_config.argtypes = [ctypes.POINTER(ServeConfig)]
+        lib.pd_serve_default_config.restype = None
+        lib.pd_serve_create.argtypes = [_vp, ctypes.POINTER(ServeConfig), ctypes.POINTER(_vp)]
+        lib.pd_serve_load_centroids.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int]
+        lib.pd_serve_submit.argtypes = [_vp, ctypes.POINTER(Query), ctypes.POINTER(ctypes.c_uint64)]
+        lib.pd_serve_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(Result)]
+        lib.pd_serve_wait.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(Result), ctypes.c_double]
+        lib.pd_serve_inject_failure.argtypes = [_vp]
+        lib.pd_serve_destroy.argtypes = [_vp]
+        lib.pd_serve_destroy.restype = None
         lib.pd_profile_enable.argtypes = [_vp, ctypes.c_int]
         lib.pd_profile_read.argtypes = [_vp, _vp, _vp]
         _lib = lib
@@ -231,3 +265,107 @@ def pd_sinkhorn_batch_noalloc(histA, massA, histB, massB, params: SinkhornParams
     if st != PD_OK:
         raise PdError(st, "pd_sinkhorn_batch_noalloc failed")
     return o
+
+
+# --------------------------------------------------------------------------- serving
+def serve_default_config(**overrides) -> ServeConfig:
+    """pd_serve_default_config, then the given fields (slots as a 4-sequence)."""
+    cfg = ServeConfig()
+    load().pd_serve_default_config(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "slots":
+            for i, x in enumerate(v):
+                cfg.slots[i] = int(x)
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+class Server:
+    """pd_server: continuous-batching request loop (pd_serve_* in the C ABI)."""
+
+    def __init__(self, ctx: Context, cfg: ServeConfig | None = None, **overrides):
+        self.lib = ctx.lib
+        self.ctx = ctx
+        cfg = cfg if cfg is not None else serve_default_config(**overrides)
+        h = _vp()
+        st = self.lib.pd_serve_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h))
+        if st != PD_OK:
+            raise PdError(st, "pd_serve_create failed")
+        self.handle = h
+
+    def load_centroids(self, d: int, z):
+        """z: CUDA float64 tensor [k, d*d] (or [k, d, d]) of centroid weights."""
+        import torch
+        z = z.reshape(z.shape[0], d * d).to(torch.float64).contiguous()
+        st = self.lib.pd_serve_load_centroids(self.handle, int(d), _ptr(z), int(z.shape[0]))
+        torch.cuda.synchronize()
+        if st != PD_OK:
+            raise PdError(st, "pd_serve_load_centroids failed")
+
+    def _submit(self, kind, d, ba, da, bb=None, db=None) -> int:
+        import numpy as np
+        ba = np.ascontiguousarray(ba, dtype=np.float64)
+        da = np.ascontiguousarray(da, dtype=np.float64)
+        q = Query(kind, int(d), ba.ctypes.data, da.ctypes.data, int(ba.size), None, None, 0)
+        if bb is not None:
+            bb = np.ascontiguousarray(bb, dtype=np.float64)
+            db = np.ascontiguousarray(db, dtype=np.float64)
+            q.birth_b_host, q.death_b_host, q.n_b = bb.ctypes.data, db.ctypes.data, int(bb.size)
+        t = ctypes.c_uint64()
+        st = self.lib.pd_serve_submit(self.handle, ctypes.byref(q), ctypes.byref(t))
+        if st != PD_OK:
+            raise PdError(st, "pd_serve_submit failed")
+        return t.value
+
+    def submit_distance(self, d, birth_a, death_a, birth_b, death_b) -> int:
+        return self._submit(PD_Q_DISTANCE, d, birth_a, death_a, birth_b, death_b)
+
+    def submit_nearest(self, d, birth, death) -> int:
+        return self._submit(PD_Q_NEAREST, d, birth, death)
+
+    @staticmethod
+    def _as_dict(r: Result):
+        return {"status": r.status, "cost": r.cost, "centroid": r.centroid, "iters": r.iters,
+                "latency_ms": r.latency_ms}
+
+    def poll(self, ticket: int):
+        """None while pending, else the result dict (the ticket is released)."""
+        r = Result()
+        st = self.lib.pd_serve_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if st == PD_PENDING:
+            return None
+        if st == PD_ERR_INVALID and r.status == 0 and r.latency_ms == 0:
+            raise PdError(st, f"unknown ticket {ticket}")
+        return self._as_dict(r)
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0):
+        r = Result()
+        st = self.lib.pd_serve_wait(self.handle, ctypes.c_uint64(ticket), ctypes.byref(r), float(timeout_ms))
+        if st == PD_PENDING:
+            return None
+        if st == PD_ERR_INVALID and r.status == 0 and r.latency_ms == 0:
+            raise PdError(st, f"unknown ticket {ticket}")
+        return self._as_dict(r)
+
+    def inject_failure(self):
+        st = self.lib.pd_serve_inject_failure(self.handle)
+        if st != PD_OK:
+            raise PdError(st, "pd_serve_inject_failure failed")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.pd_serve_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

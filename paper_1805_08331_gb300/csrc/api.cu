@@ -43,6 +43,8 @@ struct ProfScope {
     }
 };
 
+int pd_ctx_device(const pd_ctx* c) { return c ? c->device : 0; }
+
 static pd_status fail(pd_ctx* c, pd_status s, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -159,7 +161,7 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Carve the workspace for P pairs at padded size dp; returns bytes needed when
 // base == nullptr.
-static size_t carve(char* base, int P, int d, int dp, double gamma, SkWS* w, int** counter) {
+size_t pd_carve_ws(char* base, int P, int d, int dp, double gamma, SkWS* w, int** counter) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* { char* r = base ? base + off : nullptr; off += align256(bytes); return r; };
     const size_t M = (size_t)dp * dp, n = M + 1;
@@ -195,7 +197,7 @@ static size_t carve(char* base, int P, int d, int dp, double gamma, SkWS* w, int
 
 // Cost tables for m = 0..dp-1 (physical units, z = m/d): c_m/gamma = z^2/gamma and
 // cD_m/gamma = z^2/(2 gamma), each split into FP32 hi + lo words; log c_m = 2 log z.
-static cudaError_t upload_cost_tables(const SkWS& w, double gamma, cudaStream_t s) {
+cudaError_t pd_upload_cost_tables(const SkWS& w, double gamma, cudaStream_t s) {
     const int dp = w.dp, d = w.d;
     std::vector<float> tab(5 * dp);
     for (int m = 0; m < dp; ++m) {
@@ -342,7 +344,7 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     const int dp = ((d + 63) / 64) * 64;
     SkWS w;
     int* counter;
-    size_t need = carve(nullptr, P, d, dp, prm->gamma, nullptr, &counter);
+    size_t need = pd_carve_ws(nullptr, P, d, dp, prm->gamma, nullptr, &counter);
     if (need > c->ws_bytes) {
         CUDA_TRY(c, cudaStreamSynchronize(s));
         if (c->ws) cudaFree(c->ws);
@@ -354,9 +356,9 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         }
         c->ws_bytes = need;
     }
-    carve((char*)c->ws, P, d, dp, prm->gamma, &w, &counter);
+    pd_carve_ws((char*)c->ws, P, d, dp, prm->gamma, &w, &counter);
     w.histA = histA; w.histB = histB; w.massA = massA; w.massB = massB; w.pairs = pairs;
-    CUDA_TRY(c, upload_cost_tables(w, prm->gamma, s));
+    CUDA_TRY(c, pd_upload_cost_tables(w, prm->gamma, s));
     SkRun r = make_run(prm);
     if (prm->precision == PD_FP32) {
         pd_status st = lse_solve(c, w, r, g_init, cost, row_marg, col_marg, f, g, iters, err, status, counter, s);
@@ -429,11 +431,11 @@ static pd_status check_params(pd_ctx* c, const pd_sinkhorn_params* prm, const ch
 static pd_status sinkhorn_ws(pd_ctx* c, int P, const pd_sinkhorn_params* prm, SkWS* w, int** counter,
                              cudaStream_t s) {
     const int d = prm->d, dp = ((d + 63) / 64) * 64;
-    size_t need = carve(nullptr, P, d, dp, prm->gamma, nullptr, counter);
+    size_t need = pd_carve_ws(nullptr, P, d, dp, prm->gamma, nullptr, counter);
     pd_status st = ensure_buffer(c, &c->ws, &c->ws_bytes, need, s);
     if (st != PD_OK) return st;
-    carve((char*)c->ws, P, d, dp, prm->gamma, w, counter);
-    CUDA_TRY(c, upload_cost_tables(*w, prm->gamma, s));
+    pd_carve_ws((char*)c->ws, P, d, dp, prm->gamma, w, counter);
+    CUDA_TRY(c, pd_upload_cost_tables(*w, prm->gamma, s));
     return PD_OK;
 }
 
@@ -619,10 +621,10 @@ extern "C" pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint
     }
     const int dp = ((d + 63) / 64) * 64;
     int* counter = nullptr;
-    if (carve(nullptr, P, d, dp, prm->gamma, nullptr, &counter) > PD_NOALLOC_SCRATCH_BYTES)
+    if (pd_carve_ws(nullptr, P, d, dp, prm->gamma, nullptr, &counter) > PD_NOALLOC_SCRATCH_BYTES)
         return PD_ERR_INVALID;   // this many pairs at this d do not fit in the static scratch
     SkWS w;
-    carve((char*)g_noalloc_addr[dev], P, d, dp, prm->gamma, &w, &counter);
+    pd_carve_ws((char*)g_noalloc_addr[dev], P, d, dp, prm->gamma, &w, &counter);
     w.histA = histA; w.histB = histB; w.massA = massA; w.massB = massB; w.pairs = pairs;
     float tab[5 * 256];
     for (int m = 0; m < dp; ++m) {

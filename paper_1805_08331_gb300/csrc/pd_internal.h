@@ -81,6 +81,7 @@ struct SkRun {
 };
 
 cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s);
+cudaError_t sk_launch_setup_list(const SkWS& w, const double* g_init, const int* plist, int np, cudaStream_t s);
 cudaError_t sk_launch_logstep(const SkWS& w, SkRun r, cudaStream_t s);
 cudaError_t sk_launch_absorb(const SkWS& w, SkRun r, cudaStream_t s);
 cudaError_t sk_launch_iter_fp32(const SkWS& w, SkRun r, int n_inner, int* active_count, cudaStream_t s);
@@ -98,6 +99,12 @@ cudaError_t sk_launch_lse2(const SkWS& w, SkRun r, int n_inner, int* active_coun
 cudaError_t sk_launch_lse_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
                                    double* g, int32_t* iters, float* err, int32_t* status, int pot_support_only,
                                    cudaStream_t s);
+cudaError_t sk_launch_lse_finalize_list(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
+                                        double* g, int32_t* iters, float* err, int32_t* status, int pso,
+                                        const int* plist, int np, cudaStream_t s);
+// workspace helpers (api.cu)
+size_t pd_carve_ws(char* base, int P, int d, int dp, double gamma, SkWS* w, int** counter);
+cudaError_t pd_upload_cost_tables(const SkWS& w, double gamma, cudaStream_t s);
 // outer loops (outer.cu)
 cudaError_t outer_bary_init_uniform(double* z, const uint32_t* mass, int N, int d, cudaStream_t s);
 cudaError_t outer_measure_mass(const double* z, int k, int d, double* out, cudaStream_t s);

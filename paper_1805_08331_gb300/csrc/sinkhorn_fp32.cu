@@ -131,10 +131,11 @@ __device__ void build_lists(const float* m, int d, int dp, int* list, int* rowpt
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(T_CTA) sk_setup_kernel(SkWS w, const double* __restrict__ g_init) {
+__global__ void __launch_bounds__(T_CTA) sk_setup_kernel(SkWS w, const double* __restrict__ g_init,
+                                                         const int* __restrict__ plist) {
     __shared__ int sh[64];
     __shared__ double shd[32];
-    const int p = blockIdx.x, t = threadIdx.x;
+    const int p = plist ? plist[blockIdx.x] : blockIdx.x, t = threadIdx.x;
     PairPtrs q = pair_ptrs(w, p);
     const int d = w.d, dp = w.dp;
     int ia = w.pairs ? w.pairs[2 * p] : p, ib = w.pairs ? w.pairs[2 * p + 1] : p;
@@ -189,7 +190,13 @@ __global__ void __launch_bounds__(T_CTA) sk_setup_kernel(SkWS w, const double* _
 
 cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s) {
     if (w.P == 0) return cudaSuccess;
-    sk_setup_kernel<<<w.P, T_CTA, 0, s>>>(w, g_init);
+    sk_setup_kernel<<<w.P, T_CTA, 0, s>>>(w, g_init, nullptr);
+    return cudaGetLastError();
+}
+// Set-up of the pairs plist[0..np) only (the others keep their state).
+cudaError_t sk_launch_setup_list(const SkWS& w, const double* g_init, const int* plist, int np, cudaStream_t s) {
+    if (np <= 0) return cudaSuccess;
+    sk_setup_kernel<<<np, T_CTA, 0, s>>>(w, g_init, plist);
     return cudaGetLastError();
 }
 

@@ -264,10 +264,12 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_finalize_kernel(SkWS w, double* 
                                                                 double* __restrict__ fo, double* __restrict__ go,
                                                                 int32_t* __restrict__ iters_o,
                                                                 float* __restrict__ err_o,
-                                                                int32_t* __restrict__ status_o, int pso) {
+                                                                int32_t* __restrict__ status_o, int pso,
+                                                                const int* __restrict__ plist) {
     __shared__ int rows[256], cols[256], nrc[2];
     __shared__ double shd[32];
-    const int p = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    const int p = plist ? plist[blockIdx.x] : blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5,
+              nw = blockDim.x >> 5;
     PairPtrs q = pair_ptrs(w, p);
     const int d = w.d, dp = w.dp, n_out = d * d + 1, na = q.ic[IC_NA], nb = q.ic[IC_NB];
     const int st = q.ic[IC_STATUS];
@@ -437,7 +439,16 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_finalize_kernel(SkWS w, double* 
 cudaError_t sk_launch_lse_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
                                    double* g, int32_t* iters, float* err, int32_t* status, int pso, cudaStream_t s) {
     if (w.P == 0) return cudaSuccess;
-    sk_lse_finalize_kernel<<<w.P, T_CTA, 0, s>>>(w, cost, row_marg, col_marg, f, g, iters, err, status, pso);
+    sk_lse_finalize_kernel<<<w.P, T_CTA, 0, s>>>(w, cost, row_marg, col_marg, f, g, iters, err, status, pso,
+                                                 nullptr);
+    return cudaGetLastError();
+}
+// Finalize of the pairs plist[0..np) only; outputs are indexed by pair.
+cudaError_t sk_launch_lse_finalize_list(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
+                                        double* g, int32_t* iters, float* err, int32_t* status, int pso,
+                                        const int* plist, int np, cudaStream_t s) {
+    if (np <= 0) return cudaSuccess;
+    sk_lse_finalize_kernel<<<np, T_CTA, 0, s>>>(w, cost, row_marg, col_marg, f, g, iters, err, status, pso, plist);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,177 @@
+"""Serving (pd_serve_*): continuous batching of distance and nearest-centroid
+queries.  Each result must be the same alone and in a mix of concurrent
+queries (within the serving tolerance), agree with the batch API on the same
+pairs, and the nearest centroid must be the argmin of the batch costs."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1805_08331_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+GAMMA, TOL = 5e-3, 1e-4
+# relative agreement of two cold-started solves of the same pair that both
+# stopped at marginal error <= TOL
+REL = 2e-4
+# a warm-started solve stops at another iterate of the same fixed point; both
+# are within the TOL stopping error of it, measured here as cost agreement
+REL_WARM = 3e-3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    return api.Context(0)
+
+
+def _diagram(rng_seed, n):
+    b, t, o = inputs.random_diagrams(1, nmin=n, nmax=n, seed=rng_seed)
+    return b, t
+
+
+def _batch_cost(ctx, d, ba, da, bb, db):
+    """The same pair through pd_sinkhorn_batch (cold start)."""
+    import torch
+    b = np.concatenate([ba, bb])
+    t = np.concatenate([da, db])
+    o = np.array([0, len(ba), len(ba) + len(bb)], dtype=np.int64)
+    db_, dt_, do_ = (torch.from_numpy(x).cuda() for x in (b, t, o))
+    hist, mass = api.pd_rasterize(ctx, db_, dt_, do_, d)
+    prm = api.pd_sinkhorn_default_params(GAMMA, d, max_iter=5000, tol=TOL)
+    out = api.pd_sinkhorn_batch(ctx, hist[0:1], mass[0:1], hist[1:2], mass[1:2], prm)
+    return float(out["cost"][0].item()), int(out["status"][0].item())
+
+
+def _mixed_queries(n, seed):
+    rng = np.random.default_rng(seed)
+    qs = []
+    for q in range(n):
+        d = int(rng.choice(api.SERVE_D))
+        na, nb = (int(x) for x in rng.integers(5, 160, size=2))
+        ba, da = _diagram(seed * 1000 + 2 * q, na)
+        bb, db = _diagram(seed * 1000 + 2 * q + 1, nb)
+        qs.append((d, ba, da, bb, db))
+    return qs
+
+
+def test_serve_distance_alone_equals_mix(ctx):
+    qs = _mixed_queries(24, seed=3)
+    with api.Server(ctx, gamma=GAMMA, tol=TOL, max_iter=5000, slots=[16, 16, 16, 8], warm_start=0) as sv:
+        tickets = [sv.submit_distance(*q) for q in qs]           # all in flight together
+        mix = [sv.wait(t, 120000) for t in tickets]
+        alone = []
+        for q in qs:                                             # one at a time
+            alone.append(sv.wait(sv.submit_distance(*q), 120000))
+    for q, m, a in zip(qs, mix, alone):
+        assert m is not None and a is not None
+        assert m["status"] == api.PD_OK and a["status"] == api.PD_OK, (m, a)
+        assert m["centroid"] == -1
+        assert m["latency_ms"] > 0
+        assert abs(m["cost"] - a["cost"]) <= REL * a["cost"], (q[0], m, a)
+    # and the batch API on the same pairs
+    for q, m in list(zip(qs, mix))[:8]:
+        c, st = _batch_cost(ctx, *q)
+        assert st == api.PD_OK
+        assert abs(m["cost"] - c) <= REL * c, (q[0], m["cost"], c)
+
+
+def test_serve_nearest_is_argmin(ctx):
+    import torch
+    d, k = 64, 6
+    # centroids: rasterised mode diagrams (integer weights stored as doubles)
+    b, t, o, _ = inputs.mode_diagrams(k, n_modes=k, nmin=40, nmax=60, sigma=0.03, seed=5)
+    db_, dt_, do_ = (torch.from_numpy(x).cuda() for x in (b, t, o))
+    zh, zm = api.pd_rasterize(ctx, db_, dt_, do_, d)
+    Z = zh.view(k, d * d).to(torch.float64)
+    queries = [(_diagram(700 + i, 30 + 7 * i)) for i in range(10)]
+    for warm in (0, 1):
+        with api.Server(ctx, gamma=GAMMA, tol=TOL, max_iter=5000, slots=[-1, 32, -1, -1], warm_start=warm) as sv:
+            sv.load_centroids(d, Z)
+            tickets = [sv.submit_nearest(d, qb, qt) for qb, qt in queries]
+            res = [sv.wait(tk, 120000) for tk in tickets]
+        for (qb, qt), r in zip(queries, res):
+            assert r is not None and r["status"] == api.PD_OK, r
+            # batch costs of the query against every centroid
+            qq = torch.from_numpy(np.concatenate([qb])).cuda(), torch.from_numpy(np.concatenate([qt])).cuda()
+            qo = torch.tensor([0, len(qb)], dtype=torch.int64, device="cuda")
+            qh, qm = api.pd_rasterize(ctx, qq[0], qq[1], qo, d)
+            prm = api.pd_sinkhorn_default_params(GAMMA, d, max_iter=5000, tol=TOL)
+            pairs = torch.stack([torch.zeros(k, dtype=torch.int32), torch.arange(k, dtype=torch.int32)], 1).cuda()
+            out = api.pd_sinkhorn_batch(ctx, qh, qm, zh, zm, prm, pairs=pairs)
+            costs = out["cost"].cpu().numpy()
+            best = int(np.argmin(costs))
+            srt = np.sort(costs)
+            rel = REL_WARM if warm else REL
+            assert abs(r["cost"] - costs[r["centroid"]]) <= rel * costs[r["centroid"]], (warm, r, costs)
+            if srt[1] - srt[0] > 2 * rel * srt[0]:   # a clear winner must be found
+                assert r["centroid"] == best, (warm, r, costs)
+
+
+def test_serve_queue_full_and_invalid(ctx):
+    with api.Server(ctx, gamma=GAMMA, tol=TOL, slots=[8, -1, -1, -1], queue_capacity=2) as sv:
+        ba, da = _diagram(1, 20)
+        t1 = sv.submit_distance(32, ba, da, ba, da)
+        t2 = sv.submit_distance(32, ba, da, ba, da)
+        with pytest.raises(api.PdError) as e:
+            sv.submit_distance(32, ba, da, ba, da)
+        assert e.value.status == api.PD_ERR_QUEUE_FULL
+        for tk in (t1, t2):
+            r = sv.wait(tk, 60000)
+            assert r["status"] == api.PD_OK and r["cost"] >= 0
+        # the same diagram against itself: small cost (entropic), never negative
+        # invalid queries are refused at submit
+        with pytest.raises(api.PdError) as e:
+            sv.submit_distance(32, np.array([0.5]), np.array([0.2]), ba, da)    # birth > death
+        assert e.value.status == api.PD_ERR_INVALID
+        with pytest.raises(api.PdError) as e:
+            sv.submit_distance(100, ba, da, ba, da)                           # not a pool size
+        assert e.value.status == api.PD_ERR_INVALID
+        with pytest.raises(api.PdError) as e:
+            sv.submit_distance(64, ba, da, ba, da)                            # pool without slots
+        assert e.value.status == api.PD_ERR_INVALID
+        with pytest.raises(api.PdError) as e:
+            sv.submit_nearest(32, ba, da)                                     # no centroids loaded
+        assert e.value.status == api.PD_ERR_INVALID
+
+
+def test_serve_empty_diagrams(ctx):
+    with api.Server(ctx, gamma=GAMMA, tol=TOL, slots=[4, -1, -1, -1]) as sv:
+        ba, da = _diagram(2, 15)
+        e = np.zeros(0)
+        r1 = sv.wait(sv.submit_distance(32, ba, da, e, e), 60000)
+        r2 = sv.wait(sv.submit_distance(32, e, e, e, e), 60000)
+    # B empty: every point of A goes to the diagonal (closed form)
+    i = np.minimum(np.floor(ba * 32), 31)
+    j = np.minimum(np.floor(da * 32), 31)
+    expect = float(np.sum(((j - i) / 32.0) ** 2 / 2))
+    assert r1["status"] == api.PD_OK and abs(r1["cost"] - expect) <= 1e-6 * max(expect, 1e-12) + 1e-12
+    assert r2["status"] == api.PD_OK and r2["cost"] == 0.0
+
+
+def test_serve_injected_failure_fails_queries_not_process(ctx):
+    with api.Server(ctx, gamma=GAMMA, tol=TOL, slots=[-1, -1, 8, -1]) as sv:
+        qs = [(_diagram(50 + i, 150)) for i in range(6)]
+        tickets = [sv.submit_distance(128, b, t, b[::-1].copy(), t[::-1].copy()) for b, t in qs]
+        sv.inject_failure()
+        res = [sv.wait(tk, 60000) for tk in tickets]
+        assert all(r is not None for r in res)
+        assert all(r["status"] in (api.PD_OK, api.PD_ERR_CUDA) for r in res)
+        # once the worker has seen the failure, new queries are refused
+        deadline = time.time() + 10
+        refused = False
+        while time.time() < deadline and not refused:
+            try:
+                tk = sv.submit_distance(128, qs[0][0], qs[0][1], qs[0][0], qs[0][1])
+                r = sv.wait(tk, 10000)
+                assert r["status"] in (api.PD_OK, api.PD_ERR_CUDA)
+            except api.PdError as e:
+                assert e.status == api.PD_ERR_CUDA
+                refused = True
+        assert refused
+    # the process and the device are still usable
+    ba, da = _diagram(9, 20)
+    c, st = _batch_cost(ctx, 32, ba, da, ba[::-1].copy(), da[::-1].copy())
+    assert st == api.PD_OK and np.isfinite(c)
