@@ -55,6 +55,12 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=16, help="pairs in the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--parity-sample", type=int, default=4, help="pairs checked against the oracle")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving (p50/p99) leg")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered queries/s (Poisson)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="length of the query stream")
+    ap.add_argument("--serve-centroids", type=int, default=25, help="resident centroids per grid size")
+    ap.add_argument("--serve-gamma", type=float, default=5e-3)
+    ap.add_argument("--serve-tol", type=float, default=1e-4)
     return ap.parse_args()
 
 
@@ -372,6 +378,9 @@ def run_ours(args):
         c_gpu = outs["cost"].cpu().numpy()[:k]
         rel = np.abs(c_gpu - ref["cost"][:k]) / ref["cost"][:k]
         parity = {"pairs_checked": int(k), "max_rel_cost_err_vs_fp64": float(rel.max())}
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = serve_leg(args, ctx)
     ctx.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -381,12 +390,94 @@ def run_ours(args):
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clk, "parity": parity,
                 "status_counts": {str(int(s)): int((status == s).sum()) for s in np.unique(status)},
-                "max_err": float(errs.max())}
+                "max_err": float(errs.max()), "serving": serving}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+# --------------------------------------------------------------------------- serving leg
+def serve_leg(args, ctx):
+    """Poisson stream of distance / nearest-centroid queries through pd_serve:
+    mixed grid sizes {32, 64, 128, 256}, log-uniform 10..5000 points, half of
+    them nearest-centroid queries against resident centroids.  Returns the
+    latency percentiles and the throughput of the completed queries."""
+    import torch
+    from paper_1805_08331_gb300 import api
+    grids = api.SERVE_D
+    k = args.serve_centroids
+    # resident centroids: per mode, the mean of 8 rasterised diagrams of that mode
+    cents = {}
+    for d in grids:
+        b, t, o, _ = inputs.mode_diagrams(8 * k, n_modes=k, nmin=30, nmax=300, sigma=0.03,
+                                          seed=100 + d, labels=np.repeat(np.arange(k), 8))
+        db_, dt_, do_ = (torch.from_numpy(x).cuda() for x in (b, t, o))
+        h, _ = api.pd_rasterize(ctx, db_, dt_, do_, d)
+        cents[d] = h.view(k, 8, d * d).to(torch.float64).mean(1).contiguous()
+    tarr, kind, grid, counts = inputs.poisson_queries(args.serve_rate, args.serve_seconds, grids=grids,
+                                                      nmin=10, nmax=5000, seed=args.seed + 77)
+    nq = len(tarr)
+    rng = np.random.default_rng(args.seed + 78)
+    qa = inputs.random_diagrams(nq, counts=counts, seed=args.seed + 79)
+    qb = inputs.random_diagrams(nq, counts=inputs.log_uniform_counts(rng, nq, 10, 5000), seed=args.seed + 80)
+
+    def pts(q, i):
+        b, t, o = q
+        return b[o[i]:o[i + 1]], t[o[i]:o[i + 1]]
+
+    cfg = api.serve_default_config(gamma=args.serve_gamma, tol=args.serve_tol, max_iter=5000, inner_iters=32,
+                                   max_hbm_bytes=48 << 30, warm_start=1)
+    sv = api.Server(ctx, cfg)
+    for d in grids:
+        sv.load_centroids(d, cents[d])
+    tickets = [None] * nq
+    results = [None] * nq
+    submitted = threading.Event()
+
+    def collector():
+        for i in range(nq):
+            while tickets[i] is None and not submitted.is_set():
+                time.sleep(0.0002)
+            if tickets[i] is not None:
+                results[i] = sv.wait(tickets[i], 600000)
+
+    th = threading.Thread(target=collector)
+    th.start()
+    t0 = time.perf_counter()
+    refused = 0
+    for i in range(nq):
+        dt = tarr[i] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ba, da = pts(qa, i)
+        try:
+            if kind[i] == 0:
+                bb, dbb = pts(qb, i)
+                tickets[i] = sv.submit_distance(int(grid[i]), ba, da, bb, dbb)
+            else:
+                tickets[i] = sv.submit_nearest(int(grid[i]), ba, da)
+        except api.PdError:
+            refused += 1
+    submitted.set()
+    th.join()
+    wall = time.perf_counter() - t0
+    sv.close()
+    done = [r for r in results if r is not None]
+    lat = np.array([r["latency_ms"] for r in done])
+    st = np.array([r["status"] for r in done])
+    it = np.array([r["iters"] for r in done])
+    return {"p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+            "throughput_qps": len(done) / wall, "offered_qps": args.serve_rate, "stream_s": args.serve_seconds,
+            "wall_s": wall, "queries": int(nq), "completed": len(done), "refused": refused,
+            "status_counts": {str(int(x)): int((st == x).sum()) for x in np.unique(st)},
+            "mean_iters": float(it.mean()) if len(it) else None,
+            "workload": f"Poisson {args.serve_rate:g} q/s for {args.serve_seconds:g} s; half distance, half "
+                        f"nearest of {k} resident centroids per d (mean histograms of mode diagrams); "
+                        f"d uniform on {{32,64,128,256}}; 10-5000 points log-uniform; gamma={args.serve_gamma:g}, "
+                        f"tol={args.serve_tol:g}; warm-started centroid potentials"}
 
 
 def main():
