@@ -7,11 +7,11 @@
 //   - one pool of pair slots per grid size d (32, 64, 128, 256); a slot is the
 //     device workspace of one Sinkhorn pair and the pool's size is fixed by a
 //     device-memory budget at creation (admission by free memory = free slots);
-//   - a worker thread running scheduling rounds: admit queued queries (FIFO per
-//     d) into free slots, rasterise + set them up, run `inner_iters`
-//     iterations of every active pair of every pool (pools on their own streams,
-//     so their launches overlap on the device), finalise the pairs that stopped
-//     and release their slots.  A query that arrives while others are on the
+//   - one worker thread per pool running scheduling rounds: admit queued
+//     queries (FIFO) into free slots, rasterise + set them up, run
+//     `inner_iters` iterations of every active pair of the pool, finalise the
+//     pairs that stopped and release their slots.  Pools have their own
+//     streams, so the launches of different grid sizes overlap on the device.  A query that arrives while others are on the
 //     GPU joins at the next round boundary: iteration-level continuous batching;
 //   - resident centroids per d and, with warm_start, the centroid-side
 //     potential g of the last finished solve against each centroid, used as the
@@ -186,10 +186,10 @@ struct pd_server {
     pd_serve_config cfg{};
     SkRun run{};
     Pool pools[kNumPools];
-    std::thread worker;
+    std::thread workers[kNumPools];
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Req*> queue;                        // submitted, not yet taken by the worker
+    std::condition_variable cv_work[kNumPools], cv_done;
+    std::deque<Req*> queue[kNumPools];             // submitted, not yet taken by the pool's worker
     std::unordered_map<uint64_t, Req*> live;       // every ticket not yet returned by poll
     uint64_t next_ticket = 1;
     int outstanding = 0;                           // live tickets
@@ -323,29 +323,24 @@ cudaError_t pool_admit(pd_server* sv, Pool& P, const std::vector<RDiag>& diags, 
     return sk_launch_setup_list(P.w, P.ginit, (const int*)P.d_list.p, (int)inits.size(), P.stream);
 }
 
-// One scheduling round over every pool.  Returns a CUDA error (the caller
-// then fails every query) or cudaSuccess.
-cudaError_t serve_round(pd_server* sv, std::vector<Req*>& pending) {
-    // ---- 1. admission, FIFO per pool; a query that does not fit blocks the later ones of its d
-    std::vector<RDiag> diags[kNumPools];
-    std::vector<SlotInit> inits[kNumPools];
-    bool blocked[kNumPools] = {false, false, false, false};
-    for (size_t i = 0; i < pending.size();) {
-        Req* r = pending[i];
-        const int pi = pool_index(r->d);
-        Pool& P = sv->pools[pi];
+// One scheduling round of pool pi.  Returns a CUDA error (the caller then
+// fails every query) or cudaSuccess.
+cudaError_t serve_round(pd_server* sv, int pi, std::vector<Req*>& pending) {
+    Pool& P = sv->pools[pi];
+    // ---- 1. admission, FIFO; a query that does not fit blocks the later ones
+    std::vector<RDiag> diags;
+    std::vector<SlotInit> inits;
+    size_t taken = 0;
+    for (; taken < pending.size(); ++taken) {
+        Req* r = pending[taken];
         const int need = r->kind == PD_Q_DISTANCE ? 1 : P.k;
-        if (blocked[pi] || (int)P.free_slots.size() < need) {
-            blocked[pi] = true;
-            ++i;
-            continue;
-        }
-        const int ia = (int)diags[pi].size();
-        diags[pi].push_back({r, 0});
+        if ((int)P.free_slots.size() < need) break;
+        const int ia = (int)diags.size();
+        diags.push_back({r, 0});
         int ib = -1;
         if (r->kind == PD_Q_DISTANCE) {
             ib = ia + 1;
-            diags[pi].push_back({r, 1});
+            diags.push_back({r, 1});
         }
         r->npairs = need;
         for (int c = 0; c < need; ++c) {
@@ -356,160 +351,153 @@ cudaError_t serve_round(pd_server* sv, std::vector<Req*>& pending) {
             P.owner_c[slot] = cen;
             P.active.push_back(slot);
             const int warm = (cen >= 0 && sv->cfg.warm_start && P.warm_valid[cen]) ? 1 : 0;
-            inits[pi].push_back({slot, ia, ib, cen, warm});
+            inits.push_back({slot, ia, ib, cen, warm});
         }
-        pending.erase(pending.begin() + (long)i);
     }
-    // ---- 2. admission work and the shared-memory need of every pool with active pairs
-    for (int pi = 0; pi < kNumPools; ++pi) {
-        Pool& P = sv->pools[pi];
-        if (P.S == 0) continue;
-        SV_TRY(pool_admit(sv, P, diags[pi], inits[pi]));
-        if (P.active.empty()) continue;
-        SV_TRY(P.h_cnt.ensure(sizeof(int) * 4));
-        SV_TRY(cudaMemsetAsync(P.counter, 0, sizeof(int) * 4, P.stream));
-        if (P.gbits >= 0) SV_TRY(sk_launch_lse2_need(P.w, P.counter + 2, P.stream));
-        SV_TRY(cudaMemcpyAsync(P.h_cnt.p, P.counter, sizeof(int) * 4, cudaMemcpyDeviceToHost, P.stream));
-    }
-    for (int pi = 0; pi < kNumPools; ++pi)
-        if (sv->pools[pi].S) SV_TRY(cudaStreamSynchronize(sv->pools[pi].stream));
-    // ---- 3. one round of iterations per pool, then the slots' status
+    pending.erase(pending.begin(), pending.begin() + (long)taken);
+    if (P.active.empty()) return cudaSuccess;
+    // ---- 2. admission work and the shared-memory need of the active pairs
+    SV_TRY(pool_admit(sv, P, diags, inits));
+    SV_TRY(P.h_cnt.ensure(sizeof(int) * 4));
+    SV_TRY(cudaMemsetAsync(P.counter, 0, sizeof(int) * 4, P.stream));
+    if (P.gbits >= 0) SV_TRY(sk_launch_lse2_need(P.w, P.counter + 2, P.stream));
+    SV_TRY(cudaMemcpyAsync(P.h_cnt.p, P.counter, sizeof(int) * 4, cudaMemcpyDeviceToHost, P.stream));
+    SV_TRY(cudaStreamSynchronize(P.stream));
+    // ---- 3. one round of iterations, then the slots' status
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, sv->device);
     const int inner = sv->cfg.inner_iters > 0 ? sv->cfg.inner_iters : 32;
-    for (int pi = 0; pi < kNumPools; ++pi) {
-        Pool& P = sv->pools[pi];
-        if (P.S == 0 || P.active.empty()) continue;
-        const size_t smem = (size_t)((int*)P.h_cnt.p)[2];
-        const int na = (int)P.active.size();
-        const int threads = na > 2 * nsm ? 256 : (na > nsm ? 512 : 1024);
-        SV_TRY(P.gbits >= 0 ? sk_launch_lse2(P.w, sv->run, inner, P.counter, P.counter + 1, smem, P.gbits, threads,
-                                             P.stream)
-                            : sk_launch_lse_smem(P.w, sv->run, inner, P.counter, P.counter + 1, P.stream));
-        if (P.any_big) SV_TRY(sk_launch_lse_iter(P.w, sv->run, inner, P.counter, P.stream));
-        serve_status_kernel<<<(P.S + 255) / 256, 256, 0, P.stream>>>(P.w.ic, P.S, P.dstat);
-        SV_TRY(cudaGetLastError());
-        SV_TRY(P.h_stat.ensure(sizeof(int) * P.S));
-        SV_TRY(cudaMemcpyAsync(P.h_stat.p, P.dstat, sizeof(int) * P.S, cudaMemcpyDeviceToHost, P.stream));
-        SV_TRY(cudaMemcpyAsync(P.h_cnt.p, P.counter, sizeof(int) * 2, cudaMemcpyDeviceToHost, P.stream));
-    }
-    for (int pi = 0; pi < kNumPools; ++pi)
-        if (sv->pools[pi].S) SV_TRY(cudaStreamSynchronize(sv->pools[pi].stream));
+    const size_t smem = (size_t)((int*)P.h_cnt.p)[2];
+    const int na = (int)P.active.size();
+    const int threads = na > 2 * nsm ? 256 : (na > nsm ? 512 : 1024);
+    SV_TRY(P.gbits >= 0 ? sk_launch_lse2(P.w, sv->run, inner, P.counter, P.counter + 1, smem, P.gbits, threads,
+                                         P.stream)
+                        : sk_launch_lse_smem(P.w, sv->run, inner, P.counter, P.counter + 1, P.stream));
+    if (P.any_big) SV_TRY(sk_launch_lse_iter(P.w, sv->run, inner, P.counter, P.stream));
+    serve_status_kernel<<<(P.S + 255) / 256, 256, 0, P.stream>>>(P.w.ic, P.S, P.dstat);
+    SV_TRY(cudaGetLastError());
+    SV_TRY(P.h_stat.ensure(sizeof(int) * P.S));
+    SV_TRY(cudaMemcpyAsync(P.h_stat.p, P.dstat, sizeof(int) * P.S, cudaMemcpyDeviceToHost, P.stream));
+    SV_TRY(cudaMemcpyAsync(P.h_cnt.p, P.counter, sizeof(int) * 2, cudaMemcpyDeviceToHost, P.stream));
+    SV_TRY(cudaStreamSynchronize(P.stream));
     // ---- 4. finalise the pairs that stopped
-    std::vector<int> fin[kNumPools];
-    for (int pi = 0; pi < kNumPools; ++pi) {
-        Pool& P = sv->pools[pi];
-        if (P.S == 0 || P.active.empty()) continue;
-        if (((int*)P.h_cnt.p)[1] > 0) P.any_big = true;   // pairs handed to the FP64 global-memory kernel
-        const int* st = (const int*)P.h_stat.p;
-        for (int s : P.active)
-            if (st[s] != ST_ACTIVE) fin[pi].push_back(s);
-        if (fin[pi].empty()) continue;
-        const int nf = (int)fin[pi].size();
-        SV_TRY(P.h_list.ensure(sizeof(int) * nf));
-        SV_TRY(P.d_list.ensure(sizeof(int) * nf));
-        std::memcpy(P.h_list.p, fin[pi].data(), sizeof(int) * nf);
-        SV_TRY(cudaMemcpyAsync(P.d_list.p, P.h_list.p, sizeof(int) * nf, cudaMemcpyHostToDevice, P.stream));
-        SV_TRY(sk_launch_lse_finalize_list(P.w, P.cost, nullptr, nullptr, nullptr, sv->cfg.warm_start ? P.gout : nullptr,
-                                           P.iters, P.err, P.status, 1, (const int*)P.d_list.p, nf, P.stream));
-        if (sv->cfg.warm_start) {
-            std::vector<int2> wl;
-            for (int s : fin[pi])
-                if (P.owner_c[s] >= 0) wl.push_back(make_int2(s, P.owner_c[s]));
-            if (!wl.empty()) {
-                SV_TRY(P.h_list2.ensure(sizeof(int2) * wl.size()));
-                SV_TRY(P.d_list2.ensure(sizeof(int2) * wl.size()));
-                std::memcpy(P.h_list2.p, wl.data(), sizeof(int2) * wl.size());
-                SV_TRY(cudaMemcpyAsync(P.d_list2.p, P.h_list2.p, sizeof(int2) * wl.size(), cudaMemcpyHostToDevice,
-                                       P.stream));
-                serve_warm_kernel<<<(int)wl.size(), 256, 0, P.stream>>>((const int2*)P.d_list2.p, P.gout, P.Z, P.d,
-                                                                       P.warm);
-                SV_TRY(cudaGetLastError());
-            }
+    if (((int*)P.h_cnt.p)[1] > 0) P.any_big = true;   // pairs handed to the FP64 global-memory kernel
+    std::vector<int> fin;
+    const int* st = (const int*)P.h_stat.p;
+    for (int s : P.active)
+        if (st[s] != ST_ACTIVE) fin.push_back(s);
+    if (fin.empty()) return cudaSuccess;
+    const int nf = (int)fin.size();
+    SV_TRY(P.h_list.ensure(sizeof(int) * nf));
+    SV_TRY(P.d_list.ensure(sizeof(int) * nf));
+    std::memcpy(P.h_list.p, fin.data(), sizeof(int) * nf);
+    SV_TRY(cudaMemcpyAsync(P.d_list.p, P.h_list.p, sizeof(int) * nf, cudaMemcpyHostToDevice, P.stream));
+    SV_TRY(sk_launch_lse_finalize_list(P.w, P.cost, nullptr, nullptr, nullptr, sv->cfg.warm_start ? P.gout : nullptr,
+                                       P.iters, P.err, P.status, 1, (const int*)P.d_list.p, nf, P.stream));
+    if (sv->cfg.warm_start) {
+        std::vector<int2> wl;
+        for (int s : fin)
+            if (P.owner_c[s] >= 0) wl.push_back(make_int2(s, P.owner_c[s]));
+        if (!wl.empty()) {
+            SV_TRY(P.h_list2.ensure(sizeof(int2) * wl.size()));
+            SV_TRY(P.d_list2.ensure(sizeof(int2) * wl.size()));
+            std::memcpy(P.h_list2.p, wl.data(), sizeof(int2) * wl.size());
+            SV_TRY(cudaMemcpyAsync(P.d_list2.p, P.h_list2.p, sizeof(int2) * wl.size(), cudaMemcpyHostToDevice,
+                                   P.stream));
+            serve_warm_kernel<<<(int)wl.size(), 256, 0, P.stream>>>((const int2*)P.d_list2.p, P.gout, P.Z, P.d,
+                                                                   P.warm);
+            SV_TRY(cudaGetLastError());
         }
-        SV_TRY(P.d_res.ensure(sizeof(double) * 3 * nf));
-        SV_TRY(P.h_res.ensure(sizeof(double) * 3 * nf));
-        serve_collect_kernel<<<(nf + 255) / 256, 256, 0, P.stream>>>((const int*)P.d_list.p, nf, P.cost, P.iters,
-                                                                    P.status, (double*)P.d_res.p);
-        SV_TRY(cudaGetLastError());
-        SV_TRY(cudaMemcpyAsync(P.h_res.p, P.d_res.p, sizeof(double) * 3 * nf, cudaMemcpyDeviceToHost, P.stream));
     }
-    for (int pi = 0; pi < kNumPools; ++pi)
-        if (!fin[pi].empty()) SV_TRY(cudaStreamSynchronize(sv->pools[pi].stream));
+    SV_TRY(P.d_res.ensure(sizeof(double) * 3 * nf));
+    SV_TRY(P.h_res.ensure(sizeof(double) * 3 * nf));
+    serve_collect_kernel<<<(nf + 255) / 256, 256, 0, P.stream>>>((const int*)P.d_list.p, nf, P.cost, P.iters,
+                                                                P.status, (double*)P.d_res.p);
+    SV_TRY(cudaGetLastError());
+    SV_TRY(cudaMemcpyAsync(P.h_res.p, P.d_res.p, sizeof(double) * 3 * nf, cudaMemcpyDeviceToHost, P.stream));
+    SV_TRY(cudaStreamSynchronize(P.stream));
     // ---- 5. hand out results, release slots
     std::lock_guard<std::mutex> lk(sv->mu);
-    for (int pi = 0; pi < kNumPools; ++pi) {
-        Pool& P = sv->pools[pi];
-        if (fin[pi].empty()) continue;
-        const double* res = (const double*)P.h_res.p;
-        for (size_t i = 0; i < fin[pi].size(); ++i) {
-            const int s = fin[pi][i];
-            Req* r = P.owner[s];
-            const int c = P.owner_c[s];
-            const double cost = res[3 * i];
-            const int it = (int)res[3 * i + 1];
-            const int st = (int)res[3 * i + 2];
-            if (st == PD_NOT_CONVERGED && r->st == PD_OK) r->st = PD_NOT_CONVERGED;
-            else if (st != PD_OK && st != PD_NOT_CONVERGED) r->st = st;
-            r->max_iters = std::max(r->max_iters, it);
-            if (c < 0) {
+    const double* res = (const double*)P.h_res.p;
+    for (size_t i = 0; i < fin.size(); ++i) {
+        const int s = fin[i];
+        Req* r = P.owner[s];
+        const int c = P.owner_c[s];
+        const double cost = res[3 * i];
+        const int it = (int)res[3 * i + 1];
+        const int stt = (int)res[3 * i + 2];
+        if (stt == PD_NOT_CONVERGED && r->st == PD_OK) r->st = PD_NOT_CONVERGED;
+        else if (stt != PD_OK && stt != PD_NOT_CONVERGED) r->st = stt;
+        r->max_iters = std::max(r->max_iters, it);
+        if (c < 0) {
+            r->best = cost;
+        } else {
+            if (cost < r->best || (cost == r->best && c < r->best_c) || r->best_c < 0) {
                 r->best = cost;
-            } else {
-                if (cost < r->best || (cost == r->best && c < r->best_c) || r->best_c < 0) {
-                    r->best = cost;
-                    r->best_c = c;
-                }
-                if (sv->cfg.warm_start && std::isfinite(cost)) P.warm_valid[c] = 1;
+                r->best_c = c;
             }
-            if (++r->done == r->npairs) complete_locked(sv, r, PD_OK);
-            P.owner[s] = nullptr;
-            P.owner_c[s] = -1;
-            P.free_slots.push_back(s);
+            if (sv->cfg.warm_start && std::isfinite(cost)) P.warm_valid[c] = 1;
         }
-        std::vector<int> keep;
-        keep.reserve(P.active.size());
-        for (int s : P.active)
-            if (P.owner[s]) keep.push_back(s);
-        P.active.swap(keep);
+        if (++r->done == r->npairs) complete_locked(sv, r, PD_OK);
+        P.owner[s] = nullptr;
+        P.owner_c[s] = -1;
+        P.free_slots.push_back(s);
     }
+    std::vector<int> keep;
+    keep.reserve(P.active.size());
+    for (int s : P.active)
+        if (P.owner[s]) keep.push_back(s);
+    P.active.swap(keep);
     return cudaSuccess;
 }
 
-void fail_everything(pd_server* sv, std::vector<Req*>& pending, cudaError_t e) {
-    std::lock_guard<std::mutex> lk(sv->mu);
-    sv->dead = true;
-    sv->err = std::string("serving stopped: ") + cudaGetErrorString(e);
+// Fail the queries a worker holds (its pending list and its pool's slots)
+// with PD_ERR_CUDA; called with sv->mu held.
+void fail_own_locked(pd_server* sv, int pi, std::vector<Req*>& pending) {
     for (Req* r : pending) complete_locked(sv, r, PD_ERR_CUDA);
     pending.clear();
-    for (Req* r : sv->queue) complete_locked(sv, r, PD_ERR_CUDA);
-    sv->queue.clear();
-    for (auto& P : sv->pools) {
-        for (int s : P.active)
-            if (P.owner[s]) complete_locked(sv, P.owner[s], PD_ERR_CUDA);
-    }
+    for (Req* r : sv->queue[pi]) complete_locked(sv, r, PD_ERR_CUDA);
+    sv->queue[pi].clear();
+    Pool& P = sv->pools[pi];
+    for (int s : P.active)
+        if (P.owner[s]) complete_locked(sv, P.owner[s], PD_ERR_CUDA);
 }
 
-void worker_main(pd_server* sv) {
+// Worker of pool pi: rounds while it has work, sleeps otherwise.  Each pool
+// has its own worker and stream, so a slow grid size does not hold back the
+// rounds of the others.  A failure (or an injected one) stops every worker.
+void worker_main(pd_server* sv, int pi) {
     cudaSetDevice(sv->device);
+    Pool& P = sv->pools[pi];
     std::vector<Req*> pending;
     while (true) {
-        bool active = !pending.empty();
-        for (auto& P : sv->pools) active = active || !P.active.empty();
+        const bool active = !pending.empty() || !P.active.empty();
         bool inject = false;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
-            if (!active) sv->cv_work.wait(lk, [&] { return sv->stop || !sv->queue.empty() || sv->inject; });
+            if (!active)
+                sv->cv_work[pi].wait(lk, [&] { return sv->stop || sv->dead || !sv->queue[pi].empty() || sv->inject; });
             if (sv->stop) break;
-            while (!sv->queue.empty()) {
-                pending.push_back(sv->queue.front());
-                sv->queue.pop_front();
+            if (sv->dead) {
+                fail_own_locked(sv, pi, pending);
+                break;
+            }
+            while (!sv->queue[pi].empty()) {
+                pending.push_back(sv->queue[pi].front());
+                sv->queue[pi].pop_front();
             }
             inject = sv->inject;
             sv->inject = false;
         }
-        const cudaError_t e = inject ? cudaErrorUnknown : serve_round(sv, pending);
+        const cudaError_t e = inject ? cudaErrorUnknown : serve_round(sv, pi, pending);
         if (e != cudaSuccess) {
-            fail_everything(sv, pending, e);
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                sv->dead = true;
+                sv->err = std::string("serving stopped: ") + cudaGetErrorString(e);
+                fail_own_locked(sv, pi, pending);
+            }
+            for (auto& cv : sv->cv_work) cv.notify_all();
             break;
         }
     }
@@ -583,7 +571,8 @@ extern "C" pd_status pd_serve_create(pd_ctx* ctx, const pd_serve_config* cfg, pd
             }
         }
     }
-    sv->worker = std::thread(worker_main, sv);
+    for (int i = 0; i < kNumPools; ++i)
+        if (sv->pools[i].S > 0) sv->workers[i] = std::thread(worker_main, sv, i);
     *out = sv;
     return PD_OK;
 }
@@ -648,10 +637,10 @@ extern "C" pd_status pd_serve_submit(pd_server* sv, const pd_query* q, uint64_t*
         sv->live[r->ticket] = r;
         sv->outstanding++;
         sv->inflight[pi]++;
-        sv->queue.push_back(r);
+        sv->queue[pi].push_back(r);
         *ticket = r->ticket;
     }
-    sv->cv_work.notify_one();
+    sv->cv_work[pi].notify_one();
     return PD_OK;
 }
 
@@ -698,7 +687,7 @@ extern "C" pd_status pd_serve_inject_failure(pd_server* sv) {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->inject = true;
     }
-    sv->cv_work.notify_one();
+    for (auto& cv : sv->cv_work) cv.notify_all();
     return PD_OK;
 }
 
@@ -708,8 +697,9 @@ extern "C" void pd_serve_destroy(pd_server* sv) {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stop = true;
     }
-    sv->cv_work.notify_all();
-    if (sv->worker.joinable()) sv->worker.join();
+    for (auto& cv : sv->cv_work) cv.notify_all();
+    for (auto& w : sv->workers)
+        if (w.joinable()) w.join();
     cudaSetDevice(sv->device);
     for (auto& P : sv->pools) pool_destroy(P);
     for (auto& kv : sv->live) delete kv.second;

@@ -32,6 +32,7 @@
 // is (non-empty input rows) x 32 whatever the output support; several pairs
 // fit on one SM.
 #include "sk_common.cuh"
+#include <atomic>
 #include <cmath>
 
 #define L2_CW 32          // output columns per chunk
@@ -590,7 +591,7 @@ size_t sk_lse2_smem_cap() {
 template <int NT>
 static cudaError_t launch_lse2(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count, size_t smem,
                                int gbits, cudaStream_t s) {
-    static size_t configured = 0;
+    static std::atomic<size_t> configured{0};
     const size_t cap = sk_lse2_smem_cap();
     if (configured != cap) {
         cudaError_t e = cudaFuncSetAttribute(sk_lse2_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);

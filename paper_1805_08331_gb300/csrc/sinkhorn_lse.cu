@@ -21,6 +21,7 @@
 // compensation; the resulting log-values are accurate to a few 1e-7.
 #define T_CTA 256
 #include "sk_common.cuh"
+#include <atomic>
 
 struct df { float hi, lo; };
 
@@ -752,7 +753,7 @@ __global__ void __launch_bounds__(LSE_SM_THREADS) sk_lse_smem_kernel(SkWS w, SkR
 cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count,
                                cudaStream_t s) {
     if (w.P == 0) return cudaSuccess;
-    static int configured = -1;
+    static std::atomic<int> configured{-1};
     int dev = 0;
     cudaGetDevice(&dev);
     int cap = 0;
