@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--serve-centroids", type=int, default=25, help="resident centroids per grid size")
     ap.add_argument("--serve-gamma", type=float, default=5e-3)
     ap.add_argument("--serve-tol", type=float, default=1e-4)
+    ap.add_argument("--serve-nmax", type=int, default=5000, help="largest diagram of the stream (points)")
     return ap.parse_args()
 
 
@@ -417,11 +418,11 @@ def serve_leg(args, ctx):
         h, _ = api.pd_rasterize(ctx, db_, dt_, do_, d)
         cents[d] = h.view(k, 8, d * d).to(torch.float64).mean(1).contiguous()
     tarr, kind, grid, counts = inputs.poisson_queries(args.serve_rate, args.serve_seconds, grids=grids,
-                                                      nmin=10, nmax=5000, seed=args.seed + 77)
+                                                      nmin=10, nmax=args.serve_nmax, seed=args.seed + 77)
     nq = len(tarr)
     rng = np.random.default_rng(args.seed + 78)
     qa = inputs.random_diagrams(nq, counts=counts, seed=args.seed + 79)
-    qb = inputs.random_diagrams(nq, counts=inputs.log_uniform_counts(rng, nq, 10, 5000), seed=args.seed + 80)
+    qb = inputs.random_diagrams(nq, counts=inputs.log_uniform_counts(rng, nq, 10, args.serve_nmax), seed=args.seed + 80)
 
     def pts(q, i):
         b, t, o = q
@@ -466,6 +467,13 @@ def serve_leg(args, ctx):
     sv.close()
     done = [r for r in results if r is not None]
     lat = np.array([r["latency_ms"] for r in done])
+    dgrid = np.array([int(grid[i]) for i in range(nq) if results[i] is not None])
+    per_d = {}
+    for d in grids:
+        ld = lat[dgrid == d]
+        if len(ld):
+            per_d[str(d)] = {"queries": int(len(ld)), "p50_ms": float(np.percentile(ld, 50)),
+                             "p99_ms": float(np.percentile(ld, 99))}
     st = np.array([r["status"] for r in done])
     it = np.array([r["iters"] for r in done])
     return {"p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
@@ -473,10 +481,10 @@ def serve_leg(args, ctx):
             "throughput_qps": len(done) / wall, "offered_qps": args.serve_rate, "stream_s": args.serve_seconds,
             "wall_s": wall, "queries": int(nq), "completed": len(done), "refused": refused,
             "status_counts": {str(int(x)): int((st == x).sum()) for x in np.unique(st)},
-            "mean_iters": float(it.mean()) if len(it) else None,
+            "mean_iters": float(it.mean()) if len(it) else None, "per_d": per_d,
             "workload": f"Poisson {args.serve_rate:g} q/s for {args.serve_seconds:g} s; half distance, half "
                         f"nearest of {k} resident centroids per d (mean histograms of mode diagrams); "
-                        f"d uniform on {{32,64,128,256}}; 10-5000 points log-uniform; gamma={args.serve_gamma:g}, "
+                        f"d uniform on {{32,64,128,256}}; 10-{args.serve_nmax} points log-uniform; gamma={args.serve_gamma:g}, "
                         f"tol={args.serve_tol:g}; warm-started centroid potentials"}
 
 

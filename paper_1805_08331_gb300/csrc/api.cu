@@ -248,13 +248,16 @@ static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* r
 
 // Iteration rounds of the log-domain engine: each round runs up to 64
 // iterations of every active pair in the on-chip kernel (base-2 kernel when
-// gamma allows a grid, else the double-float one), then the FP64 global-memory
-// kernel for the pairs that do not fit on chip or left the base-2 range, until
-// no pair is active.  counter: 3 device ints; hbuf: 3 host ints; c (may be
+// gamma allows a grid, else the double-float one), then its global-memory
+// variant for the pairs whose supports do not fit on chip, then the FP64
+// global-memory kernel for the pairs too large for that or whose potentials
+// left the base-2 range, until
+// no pair is active.  counter: 4 device ints; hbuf: 4 host ints; c (may be
 // NULL) receives the per-launch profile records.
 static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hbuf, cudaStream_t s) {
     const int n_inner = 64;
-    const int max_rounds = r.max_iter / n_inner + 2;
+    // a pair can spend one round in each of the two hand-overs between kernels
+    const int max_rounds = r.max_iter / n_inner + 4;
     const int gbits = sk_lse2_grid_bits(w.gamma);
     size_t smem = 0;
     cudaError_t e;
@@ -277,25 +280,42 @@ static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hb
         const int v = std::atoi(ev);
         if (v == 256 || v == 512 || v == 1024) fixed_threads = v;
     }
+    // PD_LSE2_TIER=gm runs every pair in the global-memory variant, =fp64 in the
+    // FP64 global-memory kernel (tests of the tiers on small pairs).
+    size_t gcap = (size_t)-1;
+    if (const char* ev = std::getenv("PD_LSE2_TIER")) {
+        if (!std::strcmp(ev, "gm")) smem = 0;
+        if (!std::strcmp(ev, "fp64")) { smem = 0; gcap = 0; }
+    }
     int active = w.P;
-    bool any_big = false;
+    bool any_gm = false, any_old = false;
     for (int round = 0; round < max_rounds; ++round) {
-        if ((e = cudaMemsetAsync(counter, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(counter, 0, 4 * sizeof(int), s)) != cudaSuccess) return e;
         {
             ProfScope ps(c, PD_K_ITER, s);
             const int threads = fixed_threads ? fixed_threads : (active > 2 * nsm ? 256 : (active > nsm ? 512 : 1024));
-            e = gbits >= 0 ? sk_launch_lse2(w, r, n_inner, counter, counter + 1, smem, gbits, threads, s)
+            e = gbits >= 0 ? sk_launch_lse2(w, r, n_inner, counter, smem, gbits, threads, s)
                            : sk_launch_lse_smem(w, r, n_inner, counter, counter + 1, s);
             if (e != cudaSuccess) return e;
         }
-        if (any_big) {
+        if (gbits >= 0 && any_gm) {   // pairs whose supports do not fit on chip
             ProfScope ps(c, PD_K_ITER, s);
-            if ((e = sk_launch_lse_iter(w, r, n_inner, counter, s)) != cudaSuccess) return e;
+            if ((e = sk_launch_lse2_gm(w, r, n_inner, counter, gbits, gcap, s)) != cudaSuccess) return e;
         }
-        if ((e = cudaMemcpyAsync(hbuf, counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        if (any_old) {                // the FP64 global-memory kernel
+            ProfScope ps(c, PD_K_ITER, s);
+            if ((e = sk_launch_lse_iter(w, r, n_inner, counter, gbits >= 0 ? 2 : 1, s)) != cudaSuccess) return e;
+        }
+        if ((e = cudaMemcpyAsync(hbuf, counter, 4 * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return e;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        if (hbuf[1] > 0) any_big = true;   // pairs handed to the global-memory kernel (next round on)
+        // pairs handed on by this round's launches run from the next round on
+        if (gbits >= 0) {
+            if (hbuf[1] > 0) any_gm = true;
+            if (hbuf[3] > 0) any_old = true;
+        } else if (hbuf[1] > 0) {
+            any_old = true;
+        }
         if (hbuf[0] == 0) break;
         active = hbuf[0];
     }
@@ -646,7 +666,7 @@ extern "C" pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint
     r.absorb_every = 64;
     r.rel_thresh = -21.0;
     if (sk_launch_setup(w, g_init, s) != cudaSuccess) return PD_ERR_CUDA;
-    int hcount[3] = {0, 0, 0};
+    int hcount[4] = {0, 0, 0, 0};
     if (lse_rounds(nullptr, w, r, counter, hcount, s) != cudaSuccess) return PD_ERR_CUDA;
     if (sk_launch_lse_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, 0, s) != cudaSuccess)
         return PD_ERR_CUDA;

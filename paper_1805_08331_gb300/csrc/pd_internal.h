@@ -85,7 +85,8 @@ cudaError_t sk_launch_setup_list(const SkWS& w, const double* g_init, const int*
 cudaError_t sk_launch_logstep(const SkWS& w, SkRun r, cudaStream_t s);
 cudaError_t sk_launch_absorb(const SkWS& w, SkRun r, cudaStream_t s);
 cudaError_t sk_launch_iter_fp32(const SkWS& w, SkRun r, int n_inner, int* active_count, cudaStream_t s);
-cudaError_t sk_launch_lse_iter(const SkWS& w, SkRun r, int n_inner, int* active_count, cudaStream_t s);
+// FP64 global-memory iteration kernel for the pairs with IC_BIG >= min_big
+cudaError_t sk_launch_lse_iter(const SkWS& w, SkRun r, int n_inner, int* active_count, int min_big, cudaStream_t s);
 cudaError_t sk_launch_iter_bf16(const SkWS& w, SkRun r, int n_inner, int* active_count, int* error_flag,
                                 cudaStream_t s);
 cudaError_t sk_launch_refine_prep(const SkWS& w, cudaStream_t s);
@@ -94,8 +95,12 @@ cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_
 // base-2 on-chip iteration kernel (sinkhorn_log2.cu)
 int sk_lse2_grid_bits(double gamma);
 cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, cudaStream_t s);
-cudaError_t sk_launch_lse2(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count, size_t smem,
-                           int gbits, int threads, cudaStream_t s);
+// counter: [0] active pairs, [1] pairs moved to the global-memory variant,
+// [2] (need kernel) max shared bytes, [3] pairs moved to the FP64 kernel.
+cudaError_t sk_launch_lse2(const SkWS& w, SkRun r, int n_inner, int* counter, size_t smem, int gbits, int threads,
+                           cudaStream_t s);
+cudaError_t sk_launch_lse2_gm(const SkWS& w, SkRun r, int n_inner, int* counter, int gbits, size_t gcap,
+                              cudaStream_t s);
 cudaError_t sk_launch_lse_finalize(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
                                    double* g, int32_t* iters, float* err, int32_t* status, int pot_support_only,
                                    cudaStream_t s);

@@ -170,7 +170,7 @@ struct Pool {
     std::vector<Req*> owner;           // [S]
     std::vector<int> owner_c;          // [S] centroid of a nearest pair, -1 for distance
     std::vector<int> active;           // slots in use
-    bool any_big = false;
+    bool any_gm = false, any_old = false;   // pairs in the global-memory tiers
     int gbits = -1;
     cudaStream_t stream = nullptr;
     // staging
@@ -370,18 +370,28 @@ cudaError_t serve_round(pd_server* sv, int pi, std::vector<Req*>& pending) {
     const size_t smem = (size_t)((int*)P.h_cnt.p)[2];
     const int na = (int)P.active.size();
     const int threads = na > 2 * nsm ? 256 : (na > nsm ? 512 : 1024);
-    SV_TRY(P.gbits >= 0 ? sk_launch_lse2(P.w, sv->run, inner, P.counter, P.counter + 1, smem, P.gbits, threads,
-                                         P.stream)
+    SV_TRY(cudaMemsetAsync(P.counter, 0, sizeof(int) * 4, P.stream));
+    SV_TRY(P.gbits >= 0 ? sk_launch_lse2(P.w, sv->run, inner, P.counter, smem, P.gbits, threads, P.stream)
                         : sk_launch_lse_smem(P.w, sv->run, inner, P.counter, P.counter + 1, P.stream));
-    if (P.any_big) SV_TRY(sk_launch_lse_iter(P.w, sv->run, inner, P.counter, P.stream));
+    if (P.gbits >= 0 && P.any_gm) SV_TRY(sk_launch_lse2_gm(P.w, sv->run, inner, P.counter, P.gbits, (size_t)-1, P.stream));
+    if (P.any_old) SV_TRY(sk_launch_lse_iter(P.w, sv->run, inner, P.counter, P.gbits >= 0 ? 2 : 1, P.stream));
     serve_status_kernel<<<(P.S + 255) / 256, 256, 0, P.stream>>>(P.w.ic, P.S, P.dstat);
     SV_TRY(cudaGetLastError());
     SV_TRY(P.h_stat.ensure(sizeof(int) * P.S));
     SV_TRY(cudaMemcpyAsync(P.h_stat.p, P.dstat, sizeof(int) * P.S, cudaMemcpyDeviceToHost, P.stream));
-    SV_TRY(cudaMemcpyAsync(P.h_cnt.p, P.counter, sizeof(int) * 2, cudaMemcpyDeviceToHost, P.stream));
+    SV_TRY(cudaMemcpyAsync(P.h_cnt.p, P.counter, sizeof(int) * 4, cudaMemcpyDeviceToHost, P.stream));
     SV_TRY(cudaStreamSynchronize(P.stream));
     // ---- 4. finalise the pairs that stopped
-    if (((int*)P.h_cnt.p)[1] > 0) P.any_big = true;   // pairs handed to the FP64 global-memory kernel
+    {
+        // pairs handed on to the global-memory variant / the FP64 kernel run there from the next round on
+        const int* hc = (const int*)P.h_cnt.p;
+        if (P.gbits >= 0) {
+            if (hc[1] > 0) P.any_gm = true;
+            if (hc[3] > 0) P.any_old = true;
+        } else if (hc[1] > 0) {
+            P.any_old = true;
+        }
+    }
     std::vector<int> fin;
     const int* st = (const int*)P.h_stat.p;
     for (int s : P.active)

@@ -44,6 +44,14 @@
 extern __shared__ __align__(16) unsigned char l2_sm[];
 template <typename T>
 __device__ __forceinline__ T* smp(uint32_t off) { return reinterpret_cast<T*>(l2_sm + off); }
+// Per-side arrays: in shared memory (GM = false), or in the pair's global
+// workspace at gb (GM = true, pairs whose supports do not fit on chip); the
+// cost tables and the stage-1 buffer are in shared memory in both variants.
+template <typename T, bool GM>
+__device__ __forceinline__ T* sdp(unsigned char* gb, uint32_t off) {
+    if constexpr (GM) return reinterpret_cast<T*>(gb + off);
+    else return reinterpret_cast<T*>(l2_sm + off);
+}
 
 struct L2Side {
     int n, nr, nc, nch;
@@ -65,18 +73,24 @@ struct L2Side {
 
 __host__ __device__ __forceinline__ size_t l2_al(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Shared-memory bytes of a pair (the host sizes the launch with the maximum).
-__device__ __forceinline__ size_t l2_need(int nA, int nB, int nrA, int nrB, int d) {
+// Bytes of the per-side arrays of a pair.
+__host__ __device__ __forceinline__ size_t l2_side_bytes(int nA, int nB, int d) {
     size_t b = 0;
     const int ns[2] = {nA, nB};
     for (int s = 0; s < 2; ++s) {
         const size_t n = (size_t)ns[s];
         b += l2_al(24 * n) + l2_al(4 * n) + l2_al(4 * (size_t)(d + 1)) + l2_al(6 * n) + l2_al(6 * (size_t)d);
     }
-    b += l2_al(8 * (size_t)(2 * d - 1)) + l2_al(8 * (size_t)d);
-    const size_t nr = (size_t)(nrA > nrB ? nrA : nrB);
-    b += l2_al(8 * (size_t)L2_CW * nr);
     return b;
+}
+// Bytes of the cost tables and the stage-1 buffer (nrmax non-empty input rows).
+__host__ __device__ __forceinline__ size_t l2_table_bytes(int nrmax, int d) {
+    return l2_al(8 * (size_t)(2 * d - 1)) + l2_al(8 * (size_t)d) + l2_al(8 * (size_t)L2_CW * nrmax);
+}
+// Shared-memory bytes of a pair in the on-chip variant (the host sizes the
+// launch with the maximum over the pairs).
+__device__ __forceinline__ size_t l2_need(int nA, int nB, int nrA, int nrB, int d) {
+    return l2_side_bytes(nA, nB, d) + l2_table_bytes(nrA > nrB ? nrA : nrB, d);
 }
 
 // (hi, lo) split of an FP64 value on the 2^-G grid (gsc = 2^G).
@@ -134,12 +148,13 @@ static __device__ void l2_compact(const int* __restrict__ ptr, int d, short* out
 
 // Group the output cells of a side by chunk of 32 non-empty columns (warp c
 // builds chunk c; the order inside a chunk stays row-major).
-static __device__ void l2_chunks(L2Side& s, int* warp_cnt) {
+template <bool GM>
+static __device__ void l2_chunks(L2Side& s, int* warp_cnt, unsigned char* gb) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nch = s.nch, n = s.n;
-    const short* col = smp<short>(s.col);
-    const short* colpos = smp<short>(s.colpos);
-    short* chl = smp<short>(s.chl);
+    const short* col = sdp<short, GM>(gb, s.col);
+    const short* colpos = sdp<short, GM>(gb, s.colpos);
+    short* chl = sdp<short, GM>(gb, s.chl);
     if (wid < nch) {
         int cnt = 0;
         for (int b = 0; b < n; b += 32) {
@@ -208,18 +223,18 @@ __device__ __forceinline__ bool l2_update(float tot, float shift, float Ms, floa
 // One half-step: out.pot <- -LSE over the input side.  Adds the marginal-error
 // terms of `out` to errs when want_err.  Sets *range_flag if a potential left
 // the exact range (the pair then moves to the FP64 kernel).
-template <int NT>
+template <int NT, bool GM>
 static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool want_err, float& errs,
-                               float* redD, int* range_flag) {
+                               float* redD, int* range_flag, unsigned char* gb) {
     constexpr int NW = NT / 32;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int d = K.d;
     const int in_n = in.n, in_nr = in.nr;
-    const float2* in_hin = smp<float2>(in.hin);
-    const short* in_row = smp<short>(in.row);
-    const short* in_col = smp<short>(in.col);
-    const short* in_rows = smp<short>(in.rows);
-    const int* in_rp = smp<int>(in.rp);
+    const float2* in_hin = sdp<float2, GM>(gb, in.hin);
+    const short* in_row = sdp<short, GM>(gb, in.row);
+    const short* in_col = sdp<short, GM>(gb, in.col);
+    const short* in_rows = sdp<short, GM>(gb, in.rows);
+    const int* in_rp = sdp<int, GM>(gb, in.rp);
     const float2* ct = smp<float2>(K.ct);
     const float2* cdt = smp<float2>(K.cdt);
     float2* L1 = smp<float2>(K.L1);
@@ -270,7 +285,7 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
     const unsigned gmask = ((1u << L2_G) - 1u) << (lane & ~(L2_G - 1));
     const int g = lane & (L2_G - 1);
     const int out_nch = out.nch, out_nc = out.nc;
-    const short* out_cols = smp<short>(out.cols);
+    const short* out_cols = sdp<short, GM>(gb, out.cols);
     for (int ch = 0; ch < out_nch; ++ch) {
         const int c0 = ch * L2_CW;
         const int wc = min(L2_CW, out_nc - c0);
@@ -305,11 +320,11 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
         // ---- stage 2 for the chunk's output cells, L2_G lanes per cell
         {
             const int cs = out.chs[ch], ce = out.chs[ch + 1];
-            const short* out_chl = smp<short>(out.chl);
-            const short* out_row = smp<short>(out.row);
-            const short* out_col = smp<short>(out.col);
-            const short* out_colpos = smp<short>(out.colpos);
-            float2* out_pot = smp<float2>(out.pot);
+            const short* out_chl = sdp<short, GM>(gb, out.chl);
+            const short* out_row = sdp<short, GM>(gb, out.row);
+            const short* out_col = sdp<short, GM>(gb, out.col);
+            const short* out_colpos = sdp<short, GM>(gb, out.colpos);
+            float2* out_pot = sdp<float2, GM>(gb, out.pot);
             // every lane of a group runs the same trip count (the loop index is shared)
             for (int e0 = cs; e0 < ce; e0 += NT / L2_G) {
                 const int e = e0 + (t / L2_G);
@@ -376,10 +391,10 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
                 }
                 if (live && g == 0) {
                     float2 pn;
-                    if (l2_update(tot, shift, Ms, po, smp<float>(out.w)[qo], want_err, K, errs, pn)) {
+                    if (l2_update(tot, shift, Ms, po, sdp<float, GM>(gb, out.w)[qo], want_err, K, errs, pn)) {
                         out_pot[qo] = pn;
-                        const float2 lw = smp<float2>(out.lw)[qo];
-                        smp<float2>(out.hin)[qo] = make_float2(lw.x + pn.x, lw.y + pn.y);
+                        const float2 lw = sdp<float2, GM>(gb, out.lw)[qo];
+                        sdp<float2, GM>(gb, out.hin)[qo] = make_float2(lw.x + pn.x, lw.y + pn.y);
                     } else {
                         atomicOr(range_flag, 1);
                     }
@@ -391,9 +406,15 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
     if (out_nch == 0) __syncthreads();
 }
 
-template <int NT>
+// GM = false: pairs with IC_BIG == 0, everything on chip; a pair that does
+// not fit moves to IC_BIG = 1.  GM = true: pairs with IC_BIG == 1, per-side
+// arrays in the pair's FP64 scratch L64 (gcap bytes); a pair whose arrays
+// exceed it moves to IC_BIG = 2 (the FP64 global-memory kernel), as does any
+// pair whose potentials leave the exact range.  counter[0]: pairs still
+// active; counter[1]: pairs moved to 1; counter[3]: pairs moved to 2.
+template <int NT, bool GM>
 __global__ void __launch_bounds__(NT, (NT <= 256 ? 3 : (NT <= 512 ? 2 : 1)))
-sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int smem_cap, int* big_count, int gbits) {
+sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t gcap, int gbits) {
     constexpr int NW = NT / 32;
     __shared__ L2Side S[2];
     __shared__ float redD[NW], redE[NW];
@@ -402,18 +423,25 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int smem_cap, in
     __shared__ int range_flag, fits;
     const int p = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
     PairPtrs q = pair_ptrs(w, p);
-    if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG]) return;
+    if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG] != (GM ? 1 : 0)) return;
     const int d = w.d, dp = w.dp, nA = q.ic[IC_NA], nB = q.ic[IC_NB];
     l2_compact(q.rpa, d, nullptr, &cnt[0], nullptr, wcnt);
     l2_compact(q.rpb, d, nullptr, &cnt[1], nullptr, wcnt);
     const int nrA = cnt[0], nrB = cnt[1];
-    if (t == 0) fits = l2_need(nA, nB, nrA, nrB, d) <= (size_t)smem_cap;
+    if (t == 0) {
+        if (GM)
+            fits = l2_side_bytes(nA, nB, d) <= gcap && l2_table_bytes(nrA > nrB ? nrA : nrB, d) <= (size_t)smem_cap;
+        else
+            fits = l2_need(nA, nB, nrA, nrB, d) <= (size_t)smem_cap;
+    }
     __syncthreads();
     if (!fits) {
-        if (t == 0) { q.ic[IC_BIG] = 1; atomicAdd(big_count, 1); }
+        if (t == 0) { q.ic[IC_BIG] = GM ? 2 : 1; atomicAdd(&counter[GM ? 3 : 1], 1); atomicAdd(&counter[0], 1); }
         return;
     }
-    // ---- carve shared memory (byte offsets)
+    unsigned char* gb = GM ? reinterpret_cast<unsigned char*>(q.L64) : nullptr;
+    // ---- carve the per-side arrays, then the tables (byte offsets; in the GM
+    // variant the side arrays start at gb and the tables at shared offset 0)
     uint32_t sp = 0;
     auto take = [&](size_t bytes) { const uint32_t r0 = sp; sp += (uint32_t)l2_al(bytes); return r0; };
     const int ns[2] = {nA, nB};
@@ -431,6 +459,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int smem_cap, in
         }
     }
     L2Consts K;
+    if (GM) sp = 0;
     K.ct = take(8 * (size_t)(2 * d - 1));
     K.cdt = take(8 * (size_t)d);
     const int nrmax = nrA > nrB ? nrA : nrB;
@@ -449,13 +478,13 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int smem_cap, in
         for (int s = 0; s < 2; ++s) {
             L2Side& X = S[s];
             const int n = X.n;
-            short* row = smp<short>(X.row);
-            short* col = smp<short>(X.col);
-            float2* xlw = smp<float2>(X.lw);
-            float2* xpot = smp<float2>(X.pot);
-            float2* xhin = smp<float2>(X.hin);
-            float* xw = smp<float>(X.w);
-            int* xrp = smp<int>(X.rp);
+            short* row = sdp<short, GM>(gb, X.row);
+            short* col = sdp<short, GM>(gb, X.col);
+            float2* xlw = sdp<float2, GM>(gb, X.lw);
+            float2* xpot = sdp<float2, GM>(gb, X.pot);
+            float2* xhin = sdp<float2, GM>(gb, X.hin);
+            float* xw = sdp<float, GM>(gb, X.w);
+            int* xrp = sdp<int, GM>(gb, X.rp);
             for (int e = t; e < n; e += NT) {
                 const int c = lists[s][e];
                 const int i = c / dp, j = c - i * dp;
@@ -467,8 +496,8 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int smem_cap, in
                 xw[e] = wt[s][c];
             }
             for (int i = t; i <= d; i += NT) xrp[i] = rps[s][i];
-            l2_compact(rps[s], d, smp<short>(X.rows), &cnt[2], nullptr, wcnt);
-            l2_compact(cps[s], d, smp<short>(X.cols), &cnt[3], smp<short>(X.colpos), wcnt);
+            l2_compact(rps[s], d, sdp<short, GM>(gb, X.rows), &cnt[2], nullptr, wcnt);
+            l2_compact(cps[s], d, sdp<short, GM>(gb, X.cols), &cnt[3], sdp<short, GM>(gb, X.colpos), wcnt);
             if (t == 0) {
                 X.nr = cnt[2]; X.nc = cnt[3]; X.nch = (cnt[3] + L2_CW - 1) / L2_CW;
                 const double wD = q.sc[s == 0 ? SC_AD : SC_BD];
@@ -492,8 +521,8 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int smem_cap, in
     }
     if (t == 0) range_flag = 0;
     __syncthreads();
-    l2_chunks(S[0], wcnt);
-    l2_chunks(S[1], wcnt);
+    l2_chunks<GM>(S[0], wcnt, gb);
+    l2_chunks<GM>(S[1], wcnt, gb);
     K.d = d;
     K.gsc = (float)gsc; K.ginv = (float)(1.0 / gsc);
     K.lim = (float)ldexp(1.0, 21 - gbits);   // |potential| bound keeping every sum of grid words exact
@@ -505,9 +534,9 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int smem_cap, in
     bool moved = false;
     for (int it = 0; it < n_inner; ++it) {
         float errs = 0.f;
-        l2_half<NT>(S[1], S[0], K, false, errs, redD, &range_flag);   // u-update: phi from psi
+        l2_half<NT, GM>(S[1], S[0], K, false, errs, redD, &range_flag, gb);   // u-update: phi from psi
         errs = 0.f;
-        l2_half<NT>(S[0], S[1], K, true, errs, redD, &range_flag);    // v-update: psi from phi, err_t
+        l2_half<NT, GM>(S[0], S[1], K, true, errs, redD, &range_flag, gb);    // v-update: psi from phi, err_t
         errs = warp_sum(errs);
         if (lane == 0) redE[wid] = errs;
         __syncthreads();
@@ -526,7 +555,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int smem_cap, in
         const L2Side& X = S[s];
         double* pot = s == 0 ? q.phi : q.psi;
         const int* list = s == 0 ? q.sa : q.sb;
-        const float2* xpot = smp<float2>(X.pot);
+        const float2* xpot = sdp<float2, GM>(gb, X.pot);
         for (int e = t; e < X.n; e += NT) pot[list[e]] = ((double)xpot[e].x + (double)xpot[e].y) * LN2;
         if (t == 0) pot[w.n - 1] = ((double)X.potD.x + (double)X.potD.y) * LN2;
     }
@@ -535,12 +564,12 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int smem_cap, in
         q.ic[IC_ITERS] = iters;
         if (moved) {
             // the exact-range guard tripped: the FP64 global-memory kernel takes the pair over
-            q.ic[IC_BIG] = 1;
-            atomicAdd(big_count, 1);
-            atomicAdd(active_count, 1);
+            q.ic[IC_BIG] = 2;
+            atomicAdd(&counter[3], 1);
+            atomicAdd(&counter[0], 1);
         } else {
             q.ic[IC_STATUS] = status;
-            if (status == ST_ACTIVE) atomicAdd(active_count, 1);
+            if (status == ST_ACTIVE) atomicAdd(&counter[0], 1);
         }
     }
 }
@@ -588,28 +617,40 @@ size_t sk_lse2_smem_cap() {
     return (size_t)cap - 1024;   // static shared memory of the kernel
 }
 
-template <int NT>
-static cudaError_t launch_lse2(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count, size_t smem,
-                               int gbits, cudaStream_t s) {
+template <int NT, bool GM>
+static cudaError_t launch_lse2(const SkWS& w, SkRun r, int n_inner, int* counter, size_t smem, size_t gcap, int gbits,
+                               cudaStream_t s) {
     static std::atomic<size_t> configured{0};
     const size_t cap = sk_lse2_smem_cap();
     if (configured != cap) {
-        cudaError_t e = cudaFuncSetAttribute(sk_lse2_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+        cudaError_t e = cudaFuncSetAttribute(sk_lse2_kernel<NT, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)cap);
         if (e != cudaSuccess) return e;
         configured = cap;
     }
     if (smem > cap) smem = cap;
-    sk_lse2_kernel<NT><<<w.P, NT, smem, s>>>(w, r, n_inner, active_count, (int)smem, big_count, gbits);
+    sk_lse2_kernel<NT, GM><<<w.P, NT, smem, s>>>(w, r, n_inner, counter, (int)smem, gcap, gbits);
     return cudaGetLastError();
 }
 
-cudaError_t sk_launch_lse2(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count, size_t smem,
-                           int gbits, int threads, cudaStream_t s) {
+cudaError_t sk_launch_lse2(const SkWS& w, SkRun r, int n_inner, int* counter, size_t smem, int gbits, int threads,
+                           cudaStream_t s) {
     if (w.P == 0) return cudaSuccess;
     switch (threads) {
-        case 256: return launch_lse2<256>(w, r, n_inner, active_count, big_count, smem, gbits, s);
-        case 512: return launch_lse2<512>(w, r, n_inner, active_count, big_count, smem, gbits, s);
-        case 1024: return launch_lse2<1024>(w, r, n_inner, active_count, big_count, smem, gbits, s);
+        case 256: return launch_lse2<256, false>(w, r, n_inner, counter, smem, 0, gbits, s);
+        case 512: return launch_lse2<512, false>(w, r, n_inner, counter, smem, 0, gbits, s);
+        case 1024: return launch_lse2<1024, false>(w, r, n_inner, counter, smem, 0, gbits, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Global-memory variant for the pairs with IC_BIG == 1 (512 threads); the
+// side arrays of a pair may use up to `gcap` bytes of its L64 scratch
+// (SIZE_MAX: all of it).
+cudaError_t sk_launch_lse2_gm(const SkWS& w, SkRun r, int n_inner, int* counter, int gbits, size_t gcap,
+                              cudaStream_t s) {
+    if (w.P == 0) return cudaSuccess;
+    const size_t l64 = sizeof(double) * 2 * (size_t)w.dp * w.dp;
+    return launch_lse2<512, true>(w, r, n_inner, counter, l2_table_bytes(w.d, w.d), gcap < l64 ? gcap : l64, gbits,
+                                  s);
 }

@@ -215,12 +215,13 @@ __device__ __forceinline__ HalfArgs v_args(PairPtrs& q, const SkWS& w) {
 }
 
 // Iterations: u-update, then the v-update which also yields err_t.
-__global__ void __launch_bounds__(T_CTA) sk_lse_iter_kernel(SkWS w, SkRun r, int n_inner, int* active_count) {
+__global__ void __launch_bounds__(T_CTA) sk_lse_iter_kernel(SkWS w, SkRun r, int n_inner, int* active_count,
+                                                             int min_big) {
     __shared__ int rows[256], cols[256], nrc[2];
     __shared__ double shd[32];
     const int p = blockIdx.x, t = threadIdx.x;
     PairPtrs q = pair_ptrs(w, p);
-    if (q.ic[IC_STATUS] != ST_ACTIVE || !q.ic[IC_BIG]) return;
+    if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG] < min_big) return;
     const int d = w.d, dp = w.dp;
     const float* chi = w.ctab;             // c_m/gamma, hi / lo
     const float* clo = w.ctab + dp;
@@ -247,9 +248,10 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_iter_kernel(SkWS w, SkRun r, int
     }
 }
 
-cudaError_t sk_launch_lse_iter(const SkWS& w, SkRun r, int n_inner, int* active_count, cudaStream_t s) {
+cudaError_t sk_launch_lse_iter(const SkWS& w, SkRun r, int n_inner, int* active_count, int min_big,
+                               cudaStream_t s) {
     if (w.P == 0) return cudaSuccess;
-    sk_lse_iter_kernel<<<w.P, T_CTA, 0, s>>>(w, r, n_inner, active_count);
+    sk_lse_iter_kernel<<<w.P, T_CTA, 0, s>>>(w, r, n_inner, active_count, min_big < 1 ? 1 : min_big);
     return cudaGetLastError();
 }
 

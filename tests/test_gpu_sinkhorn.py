@@ -88,6 +88,39 @@ def test_small_gamma_fixed_iterations(ctx, d, gamma):
     assert rel.max() <= 1e-6, rel
 
 
+@pytest.mark.parametrize("tier", ["gm", "fp64"])
+def test_kernel_tiers_match_oracle(ctx, tier, monkeypatch):
+    """Every pair forced into the global-memory variant of the base-2 kernel
+    (gm) or into the FP64 global-memory kernel (fp64): same iterates as the
+    oracle after 400 iterations at d=128, gamma=1e-3 (relative cost <= 1e-6)."""
+    monkeypatch.setenv("PD_LSE2_TIER", tier)
+    d, gamma = 128, 1e-3
+    b, t, o = inputs.random_diagrams(4, nmin=50, nmax=500, seed=d)
+    h, _ = oracle.rasterize(b, t, o, d)
+    ref = oracle.sinkhorn_pd_batch(d, gamma, h[0::2], h[1::2], 400, 0.0)
+    g = _solve(ctx, h[0::2], h[1::2], d, gamma, 400, 0.0)
+    assert np.all(g["iters"] == 400)
+    rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
+    assert rel.max() <= 1e-6, rel
+
+
+def test_large_supports_global_variant_vs_fp64_kernel(ctx, monkeypatch):
+    """Pairs of 4000-point diagrams at d=256 have supports too large for shared
+    memory, so the default path runs them in the global-memory base-2 variant;
+    the independent FP64 global-memory kernel gives the same iterates."""
+    d, gamma = 256, 5e-3
+    b, t, o = inputs.random_diagrams(4, nmin=4000, nmax=4000, seed=11)
+    h, _ = oracle.rasterize(b, t, o, d)
+    nnz = (h.reshape(4, -1) > 0).sum(1)
+    assert np.all(nnz[0::2] + nnz[1::2] > 5000)   # beyond the on-chip limit (~4.8k cells at d=256)
+    g = _solve(ctx, h[0::2], h[1::2], d, gamma, 150, 0.0)
+    monkeypatch.setenv("PD_LSE2_TIER", "fp64")
+    r = _solve(ctx, h[0::2], h[1::2], d, gamma, 150, 0.0)
+    assert np.all(g["iters"] == 150) and np.all(r["iters"] == 150)
+    rel = np.abs(g["cost"] - r["cost"]) / r["cost"]
+    assert rel.max() <= 1e-6, rel
+
+
 def test_small_gamma_converged(ctx):
     """Stopping at relative marginal error 1e-6: costs agree with the converged
     oracle within the stopping tolerance's effect."""
