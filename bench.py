@@ -150,6 +150,14 @@ def fp32_peak_tflops(sm_mhz):
     return NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
+# DRAM bytes (read + write) of the base-2 iteration kernel per pair and
+# 64-iteration launch, from one ncu capture (512 pairs of this workload, one
+# launch: 54.56 MB read + 0.34 MB written).  The kernel keeps every pair's
+# state on chip; these bytes are the per-launch load and store of the
+# potentials, weights and support lists.
+LSE2_DRAM_BYTES_PER_PAIR_LAUNCH = (54.556160e6 + 0.337664e6) / 512
+
+
 def mufu_peak_gexp(sm_mhz):
     """Special-function-unit ex2 peak: 152 SMs x 16 ex2/clk x clock, in 1e9/s."""
     return NUM_SMS * MUFU_PER_SM * sm_mhz * 1e6 / 1e9
@@ -295,6 +303,7 @@ def run_ours(args):
     ev = []
     cells = 0.0
     iters_in_iter_kernel = 0
+    pair_launches = 0.0
     lse_terms = 0.0
     outs = None
     torch.cuda.synchronize()
@@ -309,6 +318,7 @@ def run_ours(args):
         it = outs["iters"].cpu().numpy()
         cells += float(it.sum()) * 2 * (d * d + 1)
         iters_in_iter_kernel += int(np.maximum(it - 1, 0).sum())
+        pair_launches += float(np.ceil(it / 64.0).sum())
         lse_terms += float((it * terms).sum())
     torch.cuda.synchronize()
     barrier(ws)
@@ -363,8 +373,12 @@ def run_ours(args):
         bound, unit, kname = "alu", "Gexp/s", "sk_lse2_kernel (on-chip base-2 log-domain separable Sinkhorn)"
         achieved = lse_terms / (iter_ms / 1e3) / 1e9 if iter_ms > 0 else 0.0
         src = f"{pk_kind} sm_max_mhz x 152 SMs x 16 MUFU ex2/clk (one exponential per log-sum-exp term)"
+    traffic = None
+    if precision == api.PD_FP32 and iter_launches:
+        # pair-launches: every pair is loaded once per 64-iteration launch it is active in
+        traffic = LSE2_DRAM_BYTES_PER_PAIR_LAUNCH * pair_launches / iter_launches
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak if peak else None, "traffic": None, "kernel": kname, "peak_source": src,
+            "frac": achieved / peak if peak else None, "traffic": traffic, "kernel": kname, "peak_source": src,
             "launches": iter_launches, "kernel_ms": iter_ms,
             "share_of_step": iter_ms / my_ms if my_ms else None}
     launches = int(sum(n for _, n in prof.values()))
