@@ -189,6 +189,8 @@ size_t pd_carve_ws(char* base, int P, int d, int dp, double gamma, SkWS* w, int*
     t.cia = (int*)take(sizeof(int) * M * P);
     t.cib = (int*)take(sizeof(int) * M * P);
     t.ctab = (float*)take(sizeof(float) * 5 * dp);
+    t.order_buf = (int*)take(sizeof(int) * P);
+    t.order = nullptr;
     *counter = (int*)take(sizeof(int) * 4);
     if (w) *w = t;
     return off;
@@ -255,12 +257,37 @@ static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* r
 // no pair is active.  counter: 4 device ints; hbuf: 4 host ints; c (may be
 // NULL) receives the per-launch profile records.
 static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hbuf, cudaStream_t s) {
-    const int n_inner = 64;
+    cudaError_t e;
+    // Every pair runs to its stop inside one launch (its CTA iterates until
+    // convergence or max_iter), so no round barrier idles the SMs; CTAs are
+    // handed out largest support first, which keeps the long solves from
+    // starting last (makespan).  PD_LSE2_INNER caps the iterations per launch
+    // (tuning).
+    int n_inner = r.max_iter;
+    if (const char* ev = std::getenv("PD_LSE2_INNER")) {
+        const int v = std::atoi(ev);
+        if (v >= 1) n_inner = v;
+    }
+    if (w.P > 1 && w.order_buf) {
+        std::vector<int> ic((size_t)w.P * IC_N);
+        if ((e = cudaMemcpyAsync(ic.data(), w.ic, ic.size() * sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        std::vector<int> ord(w.P);
+        for (int p = 0; p < w.P; ++p) ord[p] = p;
+        auto size = [&](int p) { return ic[(size_t)p * IC_N + IC_NA] + ic[(size_t)p * IC_N + IC_NB]; };
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return size(a) > size(b); });
+        if ((e = cudaMemcpyAsync(w.order_buf, ord.data(), sizeof(int) * w.P, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        w.order = w.order_buf;
+    }
     // a pair can spend one round in each of the two hand-overs between kernels
     const int max_rounds = r.max_iter / n_inner + 4;
     const int gbits = sk_lse2_grid_bits(w.gamma);
     size_t smem = 0;
-    cudaError_t e;
     if (gbits >= 0) {
         if ((e = cudaMemsetAsync(counter + 2, 0, sizeof(int), s)) != cudaSuccess) return e;
         if ((e = sk_launch_lse2_need(w, counter + 2, s)) != cudaSuccess) return e;

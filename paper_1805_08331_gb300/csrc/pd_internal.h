@@ -60,6 +60,8 @@ struct SkWS {
     int *rpa, *rpb, *cpa, *cpb;     // [P][dp+1] row / column pointers of the support lists
     int *cia, *cib;                 // [P][dp*dp] row indices of the column-major support lists
     float* ctab;                    // [2*dp] hi / lo FP32 split of c_m/gamma, m = 0..dp-1
+    int* order_buf;                 // [P] launch order of the pairs (filled by the host)
+    const int* order;               // NULL: CTA b runs pair b; else CTA b runs pair order[b]
     // inputs: integer histograms (histA/massA, histB/massB) or, when wA / wB is
     // non-NULL, real-valued weights [N][d*d] for that side (its mass is their sum)
     const uint32_t *histA, *histB, *massA, *massB;

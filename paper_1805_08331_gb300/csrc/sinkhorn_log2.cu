@@ -421,7 +421,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     __shared__ int wcnt[NW];
     __shared__ int cnt[4];
     __shared__ int range_flag, fits;
-    const int p = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int p = w.order ? w.order[blockIdx.x] : blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
     PairPtrs q = pair_ptrs(w, p);
     if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG] != (GM ? 1 : 0)) return;
     const int d = w.d, dp = w.dp, nA = q.ic[IC_NA], nB = q.ic[IC_NB];
