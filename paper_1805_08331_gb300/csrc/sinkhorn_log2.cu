@@ -36,7 +36,7 @@
 #include <cmath>
 
 #define L2_CW 32          // output columns per chunk
-#define L2_MAXCH 8        // chunks per side (d <= 256)
+#define L2_MAXCH (256 / L2_CW)   // chunks per side (d <= 256)
 #define L2_MAXW 32        // warps per CTA at most
 
 // Dynamic shared memory of the kernel; the per-side arrays are addressed by
@@ -146,33 +146,34 @@ static __device__ void l2_compact(const int* __restrict__ ptr, int d, short* out
     __syncthreads();
 }
 
-// Group the output cells of a side by chunk of 32 non-empty columns (warp c
-// builds chunk c; the order inside a chunk stays row-major).
+// Group the output cells of a side by chunk of L2_CW non-empty columns (warp w
+// builds chunks w, w + warps, ...; the order inside a chunk stays row-major).
 template <bool GM>
 static __device__ void l2_chunks(L2Side& s, int* warp_cnt, unsigned char* gb) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nch = s.nch, n = s.n;
     const short* col = sdp<short, GM>(gb, s.col);
     const short* colpos = sdp<short, GM>(gb, s.colpos);
     short* chl = sdp<short, GM>(gb, s.chl);
-    if (wid < nch) {
+    // counts per chunk (warp_cnt holds L2_MAXCH entries)
+    for (int c = wid; c < nch; c += nw) {
         int cnt = 0;
         for (int b = 0; b < n; b += 32) {
             const int e = b + lane;
-            const bool f = e < n && (colpos[col[e]] >> 5) == wid;
+            const bool f = e < n && colpos[col[e]] / L2_CW == c;
             cnt += __popc(__ballot_sync(0xffffffffu, f));
         }
-        if (lane == 0) warp_cnt[wid] = cnt;
+        if (lane == 0) warp_cnt[c] = cnt;
     }
     __syncthreads();
-    if (wid < nch) {
+    for (int c = wid; c < nch; c += nw) {
         int off = 0;
-        for (int q = 0; q < wid; ++q) off += warp_cnt[q];
-        if (lane == 0) s.chs[wid] = (short)off;
-        if (wid == nch - 1 && lane == 0) s.chs[nch] = (short)(off + warp_cnt[wid]);
+        for (int q = 0; q < c; ++q) off += warp_cnt[q];
+        if (lane == 0) s.chs[c] = (short)off;
+        if (c == nch - 1 && lane == 0) s.chs[nch] = (short)(off + warp_cnt[c]);
         for (int b = 0; b < n; b += 32) {
             const int e = b + lane;
-            const bool f = e < n && (colpos[col[e]] >> 5) == wid;
+            const bool f = e < n && colpos[col[e]] / L2_CW == c;
             const unsigned bal = __ballot_sync(0xffffffffu, f);
             if (f) chl[off + __popc(bal & ((1u << lane) - 1u))] = (short)e;
             off += __popc(bal);
@@ -418,7 +419,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     constexpr int NW = NT / 32;
     __shared__ L2Side S[2];
     __shared__ float redD[NW], redE[NW];
-    __shared__ int wcnt[NW];
+    __shared__ int wcnt[NW > L2_MAXCH ? NW : L2_MAXCH];
     __shared__ int cnt[4];
     __shared__ int range_flag, fits;
     const int p = w.order ? w.order[blockIdx.x] : blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
