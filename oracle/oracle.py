@@ -55,6 +55,8 @@ def _load():
             lib.or_kmeans.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_uint64, _i32p, _dp, _dp]
+            lib.or_round_bound.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                           _dp, _dp]
             lib.or_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -117,6 +119,19 @@ def sinkhorn_w(d, gamma, a, b, max_iter, tol, g_init=None):
     if rc != 0:
         raise ValueError("or_sinkhorn_w: invalid weights (negative or unequal total mass)")
     return dict(cost=c.value, f=f, g=g, rmarg=rm, cmarg=cm, iters=it.value, err=er.value)
+
+
+def round_bound(d, gamma, a, b, f, g):
+    """Rounded plan of P(f, g) onto Pi(a, b) and its cost <R, C> (Prop. 3's
+    upper bound), on the dense matrices.  a, b, f, g: length d*d+1."""
+    n = d * d + 1
+    arr = [np.ascontiguousarray(x, dtype=np.float64) for x in (a, b, f, g)]
+    assert all(x.shape == (n,) for x in arr)
+    out = [ctypes.c_double() for _ in range(5)]
+    rc = _load().or_round_bound(d, gamma, *[_ptr(x, _dp) for x in arr], *[ctypes.byref(o) for o in out])
+    if rc != 0:
+        raise ValueError("or_round_bound: d > 64")
+    return dict(upper=out[0].value, row_dev=out[1].value, col_dev=out[2].value, er=out[3].value, ec=out[4].value)
 
 
 def sinkhorn_pd(d, gamma, hA, hB, max_iter, tol, g_init=None):

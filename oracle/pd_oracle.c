@@ -31,6 +31,10 @@
  *                        update.
  *   or_kmeans         -- Sec. 5 k-means: assignment by Alg. 1 cost, centroid
  *                        update by Alg. 2.
+ *   or_round_bound    -- the rounding algorithm of the supplementary (Altschuler
+ *                        et al.) applied to the plan P(f, g), written out on the
+ *                        explicit dense matrices, and the transport cost of the
+ *                        rounded plan R, <R, C> (the upper bound of Prop. 3).
  *
  * Conventions (shared with the CUDA library by specification only):
  *   - Grid cell (i,j): i = birth index (row), j = death index (column), both in
@@ -409,4 +413,92 @@ int or_num_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* ---------------------------------------------------------------------- */
+/* Rounding (supplementary, algorithm of Altschuler et al.) of the plan
+ * P_xy = a_x b_y exp((f_x + g_y - C_xy)/gamma) onto Pi(a, b), and <R, C>.
+ * Literal, on the dense (d^2+1) x (d^2+1) matrices (no separability):
+ *   X = min(a / r(P), 1), P' = diag(X) P, Y = min(b / c(P'), 1),
+ *   P'' = P' diag(Y), e_r = a - r(P''), e_c = b - c(P''),
+ *   R = P'' + e_r e_c^T / ||e_c||_1.
+ * A zero row or column sum of P gives a factor 1 (min(+inf, 1)).
+ * Outputs: *upper = <R, C>; *row_dev, *col_dev = max |r(R) - a|, max |c(R) - b|
+ * (R has the marginals (a, b) exactly, up to rounding); *er, *ec = ||e_r||_1,
+ * ||e_c||_1.  Returns -1 when d > 64 (the dense plan would not fit). */
+int or_round_bound(int d, double gamma, const double* a, const double* b, const double* f, const double* g,
+                   double* upper, double* row_dev, double* col_dev, double* er, double* ec) {
+    if (d > 64) return -1;
+    const int n = d * d + 1;
+    double* P = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* rs = (double*)calloc(n, sizeof(double));
+    double* cs = (double*)calloc(n, sizeof(double));
+    double* X = (double*)malloc(sizeof(double) * n);
+    double* Y = (double*)malloc(sizeof(double) * n);
+    double* e_r = (double*)malloc(sizeof(double) * n);
+    double* e_c = (double*)malloc(sizeof(double) * n);
+    for (int x = 0; x < n; ++x)
+        for (int y = 0; y < n; ++y) {
+            double v = 0.0;
+            if (a[x] > 0 && b[y] > 0) v = exp(log(a[x]) + log(b[y]) + (f[x] + g[y] - or_cost(d, x, y)) / gamma);
+            P[(size_t)x * n + y] = v;
+        }
+    /* X, then P' = diag(X) P */
+    for (int x = 0; x < n; ++x) {
+        or_ksum k = {0, 0};
+        for (int y = 0; y < n; ++y) ks_add(&k, P[(size_t)x * n + y]);
+        rs[x] = ks_val(&k);
+        X[x] = rs[x] > 0 ? fmin(a[x] / rs[x], 1.0) : 1.0;
+        for (int y = 0; y < n; ++y) P[(size_t)x * n + y] *= X[x];
+    }
+    /* Y, then P'' = P' diag(Y) */
+    for (int y = 0; y < n; ++y) {
+        or_ksum k = {0, 0};
+        for (int x = 0; x < n; ++x) ks_add(&k, P[(size_t)x * n + y]);
+        cs[y] = ks_val(&k);
+        Y[y] = cs[y] > 0 ? fmin(b[y] / cs[y], 1.0) : 1.0;
+    }
+    for (int x = 0; x < n; ++x)
+        for (int y = 0; y < n; ++y) P[(size_t)x * n + y] *= Y[y];
+    /* marginal errors of P'' */
+    or_ksum ner = {0, 0}, nec = {0, 0};
+    for (int x = 0; x < n; ++x) {
+        or_ksum k = {0, 0};
+        for (int y = 0; y < n; ++y) ks_add(&k, P[(size_t)x * n + y]);
+        e_r[x] = a[x] - ks_val(&k);
+        ks_add(&ner, e_r[x]);
+    }
+    for (int y = 0; y < n; ++y) {
+        or_ksum k = {0, 0};
+        for (int x = 0; x < n; ++x) ks_add(&k, P[(size_t)x * n + y]);
+        e_c[y] = b[y] - ks_val(&k);
+        ks_add(&nec, e_c[y]);
+    }
+    const double ecn = ks_val(&nec);
+    /* R = P'' + e_r e_c^T / ||e_c||_1, its cost and its marginals */
+    if (ecn > 0)
+        for (int x = 0; x < n; ++x)
+            for (int y = 0; y < n; ++y) P[(size_t)x * n + y] += e_r[x] * e_c[y] / ecn;
+    or_ksum ck = {0, 0};
+    double rd = 0, cd = 0;
+    for (int x = 0; x < n; ++x) {
+        or_ksum k = {0, 0};
+        for (int y = 0; y < n; ++y) {
+            ks_add(&ck, P[(size_t)x * n + y] * or_cost(d, x, y));
+            ks_add(&k, P[(size_t)x * n + y]);
+        }
+        rd = fmax(rd, fabs(ks_val(&k) - a[x]));
+    }
+    for (int y = 0; y < n; ++y) {
+        or_ksum k = {0, 0};
+        for (int x = 0; x < n; ++x) ks_add(&k, P[(size_t)x * n + y]);
+        cd = fmax(cd, fabs(ks_val(&k) - b[y]));
+    }
+    if (upper) *upper = ks_val(&ck);
+    if (row_dev) *row_dev = rd;
+    if (col_dev) *col_dev = cd;
+    if (er) *er = ks_val(&ner);
+    if (ec) *ec = ecn;
+    free(P); free(rs); free(cs); free(X); free(Y); free(e_r); free(e_c);
+    return 0;
 }

@@ -360,3 +360,45 @@ def test_kmeans_best_run_recovers_modes():
     best = min(runs, key=lambda r: r[0])[1]
     pairs = set(zip(lab.tolist(), best.tolist()))
     assert len(pairs) == 3 and len({p[1] for p in pairs}) == 3
+
+
+# --------------------------------------------------------------------------- Prop. 3 rounding upper bound
+@pytest.mark.parametrize("T", [2, 10, 60, None])
+def test_round_bound_plan_is_feasible_and_closes(T):
+    """The rounded plan R has the marginals (a, b) exactly at any iterate, and
+    once the iterates converge the correction vanishes: <R, C> -> <P, C>."""
+    d, gamma = 16, 1e-2
+    b, t, o = inputs.random_diagrams(2, nmin=12, nmax=12, seed=7)
+    h, _ = oracle.rasterize(b, t, o, d)
+    a, bb = oracle.augment(h[0], h[1])
+    r = oracle.sinkhorn_w(d, gamma, a, bb, T, 0.0) if T else oracle.sinkhorn_w(d, gamma, a, bb, 200000, 1e-13)
+    rb = oracle.round_bound(d, gamma, a, bb, r["f"], r["g"])
+    assert rb["row_dev"] <= 1e-12 * a.sum() and rb["col_dev"] <= 1e-12 * a.sum()
+    assert rb["er"] >= -1e-12 and rb["ec"] >= -1e-12
+    assert abs(rb["er"] - rb["ec"]) <= 1e-10 * a.sum()        # both sides lose the same mass
+    if T is None:   # converged (marginal error 1e-13)
+        assert rb["ec"] <= 1e-9 * a.sum()
+        assert rb["upper"] == pytest.approx(r["cost"], rel=1e-9)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_round_bound_is_above_exact_transport(seed):
+    """R is a feasible transport plan, so <R, C> >= the exact optimal cost,
+    which for rasterised diagrams is d_2^2 of the snapped points (Prop. 1),
+    computed here by assignment; at early iterates the plan P itself can be far
+    below it (not feasible), the rounded one never is."""
+    d = 16
+    b, t, o = inputs.random_diagrams(2, nmin=6, nmax=9, seed=seed, log_uniform=False)
+    h, _ = oracle.rasterize(b, t, o, d)
+    X = _snapped_points(b[o[0]:o[1]], t[o[0]:o[1]], d)
+    Y = _snapped_points(b[o[1]:o[2]], t[o[1]:o[2]], d)
+    L, _ = _diag_matching_sq(X, Y)
+    a, bb = oracle.augment(h[0], h[1])
+    below = 0
+    for gamma in (1e-2, 1e-3):
+        for T in (1, 3, 20, 400):
+            r = oracle.sinkhorn_w(d, gamma, a, bb, T, 0.0)
+            rb = oracle.round_bound(d, gamma, a, bb, r["f"], r["g"])
+            assert rb["upper"] >= L - 1e-12, (gamma, T, rb["upper"], L)
+            below += r["cost"] < L - 1e-9
+    assert below > 0   # the check has teeth: some unrounded plans undercut the optimum
