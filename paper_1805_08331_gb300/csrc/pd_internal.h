@@ -15,6 +15,7 @@ enum {
     SC_TOTAL,    // total mass |A| + |B|
     SC_ERR,      // last relative marginal error
     SC_TAU,      // residual threshold that triggers the next absorption
+    SC_CORR,     // Prop. 3: rank-one correction term of the rounded plan's cost
     SC_N
 };
 // Per-pair int slots.
@@ -109,6 +110,12 @@ cudaError_t sk_launch_lse_finalize(const SkWS& w, double* cost, float* row_marg,
 cudaError_t sk_launch_lse_finalize_list(const SkWS& w, double* cost, float* row_marg, float* col_marg, double* f,
                                         double* g, int32_t* iters, float* err, int32_t* status, int pso,
                                         const int* plist, int np, cudaStream_t s);
+// Prop. 3 upper bound (sinkhorn_lse.cu): replaces every usable pair's potentials
+// by those of the rescaled plan P2 of the rounding and stores the rank-one term
+// in sc[SC_CORR]; the finalize cost of the new potentials plus that term is
+// <R, C> (sk_launch_add_corr adds it).
+cudaError_t sk_launch_round_bound(const SkWS& w, cudaStream_t s);
+cudaError_t sk_launch_add_corr(const SkWS& w, double* upper, cudaStream_t s);
 // workspace helpers (api.cu)
 size_t pd_carve_ws(char* base, int P, int d, int dp, double gamma, SkWS* w, int** counter);
 cudaError_t pd_upload_cost_tables(const SkWS& w, double gamma, cudaStream_t s);

@@ -769,3 +769,128 @@ cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_
     sk_lse_smem_kernel<<<w.P, LSE_SM_THREADS, cap, s>>>(w, r, n_inner, active_count, cap, big_count);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Prop. 3: cost of the rounded plan R (the rounding algorithm of the
+// supplementary, after Altschuler et al.) from the final potentials, without
+// forming any plan.  Write phi_u(psi) = -log(K (b e^psi)) for the value the
+// u-update would give and psi_v(phi) = -log(K^T (a e^phi)) for the v-update.
+// The row marginal of P is r(P) = a e^(phi - phi_u(psi)), so
+//   X = min(a / r(P), 1)          <=>  phi1 = min(phi, phi_u(psi)),
+//   c(diag(X) P) = b e^(psi - psi_v(phi1)),
+//   Y = min(b / c(diag(X) P), 1)  <=>  psi2 = min(psi, psi_v(phi1)),
+//   e_c = b - c(P2) = b max(0, 1 - e^(psi - psi_v(phi1))),
+//   e_r = a - r(P2) = a (1 - e^(phi1 - phi_u(psi2))),
+// with P2 = diag(X) P diag(Y), and <R, C> = <P2, C> + e_r^T C e_c / |e_c|_1.
+// <P2, C> is Prop. 2 with the potentials (phi1, psi2), which this kernel
+// leaves in place of (phi, psi).  The rank-one term uses the separable cost:
+// sum_{x,y} e_r(x) e_c(y) C(x,y) = sum_{ik} c_ik ER_i EC_k + sum_{jl} c_jl
+// ER'_j EC'_l (row / column sums of the grid parts) + e_c(Delta) <e_r, cD> +
+// e_r(Delta) <e_c, cD>.
+__global__ void __launch_bounds__(T_CTA) sk_round_bound_kernel(SkWS w) {
+    __shared__ int rows[256], cols[256], nrc[2];
+    __shared__ double shd[32];
+    __shared__ double sums[4][256];   // e_r row sums, e_r column sums, e_c row sums, e_c column sums
+    __shared__ double dval[2];
+    const int p = blockIdx.x, t = threadIdx.x;
+    PairPtrs q = pair_ptrs(w, p);
+    const int st = q.ic[IC_STATUS];
+    if (t == 0) q.sc[SC_CORR] = 0.0;
+    if (!((st == ST_CONVERGED || st == ST_MAXITER) && q.sc[SC_TOTAL] > 0)) return;
+    const int d = w.d, dp = w.dp, n1 = w.n - 1, na = q.ic[IC_NA], nb = q.ic[IC_NB];
+    const float* chi = w.ctab;
+    const float* clo = w.ctab + dp;
+    const float* chi2 = w.ctab + 2 * dp;
+    const float* clo2 = w.ctab + 3 * dp;
+    double* S1 = q.L64;                       // [dp*dp] u-side values by padded cell
+    double* S2 = q.L64 + (size_t)dp * dp;     // [dp*dp] v-side values
+    const double aD = q.sc[SC_AD], bD = q.sc[SC_BD];
+    for (int i = t; i < 4 * 256; i += blockDim.x) (&sums[0][0])[i] = 0.0;
+    // ---- phi_u(psi), then phi1 = min(phi, phi_u(psi))
+    {
+        HalfArgs ua = u_args(q, w);
+        ua.pout = S1;
+        ua.pD_out = &dval[0];
+        if (t == 0) dval[0] = q.phi[n1];
+        __syncthreads();
+        lse_halfstep(ua, chi, clo, chi2, clo2, d, dp, rows, cols, nrc, false, shd);
+        for (int e = t; e < na; e += blockDim.x) {
+            const int c = q.sa[e];
+            q.phi[c] = fmin(q.phi[c], S1[c]);
+        }
+        if (t == 0 && aD > 0) q.phi[n1] = fmin(q.phi[n1], dval[0]);
+        __syncthreads();
+    }
+    // ---- psi_v(phi1), e_c, then psi2 = min(psi, psi_v(phi1))
+    double ec_sum = 0.0, ec_cd = 0.0, ecD = 0.0;
+    {
+        HalfArgs va = v_args(q, w);
+        va.pout = S2;
+        va.pD_out = &dval[1];
+        if (t == 0) dval[1] = q.psi[n1];
+        __syncthreads();
+        lse_halfstep(va, chi, clo, chi2, clo2, d, dp, rows, cols, nrc, false, shd);
+        for (int e = t; e < nb; e += blockDim.x) {
+            const int c = q.sb[e], k = c / dp, l = c % dp;
+            const double ec = exp(q.lb[c]) * fmax(0.0, -expm1(q.psi[c] - S2[c]));
+            ec_sum += ec;
+            ec_cd += ec * pd_cdiag(k, l, d);
+            atomicAdd(&sums[2][k], ec);
+            atomicAdd(&sums[3][l], ec);
+            q.psi[c] = fmin(q.psi[c], S2[c]);
+        }
+        if (bD > 0) ecD = bD * fmax(0.0, -expm1(q.psi[n1] - dval[1]));
+        __syncthreads();
+        if (t == 0 && bD > 0) q.psi[n1] = fmin(q.psi[n1], dval[1]);
+        __syncthreads();
+    }
+    // ---- phi_u(psi2), e_r
+    double er_cd = 0.0, erD = 0.0;
+    {
+        HalfArgs ua = u_args(q, w);
+        ua.pout = S1;
+        ua.pD_out = &dval[0];
+        __syncthreads();
+        lse_halfstep(ua, chi, clo, chi2, clo2, d, dp, rows, cols, nrc, false, shd);
+        for (int e = t; e < na; e += blockDim.x) {
+            const int c = q.sa[e], i = c / dp, j = c % dp;
+            const double er = exp(q.la[c]) * fmax(0.0, -expm1(q.phi[c] - S1[c]));
+            er_cd += er * pd_cdiag(i, j, d);
+            atomicAdd(&sums[0][i], er);
+            atomicAdd(&sums[1][j], er);
+        }
+        if (aD > 0) erD = aD * fmax(0.0, -expm1(q.phi[n1] - dval[0]));
+        __syncthreads();
+    }
+    // ---- rank-one term
+    double bil = 0.0;
+    for (int e = t; e < d * d; e += blockDim.x) {
+        const int i = e / d, k = e % d;
+        bil += pd_c1(i, k, d) * (sums[0][i] * sums[2][k] + sums[1][i] * sums[3][k]);
+    }
+    bil = block_sum(bil, shd);
+    ec_sum = block_sum(ec_sum, shd);
+    ec_cd = block_sum(ec_cd, shd);
+    er_cd = block_sum(er_cd, shd);
+    if (t == 0) {
+        const double ec_tot = ec_sum + ecD;
+        const double num = bil + ecD * er_cd + erD * ec_cd;
+        q.sc[SC_CORR] = ec_tot > 0 ? num / ec_tot : 0.0;
+    }
+}
+
+__global__ void sk_add_corr_kernel(SkWS w, double* __restrict__ upper) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < w.P) upper[p] += w.sc[(size_t)p * SC_N + SC_CORR];
+}
+
+cudaError_t sk_launch_round_bound(const SkWS& w, cudaStream_t s) {
+    if (w.P == 0) return cudaSuccess;
+    sk_round_bound_kernel<<<w.P, T_CTA, 0, s>>>(w);
+    return cudaGetLastError();
+}
+cudaError_t sk_launch_add_corr(const SkWS& w, double* upper, cudaStream_t s) {
+    if (w.P == 0) return cudaSuccess;
+    sk_add_corr_kernel<<<(w.P + 255) / 256, 256, 0, s>>>(w, upper);
+    return cudaGetLastError();
+}

@@ -69,3 +69,29 @@ def test_fullsize_sampled_pairs_match_oracle(solved):
             assert rel <= 1e-6, (p, rel)          # the same iterate on both sides
         else:
             assert rel <= 5e-6, (p, rel, r["iters"][p], ref["iters"][k])
+
+
+def test_fullsize_upper_bound_within_rounding_distance(solved):
+    """Prop. 3 on the full batch: the rounded plan R differs from P by at most
+    2 (|r(P) - a|_1 + |c(P) - b|_1) in l1 (the rounding lemma of the
+    supplementary), and C <= 2 on the grid, so |<R,C> - <P,C>| is at most
+    4 x the plan's marginal error in mass units, for every pair."""
+    h, r = solved
+    api.load(build_if_missing=True)
+    ctx = api.Context(0)
+    hist = torch.from_numpy(h.reshape(2 * P, D, D).view(np.int32)).cuda()
+    mass = torch.from_numpy(h.reshape(2 * P, -1).sum(1).astype(np.uint32).view(np.int32)).cuda()
+    pairs = torch.arange(2 * P, dtype=torch.int32, device="cuda").view(P, 2).contiguous()
+    prm = api.pd_sinkhorn_default_params(GAMMA, D, max_iter=MAX_ITER, tol=TOL)
+    u = api.pd_sinkhorn_upper_bound(ctx, hist, mass, hist, mass, prm, pairs=pairs)
+    torch.cuda.synchronize()
+    cost, upper = u["cost"].cpu().numpy(), u["upper"].cpu().numpy()
+    ctx.close()
+    assert np.array_equal(u["iters"].cpu().numpy(), r["iters"])
+    nA = h[0::2].reshape(P, -1).sum(1).astype(np.float64)
+    nB = h[1::2].reshape(P, -1).sum(1).astype(np.float64)
+    a = np.concatenate([h[0::2].reshape(P, -1).astype(np.float64), nB[:, None]], 1)
+    b = np.concatenate([h[1::2].reshape(P, -1).astype(np.float64), nA[:, None]], 1)
+    dev_l1 = np.abs(r["row_marg"] - a).sum(1) + np.abs(r["col_marg"] - b).sum(1)
+    assert np.all(np.isfinite(upper))
+    assert np.all(np.abs(upper - cost) <= 4.0 * dev_l1 + 1e-6 * cost + 1e-9)
