@@ -97,6 +97,10 @@ typedef struct {
     double rel_log_thresh; /* a term counts as relevant to an output when it is within exp(rel_log_thresh)
                               of the output's sum; the absorbed representation keeps every relevant
                               term in range (>= 0: default, -21 for PD_FP32 and -14 for PD_BF16) */
+    int eps_stages;    /* PD_FP32: gamma-continuation (epsilon-scaling) stages before the target gamma:
+                          stage k = eps_stages..1 iterates at gamma * 4^k until err <= max(tol, 1e-4),
+                          the potentials f, g carried over; then gamma itself to tol.  The result is the
+                          same fixed point; iters counts all stages.  0 (default) = off */
 } pd_sinkhorn_params;
 
 /* Fill *p with defaults for (gamma, d): max_iter 20000, tol 1e-6, PD_FP32,

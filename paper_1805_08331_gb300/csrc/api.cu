@@ -155,6 +155,7 @@ extern "C" void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, 
     p->absorb_tau = 20.0;
     p->absorb_every = 64;
     p->rel_log_thresh = 0.0;
+    p->eps_stages = 0;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -216,13 +217,14 @@ cudaError_t pd_upload_cost_tables(const SkWS& w, double gamma, cudaStream_t s) {
 }
 
 static SkRun make_run(const pd_sinkhorn_params* prm) {
-    SkRun r;
+    SkRun r{};
     r.max_iter = prm->max_iter;
     r.tol = prm->tol;
     r.tau = prm->absorb_tau > 0 ? prm->absorb_tau : 20.0;
     r.absorb_every = prm->absorb_every > 0 ? prm->absorb_every : 64;
     r.rel_thresh = prm->rel_log_thresh < 0 ? prm->rel_log_thresh : (prm->precision == PD_BF16 ? -14.0 : -21.0);
     r.pot_support_only = 0;
+    r.eps_stages = (prm->precision == PD_FP32 && prm->eps_stages > 0) ? std::min(prm->eps_stages, 16) : 0;
     return r;
 }
 
@@ -352,6 +354,25 @@ static pd_status lse_solve(pd_ctx* c, SkWS& w, SkRun r, const double* g_init, do
                            float* col_marg, double* f, double* g, int32_t* iters, float* err, int32_t* status,
                            int* counter, cudaStream_t s) {
     { ProfScope ps(c, PD_K_SETUP, s); CUDA_TRY(c, sk_launch_setup(w, g_init, s)); }
+    if (r.eps_stages > 0) {
+        // gamma-continuation: stages at gamma * 4^k, k = eps_stages..1, each to
+        // err <= max(tol, 1e-4), carrying f and g (phi = f / gamma is rescaled)
+        const double g_target = w.gamma;
+        double g_prev = g_target;
+        for (int k = r.eps_stages; k >= 1; --k) {
+            const double gk = g_target * std::ldexp(1.0, 2 * k);
+            CUDA_TRY(c, sk_launch_regamma(w, g_prev / gk, r.max_iter, s));
+            w.gamma = gk;
+            CUDA_TRY(c, pd_upload_cost_tables(w, gk, s));
+            SkRun rk = r;
+            rk.tol = std::max(r.tol, 1e-4);
+            CUDA_TRY(c, lse_rounds(c, w, rk, counter, c->hflag, s));
+            g_prev = gk;
+        }
+        CUDA_TRY(c, sk_launch_regamma(w, g_prev / g_target, r.max_iter, s));
+        w.gamma = g_target;
+        CUDA_TRY(c, pd_upload_cost_tables(w, g_target, s));
+    }
     return lse_iterate(c, w, r, cost, row_marg, col_marg, f, g, iters, err, status, counter, s);
 }
 
@@ -724,7 +745,7 @@ extern "C" pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint
     }
     if (cudaMemcpyAsync(w.ctab, tab, sizeof(float) * 5 * dp, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return PD_ERR_CUDA;
-    SkRun r;
+    SkRun r{};
     r.max_iter = prm->max_iter;
     r.tol = prm->tol;
     r.tau = 20.0;

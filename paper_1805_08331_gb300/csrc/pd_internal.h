@@ -81,9 +81,14 @@ struct SkRun {
     int absorb_every;
     double rel_thresh;   // relevance threshold (log) for the intermediate fits
     int pot_support_only; // finalize: potentials on the supports and Delta only
+    int eps_stages;       // gamma-continuation stages before the target gamma (PD_FP32)
 };
 
 cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s);
+// gamma-continuation step: potentials/gamma scaled by `ratio` (old gamma / new
+// gamma, f unchanged) and every pair that stopped at the previous gamma (and is
+// below max_iter) made active again
+cudaError_t sk_launch_regamma(const SkWS& w, double ratio, int max_iter, cudaStream_t s);
 cudaError_t sk_launch_setup_list(const SkWS& w, const double* g_init, const int* plist, int np, cudaStream_t s);
 cudaError_t sk_launch_logstep(const SkWS& w, SkRun r, cudaStream_t s);
 cudaError_t sk_launch_absorb(const SkWS& w, SkRun r, cudaStream_t s);

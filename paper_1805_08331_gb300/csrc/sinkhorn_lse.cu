@@ -894,3 +894,32 @@ cudaError_t sk_launch_add_corr(const SkWS& w, double* upper, cudaStream_t s) {
     sk_add_corr_kernel<<<(w.P + 255) / 256, 256, 0, s>>>(w, upper);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// gamma-continuation step (see sk_launch_regamma): phi, psi hold f/gamma and
+// g/gamma; a new gamma keeps f and g, so both scale by old/new.  Pairs that
+// stopped (converged or at max_iter of the stage) are made active again unless
+// they are invalid, out of range, have no mass, or used up max_iter.
+__global__ void sk_regamma_kernel(SkWS w, double ratio, int max_iter) {
+    const int p = blockIdx.x;
+    PairPtrs q = pair_ptrs(w, p);
+    const int st = q.ic[IC_STATUS];
+    if (st == ST_INVALID || st == ST_RANGE || !(q.sc[SC_TOTAL] > 0)) return;
+    const int na = q.ic[IC_NA], nb = q.ic[IC_NB];
+    for (int e = threadIdx.x; e < na; e += blockDim.x) q.phi[q.sa[e]] *= ratio;
+    for (int e = threadIdx.x; e < nb; e += blockDim.x) q.psi[q.sb[e]] *= ratio;
+    if (threadIdx.x == 0) {
+        q.phi[w.n - 1] *= ratio;
+        q.psi[w.n - 1] *= ratio;
+        if (q.ic[IC_ITERS] < max_iter) {
+            q.ic[IC_STATUS] = ST_ACTIVE;
+            q.sc[SC_ERR] = INFINITY;
+        }
+    }
+}
+
+cudaError_t sk_launch_regamma(const SkWS& w, double ratio, int max_iter, cudaStream_t s) {
+    if (w.P == 0) return cudaSuccess;
+    sk_regamma_kernel<<<w.P, 128, 0, s>>>(w, ratio, max_iter);
+    return cudaGetLastError();
+}
