@@ -57,6 +57,7 @@ def _load():
                                       ctypes.c_double, ctypes.c_uint64, _i32p, _dp, _dp]
             lib.or_round_bound.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                            _dp, _dp]
+            lib.or_ctransform_bound.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp]
             lib.or_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -132,6 +133,16 @@ def round_bound(d, gamma, a, b, f, g):
     if rc != 0:
         raise ValueError("or_round_bound: d > 64")
     return dict(upper=out[0].value, row_dev=out[1].value, col_dev=out[2].value, er=out[3].value, ec=out[4].value)
+
+
+def ctransform_bound(d, gamma, a, b, f):
+    """Lower bound m_t = <alpha^cc, a> + <alpha^c, b> with alpha = f + gamma log a."""
+    n = d * d + 1
+    arr = [np.ascontiguousarray(x, dtype=np.float64) for x in (a, b, f)]
+    assert all(x.shape == (n,) for x in arr)
+    out = ctypes.c_double()
+    _load().or_ctransform_bound(d, gamma, *[_ptr(x, _dp) for x in arr], ctypes.byref(out))
+    return out.value
 
 
 def sinkhorn_pd(d, gamma, hA, hB, max_iter, tol, g_init=None):

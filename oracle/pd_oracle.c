@@ -35,6 +35,9 @@
  *                        et al.) applied to the plan P(f, g), written out on the
  *                        explicit dense matrices, and the transport cost of the
  *                        rounded plan R, <R, C> (the upper bound of Prop. 3).
+ *   or_ctransform_bound -- the lower bound m_t of Sec. 3 "Upper and Lower
+ *                        Bounds" from the C- and C^T-transforms of alpha =
+ *                        gamma log u, by plain minimisation over the supports.
  *
  * Conventions (shared with the CUDA library by specification only):
  *   - Grid cell (i,j): i = birth index (row), j = death index (column), both in
@@ -500,5 +503,41 @@ int or_round_bound(int d, double gamma, const double* a, const double* b, const 
     if (er) *er = ks_val(&ner);
     if (ec) *ec = ecn;
     free(P); free(rs); free(cs); free(X); free(Y); free(e_r); free(e_c);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Lower bound m_t of Sec. 3 "Upper and Lower Bounds": from the first dual
+ * variable alpha = gamma log u (u = a exp(f/gamma), so alpha = f + gamma log a
+ * on the support of a), its C-transform and the C^T-transform of that,
+ *   alpha^c(y)   = min_{x in supp a} C(x,y) - alpha(x),     y in supp b,
+ *   alpha^cc(x)  = min_{y in supp b} C(x,y) - alpha^c(y),   x in supp a,
+ * (the transforms are infima: the pair (alpha^cc, alpha^c) then satisfies the
+ * dual constraint alpha^cc(x) + alpha^c(y) <= C(x,y) on the supports), and
+ *   m = <alpha^cc, a> + <alpha^c, b>  <=  the exact transport cost (weak duality).
+ * Plain double loops over the supports with the explicit cost. */
+int or_ctransform_bound(int d, double gamma, const double* a, const double* b, const double* f, double* lower) {
+    const int n = d * d + 1;
+    int na = 0, nb = 0;
+    int* sa = (int*)malloc(sizeof(int) * n);
+    int* sb = (int*)malloc(sizeof(int) * n);
+    for (int x = 0; x < n; ++x) { if (a[x] > 0) sa[na++] = x; if (b[x] > 0) sb[nb++] = x; }
+    double* alpha = (double*)malloc(sizeof(double) * (na + 1));
+    double* ac = (double*)malloc(sizeof(double) * (nb + 1));
+    for (int p = 0; p < na; ++p) alpha[p] = f[sa[p]] + gamma * log(a[sa[p]]);
+    for (int q = 0; q < nb; ++q) {
+        double m = INFINITY;
+        for (int p = 0; p < na; ++p) m = fmin(m, or_cost(d, sa[p], sb[q]) - alpha[p]);
+        ac[q] = m;
+    }
+    or_ksum s = {0, 0};
+    for (int p = 0; p < na; ++p) {
+        double m = INFINITY;
+        for (int q = 0; q < nb; ++q) m = fmin(m, or_cost(d, sa[p], sb[q]) - ac[q]);
+        ks_add(&s, a[sa[p]] * m);
+    }
+    for (int q = 0; q < nb; ++q) ks_add(&s, b[sb[q]] * ac[q]);
+    if (lower) *lower = (na > 0 && nb > 0) ? ks_val(&s) : 0.0;
+    free(sa); free(sb); free(alpha); free(ac);
     return 0;
 }

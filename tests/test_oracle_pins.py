@@ -402,3 +402,41 @@ def test_round_bound_is_above_exact_transport(seed):
             assert rb["upper"] >= L - 1e-12, (gamma, T, rb["upper"], L)
             below += r["cost"] < L - 1e-9
     assert below > 0   # the check has teeth: some unrounded plans undercut the optimum
+
+
+# --------------------------------------------------------------------------- C-transform lower bound m_t
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_ctransform_bound_below_exact_transport(seed):
+    """Sec. 3 "Upper and Lower Bounds": m_t <= L_C(a, b) <= M_t at every
+    iterate (weak duality below, feasibility of the rounded plan above), with
+    L_C = d_2^2 of the snapped points from an assignment solver (Prop. 1), and
+    both bounds close in on L_C as gamma -> 0 and the iterates converge."""
+    d = 16
+    b, t, o = inputs.random_diagrams(2, nmin=6, nmax=9, seed=seed, log_uniform=False)
+    h, _ = oracle.rasterize(b, t, o, d)
+    X = _snapped_points(b[o[0]:o[1]], t[o[0]:o[1]], d)
+    Y = _snapped_points(b[o[1]:o[2]], t[o[1]:o[2]], d)
+    L, _ = _diag_matching_sq(X, Y)
+    a, bb = oracle.augment(h[0], h[1])
+    for gamma in (1e-2, 1e-3, 2e-4):
+        for T in (1, 5, 50, 2000):
+            r = oracle.sinkhorn_w(d, gamma, a, bb, T, 0.0)
+            m = oracle.ctransform_bound(d, gamma, a, bb, r["f"])
+            M = oracle.round_bound(d, gamma, a, bb, r["f"], r["g"])["upper"]
+            assert m <= L + 1e-12 <= M + 2e-12, (gamma, T, m, L, M)
+    r = oracle.sinkhorn_w(d, 2e-4, a, bb, 400000, 1e-12)
+    m = oracle.ctransform_bound(d, 2e-4, a, bb, r["f"])
+    assert L - m <= 1e-3 * max(L, 1e-3)
+
+
+def test_ctransform_bound_exact_on_a_single_point():
+    """One point against the empty diagram: the only feasible plan sends the
+    point to the diagonal, and with any alpha the transforms give exactly its
+    cost (alpha^c(Delta) = cD - alpha, alpha^cc = cD - alpha^c = alpha)."""
+    d = 16
+    h = np.zeros((2, d, d), np.uint32)
+    h[0, 3, 9] = 1
+    a, bb = oracle.augment(h[0], h[1])
+    f = np.random.default_rng(0).normal(size=d * d + 1)
+    m = oracle.ctransform_bound(d, 1e-2, a, bb, f)
+    assert m == pytest.approx((9 - 3) ** 2 / (2 * d * d), rel=1e-12)
