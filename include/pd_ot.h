@@ -143,24 +143,29 @@ pd_status pd_sinkhorn_batch(pd_ctx* ctx, const uint32_t* histA, const uint32_t* 
 
 
 /*
- * pd_sinkhorn_upper_bound -- Prop. 3: the PD_FP32 solve of pd_sinkhorn_batch
- * (same inputs, parameters and cost / iters / err / status outputs), then the
- * transport cost of the rounded plan R of each pair's final plan P:
- * the rounding algorithm of the supplementary (after Altschuler et al.) maps P
- * to R in Pi(a, b) by X = min(a / r(P), 1), Y = min(b / c(diag(X) P), 1),
- * R = diag(X) P diag(Y) + e_r e_c^T / |e_c|_1, with e_r, e_c the marginal
- * errors of the rescaled plan.  R is a feasible transport plan, so
- * upper[p] = <R, C> bounds the exact (unregularised) transport cost from
- * above; it is computed without forming R (Prop. 3: Prop. 2 on the rescaled
- * potentials plus the rank-one term through the separable cost).
- *   upper : double [P] (device, output)
+ * pd_sinkhorn_bounds -- Sec. 3 "Upper and Lower Bounds": the PD_FP32 solve of
+ * pd_sinkhorn_batch (same inputs, parameters and cost / iters / err / status
+ * outputs), then for each pair, from its final iterate, the bounds
+ *   lower[p] = m_t = <alpha^cc, a> + <alpha^c, b>  <=  L_C(a, b)  <=  upper[p] = M_t = <R, C>
+ * on the exact (unregularised) transport cost L_C:
+ *   - m_t: alpha = gamma log u (u = a exp(f/gamma)), its C-transform
+ *     alpha^c(y) = min_x C(x,y) - alpha(x) and the C^T-transform
+ *     alpha^cc(x) = min_y C(x,y) - alpha^c(y), over the supports (weak duality);
+ *     evaluated exactly in FP64 as two separable (min, +) stages;
+ *   - M_t (Prop. 3): the rounding algorithm of the supplementary (after
+ *     Altschuler et al.) maps P to R in Pi(a, b) by X = min(a / r(P), 1),
+ *     Y = min(b / c(diag(X) P), 1), R = diag(X) P diag(Y) + e_r e_c^T / |e_c|_1,
+ *     with e_r, e_c the marginal errors of the rescaled plan; R is feasible,
+ *     and <R, C> is computed without forming R (Prop. 2 on the rescaled
+ *     potentials plus the rank-one term through the separable cost).
+ *   lower, upper : double [P] (device, output; either may be NULL)
  * Synchronises `stream`.  Errors: as pd_sinkhorn_batch; precision must be
  * PD_FP32.  A pair whose status is not PD_OK / PD_NOT_CONVERGED gets NaN.
  */
-pd_status pd_sinkhorn_upper_bound(pd_ctx* ctx, const uint32_t* histA, const uint32_t* massA, const uint32_t* histB,
-                                  const uint32_t* massB, const int32_t* pairs, int P, const pd_sinkhorn_params* params,
-                                  const double* g_init, double* cost, double* upper, int32_t* iters, float* err,
-                                  int32_t* status, pd_stream stream);
+pd_status pd_sinkhorn_bounds(pd_ctx* ctx, const uint32_t* histA, const uint32_t* massA, const uint32_t* histB,
+                             const uint32_t* massB, const int32_t* pairs, int P, const pd_sinkhorn_params* params,
+                             const double* g_init, double* cost, double* lower, double* upper, int32_t* iters,
+                             float* err, int32_t* status, pd_stream stream);
 
 /*
  * pd_barycenter -- Alg. 2 (smoothed barycenter).  z starts as z_init, or, when

@@ -25,7 +25,7 @@ EXPORTED = ["pd_abi_version", "pd_ctx_create", "pd_ctx_destroy", "pd_last_error"
             "pd_sinkhorn_default_params", "pd_sinkhorn_batch", "pd_profile_enable", "pd_profile_read",
             "pd_sinkhorn_batch_noalloc", "pd_barycenter", "pd_kmeans", "pd_serve_default_config",
             "pd_serve_create", "pd_serve_load_centroids", "pd_serve_submit", "pd_serve_poll", "pd_serve_wait",
-            "pd_serve_inject_failure", "pd_serve_destroy", "pd_sinkhorn_upper_bound"]
+            "pd_serve_inject_failure", "pd_serve_destroy", "pd_sinkhorn_bounds"]
 PD_Q_DISTANCE, PD_Q_NEAREST = 0, 1
 SERVE_D = (32, 64, 128, 256)
 PD_K_RASTER, PD_K_SETUP, PD_K_LOGSTEP, PD_K_ABSORB, PD_K_ITER, PD_K_FINALIZE, PD_K_COUNT = 0, 1, 2, 3, 4, 5, 16
@@ -101,8 +101,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.pd_sinkhorn_batch_noalloc.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int,
                                                   ctypes.POINTER(SinkhornParams), _vp, _vp, _vp, _vp, _vp, _vp,
                                                   _vp, _vp, _vp, _vp]
-        lib.pd_sinkhorn_upper_bound.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
-                                                ctypes.POINTER(SinkhornParams), _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        lib.pd_sinkhorn_bounds.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                           ctypes.POINTER(SinkhornParams), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         lib.pd_barycenter.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(SinkhornParams), ctypes.c_double,
                                       ctypes.c_int, _vp, _vp, _vp, _vp]
         lib.pd_kmeans.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SinkhornParams),
@@ -224,22 +224,23 @@ def pd_sinkhorn_batch(ctx: Context, histA, massA, histB, massB, params: Sinkhorn
     return o
 
 
-def pd_sinkhorn_upper_bound(ctx: Context, histA, massA, histB, massB, params: SinkhornParams, pairs=None,
-                            g_init=None, stream=None):
-    """pd_sinkhorn_upper_bound (Prop. 3): dict with cost, upper (cost of the
-    rounded plan), iters, err, status."""
+def pd_sinkhorn_bounds(ctx: Context, histA, massA, histB, massB, params: SinkhornParams, pairs=None,
+                       g_init=None, stream=None):
+    """pd_sinkhorn_bounds (Sec. 3 bounds): dict with cost, lower (m_t), upper
+    (M_t, the rounded plan's cost, Prop. 3), iters, err, status."""
     import torch
     P = pairs.shape[0] if pairs is not None else histA.shape[0]
     dev = histA.device
     o = {"cost": torch.empty(P, dtype=torch.float64, device=dev),
+         "lower": torch.empty(P, dtype=torch.float64, device=dev),
          "upper": torch.empty(P, dtype=torch.float64, device=dev),
          "iters": torch.empty(P, dtype=torch.int32, device=dev),
          "err": torch.empty(P, dtype=torch.float32, device=dev),
          "status": torch.empty(P, dtype=torch.int32, device=dev)}
-    ctx.check(ctx.lib.pd_sinkhorn_upper_bound(
+    ctx.check(ctx.lib.pd_sinkhorn_bounds(
         ctx.handle, _ptr(histA), _ptr(massA), _ptr(histB), _ptr(massB), _ptr(pairs), int(P), ctypes.byref(params),
-        _ptr(g_init), _ptr(o["cost"]), _ptr(o["upper"]), _ptr(o["iters"]), _ptr(o["err"]), _ptr(o["status"]),
-        _stream(stream)))
+        _ptr(g_init), _ptr(o["cost"]), _ptr(o["lower"]), _ptr(o["upper"]), _ptr(o["iters"]), _ptr(o["err"]),
+        _ptr(o["status"]), _stream(stream)))
     return o
 
 

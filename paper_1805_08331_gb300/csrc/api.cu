@@ -507,26 +507,27 @@ static pd_status sinkhorn_ws(pd_ctx* c, int P, const pd_sinkhorn_params* prm, Sk
     return PD_OK;
 }
 
-// Prop. 3: the PD_FP32 solve of pd_sinkhorn_batch, then the cost of the rounded plan.
-extern "C" pd_status pd_sinkhorn_upper_bound(pd_ctx* c, const uint32_t* histA, const uint32_t* massA,
-                                             const uint32_t* histB, const uint32_t* massB, const int32_t* pairs, int P,
-                                             const pd_sinkhorn_params* prm, const double* g_init, double* cost,
-                                             double* upper, int32_t* iters, float* err, int32_t* status,
-                                             pd_stream stream) {
+// Sec. 3 "Upper and Lower Bounds": the PD_FP32 solve of pd_sinkhorn_batch, then
+// the C-transform lower bound m_t and the rounded plan's cost M_t (Prop. 3).
+extern "C" pd_status pd_sinkhorn_bounds(pd_ctx* c, const uint32_t* histA, const uint32_t* massA,
+                                        const uint32_t* histB, const uint32_t* massB, const int32_t* pairs, int P,
+                                        const pd_sinkhorn_params* prm, const double* g_init, double* cost,
+                                        double* lower, double* upper, int32_t* iters, float* err, int32_t* status,
+                                        pd_stream stream) {
     if (!c) return PD_ERR_INVALID;
     c->err.clear();
-    if (!prm) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_upper_bound: NULL params");
+    if (!prm) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: NULL params");
     const int d = prm->d;
-    if (d < 2 || d > 256) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_upper_bound: d must be in [2,256]");
+    if (d < 2 || d > 256) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: d must be in [2,256]");
     if (!(prm->gamma > 0) || !std::isfinite(prm->gamma))
-        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_upper_bound: gamma must be > 0");
-    if (prm->max_iter < 1) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_upper_bound: max_iter must be >= 1");
-    if (!(prm->tol >= 0)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_upper_bound: tol must be >= 0");
-    if (prm->precision != PD_FP32) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_upper_bound: only PD_FP32 is supported");
-    if (P < 0) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_upper_bound: P < 0");
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: gamma must be > 0");
+    if (prm->max_iter < 1) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: max_iter must be >= 1");
+    if (!(prm->tol >= 0)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: tol must be >= 0");
+    if (prm->precision != PD_FP32) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: only PD_FP32 is supported");
+    if (P < 0) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: P < 0");
     if (P == 0) return PD_OK;
-    if (!cost || !upper || !histA || !histB || !massA || !massB)
-        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_upper_bound: NULL input/cost/upper");
+    if (!cost || !histA || !histB || !massA || !massB)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: NULL input/cost");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(c, cudaSetDevice(c->device));
     SkWS w;
@@ -537,10 +538,14 @@ extern "C" pd_status pd_sinkhorn_upper_bound(pd_ctx* c, const uint32_t* histA, c
     SkRun r = make_run(prm);
     st = lse_solve(c, w, r, g_init, cost, nullptr, nullptr, nullptr, nullptr, iters, err, status, counter, s);
     if (st != PD_OK) return st;
-    { ProfScope ps(c, PD_K_FINALIZE, s); CUDA_TRY(c, sk_launch_round_bound(w, s)); }
-    { ProfScope ps(c, PD_K_FINALIZE, s);
-      CUDA_TRY(c, sk_launch_lse_finalize(w, upper, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s)); }
-    CUDA_TRY(c, sk_launch_add_corr(w, upper, s));
+    // the lower bound reads the final potentials; the upper bound then rescales them in place
+    if (lower) { ProfScope ps(c, PD_K_FINALIZE, s); CUDA_TRY(c, sk_launch_ctransform(w, lower, s)); }
+    if (upper) {
+        { ProfScope ps(c, PD_K_FINALIZE, s); CUDA_TRY(c, sk_launch_round_bound(w, s)); }
+        { ProfScope ps(c, PD_K_FINALIZE, s);
+          CUDA_TRY(c, sk_launch_lse_finalize(w, upper, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s)); }
+        CUDA_TRY(c, sk_launch_add_corr(w, upper, s));
+    }
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return PD_OK;
 }

@@ -121,6 +121,8 @@ cudaError_t sk_launch_lse_finalize_list(const SkWS& w, double* cost, float* row_
 // <R, C> (sk_launch_add_corr adds it).
 cudaError_t sk_launch_round_bound(const SkWS& w, cudaStream_t s);
 cudaError_t sk_launch_add_corr(const SkWS& w, double* upper, cudaStream_t s);
+// lower bound m_t of every usable pair from its current potentials (bounds.cu)
+cudaError_t sk_launch_ctransform(const SkWS& w, double* lower, cudaStream_t s);
 // workspace helpers (api.cu)
 size_t pd_carve_ws(char* base, int P, int d, int dp, double gamma, SkWS* w, int** counter);
 cudaError_t pd_upload_cost_tables(const SkWS& w, double gamma, cudaStream_t s);

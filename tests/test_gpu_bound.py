@@ -1,8 +1,10 @@
-"""Prop. 3 on the GPU: the cost of the rounded plan, <R, C>, against the
-oracle's literal rounding of the same iterate (dense plan, supplementary's
-rounding algorithm), at fixed iteration counts so both sides hold the same
-potentials; early iterates have large marginal errors, so the rank-one term
-is exercised, late ones check that the bound closes onto the cost."""
+"""Sec. 3 "Upper and Lower Bounds" on the GPU, against the oracle at the same
+iterate (fixed iteration counts, so both sides hold the same potentials):
+the rounded plan's cost M_t = <R, C> (Prop. 3) against the oracle's literal
+rounding of the dense plan, and the C-transform bound m_t against the
+oracle's plain minimisation over the supports.  Early iterates have large
+marginal errors, so the rank-one term is exercised; late ones check that the
+bounds close in on the cost."""
 import numpy as np
 import pytest
 import torch
@@ -29,9 +31,14 @@ def ctx():
     c.close()
 
 
+# m_t is exact FP64 min-plus arithmetic on the potentials; its agreement is set
+# by the potentials' own error (f/gamma to ~1e-7 relative), well below this
+LOWER_REL = 1e-6
+
+
 def _gpu(ctx, hA, hB, d, gamma, T, tol=0.0):
     p = api.pd_sinkhorn_default_params(gamma, d, max_iter=T, tol=tol)
-    out = api.pd_sinkhorn_upper_bound(ctx, hists_to_gpu(hA), dev(masses(hA).view(np.int32)), hists_to_gpu(hB),
+    out = api.pd_sinkhorn_bounds(ctx, hists_to_gpu(hA), dev(masses(hA).view(np.int32)), hists_to_gpu(hB),
                                       dev(masses(hB).view(np.int32)), p)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}
@@ -50,7 +57,10 @@ def test_upper_bound_matches_oracle_rounding(ctx, d, gamma, nmin, nmax, T):
         a, bb = oracle.augment(hA[k], hB[k])
         r = oracle.sinkhorn_w(d, gamma, a, bb, T, 0.0)
         rb = oracle.round_bound(d, gamma, a, bb, r["f"], r["g"])
+        lo = oracle.ctransform_bound(d, gamma, a, bb, r["f"])
         assert abs(g["cost"][k] - r["cost"]) <= 1e-6 * r["cost"]
+        assert abs(g["lower"][k] - lo) <= LOWER_REL * abs(lo) + 1e-12, (k, g["lower"][k], lo)
+        assert g["lower"][k] <= g["upper"][k]
         assert abs(g["upper"][k] - rb["upper"]) <= UPPER_REL * rb["upper"] + 1e-12, (k, g["upper"][k], rb["upper"])
         print(f"d={d} T={T} pair {k}: cost rel {abs(g['cost'][k] - r['cost']) / r['cost']:.2e}, "
               f"upper rel {abs(g['upper'][k] - rb['upper']) / rb['upper']:.2e}, upper-cost {rb['upper'] - r['cost']:.3e}")
@@ -67,9 +77,11 @@ def test_upper_bound_empty_side_and_converged(ctx):
     expect = float(np.sum(h[0][i, j] * ((j - i) / d) ** 2 / 2))
     assert abs(g["cost"][0] - expect) <= 1e-7 * expect
     assert abs(g["upper"][0] - expect) <= 1e-7 * expect
+    assert abs(g["lower"][0] - expect) <= 1e-12 * expect    # the forced plan: m_t is exact
     # converged to 1e-9: the exact gap is of the order of the marginal error;
     # the GPU's is bounded by the potentials' FP32-level noise (min() of two
     # noisy potentials in the rescaling), i.e. the stated UPPER_REL
     g = _gpu(ctx, h[:1], h[1:], d, gamma, 50000, 1e-9)
     assert g["status"][0] == api.PD_OK
     assert abs(g["upper"][0] - g["cost"][0]) <= UPPER_REL * g["cost"][0]
+    assert g["lower"][0] <= g["cost"][0] + 1e-12

@@ -83,9 +83,9 @@ def test_fullsize_upper_bound_within_rounding_distance(solved):
     mass = torch.from_numpy(h.reshape(2 * P, -1).sum(1).astype(np.uint32).view(np.int32)).cuda()
     pairs = torch.arange(2 * P, dtype=torch.int32, device="cuda").view(P, 2).contiguous()
     prm = api.pd_sinkhorn_default_params(GAMMA, D, max_iter=MAX_ITER, tol=TOL)
-    u = api.pd_sinkhorn_upper_bound(ctx, hist, mass, hist, mass, prm, pairs=pairs)
+    u = api.pd_sinkhorn_bounds(ctx, hist, mass, hist, mass, prm, pairs=pairs)
     torch.cuda.synchronize()
-    cost, upper = u["cost"].cpu().numpy(), u["upper"].cpu().numpy()
+    cost, upper, lower = u["cost"].cpu().numpy(), u["upper"].cpu().numpy(), u["lower"].cpu().numpy()
     ctx.close()
     assert np.array_equal(u["iters"].cpu().numpy(), r["iters"])
     nA = h[0::2].reshape(P, -1).sum(1).astype(np.float64)
@@ -93,5 +93,7 @@ def test_fullsize_upper_bound_within_rounding_distance(solved):
     a = np.concatenate([h[0::2].reshape(P, -1).astype(np.float64), nB[:, None]], 1)
     b = np.concatenate([h[1::2].reshape(P, -1).astype(np.float64), nA[:, None]], 1)
     dev_l1 = np.abs(r["row_marg"] - a).sum(1) + np.abs(r["col_marg"] - b).sum(1)
-    assert np.all(np.isfinite(upper))
+    assert np.all(np.isfinite(upper)) and np.all(np.isfinite(lower))
     assert np.all(np.abs(upper - cost) <= 4.0 * dev_l1 + 1e-6 * cost + 1e-9)
+    # m_t <= L_C <= M_t on every pair (weak duality and feasibility of R)
+    assert np.all(lower <= upper + 1e-12 * upper)
