@@ -49,6 +49,14 @@ def _load():
             lib.or_sinkhorn_pd_batch.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, _u32p,
                                                  ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                  _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int), _dp]
+            lib.or_sinkhorn_pd_batchp.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _u32p, _u32p,
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                  _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int), _dp]
+            lib.or_sinkhorn_wp.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp, ctypes.c_int,
+                                           ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp,
+                                           ctypes.POINTER(ctypes.c_int), _dp]
+            lib.or_cost_p.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+            lib.or_cost_p.restype = ctypes.c_double
             lib.or_barycenter.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                           _dp, _dp, _dp]
@@ -87,9 +95,11 @@ def rasterize(birth, death, offsets, d):
     return hist, mass
 
 
-def cost(d, x, y):
-    """Entry C_xy of the augmented cost (index d*d is the Delta bin)."""
-    return float(_load().or_cost(d, int(x), int(y)))
+def cost(d, x, y, p=2.0):
+    """Entry C_xy of the augmented cost (index d*d is the Delta bin), ground cost ||.||_p^p."""
+    if p == 2.0:
+        return float(_load().or_cost(d, int(x), int(y)))
+    return float(_load().or_cost_p(d, float(p), int(x), int(y)))
 
 
 def augment(hA, hB):
@@ -99,9 +109,10 @@ def augment(hA, hB):
     return np.concatenate([hA, [hB.sum()]]), np.concatenate([hB, [hA.sum()]])
 
 
-def sinkhorn_w(d, gamma, a, b, max_iter, tol, g_init=None):
+def sinkhorn_w(d, gamma, a, b, max_iter, tol, g_init=None, p=2.0):
     """Log-domain FP64 Sinkhorn on the explicit augmented cost (weights a, b of
-    length d*d+1).  Returns a dict with cost, f, g, rmarg, cmarg, iters, err."""
+    length d*d+1; ground cost ||.||_p^p).  Returns a dict with cost, f, g,
+    rmarg, cmarg, iters, err."""
     n = d * d + 1
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -114,7 +125,7 @@ def sinkhorn_w(d, gamma, a, b, max_iter, tol, g_init=None):
     g = np.empty(n)
     rm = np.empty(n)
     cm = np.empty(n)
-    rc = _load().or_sinkhorn_w(d, gamma, _ptr(a, _dp), _ptr(b, _dp), int(max_iter), float(tol),
+    rc = _load().or_sinkhorn_wp(d, float(p), gamma, _ptr(a, _dp), _ptr(b, _dp), int(max_iter), float(tol),
                                _ptr(gi, _dp), ctypes.byref(c), _ptr(f, _dp), _ptr(g, _dp),
                                _ptr(rm, _dp), _ptr(cm, _dp), ctypes.byref(it), ctypes.byref(er))
     if rc != 0:
@@ -145,13 +156,13 @@ def ctransform_bound(d, gamma, a, b, f):
     return out.value
 
 
-def sinkhorn_pd(d, gamma, hA, hB, max_iter, tol, g_init=None):
+def sinkhorn_pd(d, gamma, hA, hB, max_iter, tol, g_init=None, p=2.0):
     """Alg. 1 for one pair of d x d histograms (Prop. 1 augmentation)."""
     a, b = augment(hA, hB)
-    return sinkhorn_w(d, gamma, a, b, max_iter, tol, g_init)
+    return sinkhorn_w(d, gamma, a, b, max_iter, tol, g_init, p=p)
 
 
-def sinkhorn_pd_batch(d, gamma, hA, hB, max_iter, tol, want_potentials=False, want_marginals=False):
+def sinkhorn_pd_batch(d, gamma, hA, hB, max_iter, tol, want_potentials=False, want_marginals=False, p=2.0):
     """Alg. 1 over P pairs (OpenMP over pairs).  hA, hB: uint32 [P,d,d]."""
     hA = np.ascontiguousarray(hA, dtype=np.uint32)
     hB = np.ascontiguousarray(hB, dtype=np.uint32)
@@ -164,7 +175,7 @@ def sinkhorn_pd_batch(d, gamma, hA, hB, max_iter, tol, want_potentials=False, wa
     g = np.empty((P, n)) if want_potentials else None
     rm = np.empty((P, n)) if want_marginals else None
     cm = np.empty((P, n)) if want_marginals else None
-    rc = _load().or_sinkhorn_pd_batch(d, gamma, _ptr(hA, _u32p), _ptr(hB, _u32p), P, int(max_iter),
+    rc = _load().or_sinkhorn_pd_batchp(d, float(p), gamma, _ptr(hA, _u32p), _ptr(hB, _u32p), P, int(max_iter),
                                       float(tol), _ptr(cost_, _dp), _ptr(f, _dp), _ptr(g, _dp),
                                       _ptr(rm, _dp), _ptr(cm, _dp),
                                       it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(er, _dp))

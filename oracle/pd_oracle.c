@@ -16,7 +16,8 @@
  *                        floor(yd)/d).
  *   or_cost           -- Prop. 1 block cost matrix with the Delta row/column
  *                        and the grid cost of Sec. 3 "Convolutions"
- *                        (squared Euclidean, p = 2, physical units on [0,1]^2).
+ *                        (squared Euclidean, p = 2, physical units on [0,1]^2);
+ *                        or_cost_p: the same for ||.||_p^p.
  *   or_sinkhorn_w     -- Eq. (SinkhornMap) iterated in the log domain on the
  *                        explicit cost matrix (no separability is used), the
  *                        marginal error dist(P, Pi(a,b)) of Eq. (Altschuler
@@ -114,6 +115,23 @@ double or_cost(int d, int x, int y) {
     return ((i - k) * (i - k) + (j - l) * (j - l)) / ((double)d * d);
 }
 
+/* The same block cost for a ground cost ||.||_p^p (p >= 1), separable on the
+ * grid: |i-k|^p / d^p + |j-l|^p / d^p; a grid cell to the diagonal bin costs
+ * ||x - pi_Delta(x)||_p^p with pi_Delta the orthogonal projection, i.e.
+ * 2 |(j-i) / (2d)|^p; Delta-Delta costs 0.  p = 2 is or_cost itself. */
+double or_cost_p(int d, double p, int x, int y) {
+    if (p == 2.0) return or_cost(d, x, y);
+    const int D = d * d;
+    if (x == D && y == D) return 0.0;
+    if (x == D || y == D) {
+        int z = (x == D) ? y : x;
+        double i = z / d, j = z % d;
+        return 2.0 * pow(fabs(j - i) / (2.0 * d), p);
+    }
+    double i = x / d, j = x % d, k = y / d, l = y % d;
+    return pow(fabs(i - k) / d, p) + pow(fabs(j - l) / d, p);
+}
+
 /* log-sum-exp of n values (two passes: max, then sum). */
 static double lse(const double* v, int n) {
     double m = -INFINITY;
@@ -137,10 +155,10 @@ static double lse(const double* v, int n) {
  * entries get the same formula, a soft c-transform, finite); rmarg, cmarg the
  * two marginals of P; iters; err (relative to the total mass).
  * Returns 0, or -1 on bad input (negative weight, unequal total mass).     */
-int or_sinkhorn_w(int d, double gamma, const double* a, const double* b,
-                  int max_iter, double tol, const double* g_init,
-                  double* cost, double* f_out, double* g_out,
-                  double* rmarg, double* cmarg, int* iters, double* err_out) {
+int or_sinkhorn_wp(int d, double pw, double gamma, const double* a, const double* b,
+                   int max_iter, double tol, const double* g_init,
+                   double* cost, double* f_out, double* g_out,
+                   double* rmarg, double* cmarg, int* iters, double* err_out) {
     const int n = d * d + 1;
     double ma = 0, mb = 0;
     for (int x = 0; x < n; ++x) {
@@ -155,7 +173,7 @@ int or_sinkhorn_w(int d, double gamma, const double* a, const double* b,
     for (int x = 0; x < n; ++x) { if (a[x] > 0) sa[na++] = x; if (b[x] > 0) sb[nb++] = x; }
     double* C = (double*)malloc(sizeof(double) * (size_t)na * (nb > 0 ? nb : 1));
     for (int p = 0; p < na; ++p)
-        for (int q = 0; q < nb; ++q) C[(size_t)p * nb + q] = or_cost(d, sa[p], sb[q]);
+        for (int q = 0; q < nb; ++q) C[(size_t)p * nb + q] = or_cost_p(d, pw, sa[p], sb[q]);
     double* la = (double*)malloc(sizeof(double) * (na + 1));
     double* lb = (double*)malloc(sizeof(double) * (nb + 1));
     for (int p = 0; p < na; ++p) la[p] = log(a[sa[p]]);
@@ -206,14 +224,14 @@ int or_sinkhorn_w(int d, double gamma, const double* a, const double* b,
     /* potentials on every entry: the update formulas evaluated everywhere */
     if (f_out) {
         for (int x = 0; x < n; ++x) {
-            for (int q = 0; q < nb; ++q) tmp[q] = lb[q] + (g[q] - or_cost(d, x, sb[q])) / gamma;
+            for (int q = 0; q < nb; ++q) tmp[q] = lb[q] + (g[q] - or_cost_p(d, pw, x, sb[q])) / gamma;
             f_out[x] = nb > 0 ? -gamma * lse(tmp, nb) : 0.0;
         }
         for (int p = 0; p < na; ++p) f_out[sa[p]] = f[p];
     }
     if (g_out) {
         for (int y = 0; y < n; ++y) {
-            for (int p = 0; p < na; ++p) tmp[p] = la[p] + (f[p] - or_cost(d, sa[p], y)) / gamma;
+            for (int p = 0; p < na; ++p) tmp[p] = la[p] + (f[p] - or_cost_p(d, pw, sa[p], y)) / gamma;
             g_out[y] = na > 0 ? -gamma * lse(tmp, na) : 0.0;
         }
         for (int q = 0; q < nb; ++q) g_out[sb[q]] = g[q];
@@ -222,6 +240,14 @@ int or_sinkhorn_w(int d, double gamma, const double* a, const double* b,
     if (err_out) *err_out = err;
     free(sa); free(sb); free(C); free(la); free(lb); free(f); free(g); free(tmp);
     return 0;
+}
+
+/* Eq. (SinkhornMap) with the p = 2 cost (see or_sinkhorn_wp). */
+int or_sinkhorn_w(int d, double gamma, const double* a, const double* b,
+                  int max_iter, double tol, const double* g_init,
+                  double* cost, double* f_out, double* g_out,
+                  double* rmarg, double* cmarg, int* iters, double* err_out) {
+    return or_sinkhorn_wp(d, 2.0, gamma, a, b, max_iter, tol, g_init, cost, f_out, g_out, rmarg, cmarg, iters, err_out);
 }
 
 /* Prop. 1 augmentation: a = (hist_A, |B|), b = (hist_B, |A|). */
@@ -233,7 +259,7 @@ static void augment(int d, const uint32_t* hA, const uint32_t* hB, double* a, do
 }
 
 /* Alg. 1 for one pair of rasterised diagrams. */
-int or_sinkhorn_pd(int d, double gamma, const uint32_t* hA, const uint32_t* hB,
+int or_sinkhorn_pdp(int d, double pw, double gamma, const uint32_t* hA, const uint32_t* hB,
                    int max_iter, double tol, const double* g_init,
                    double* cost, double* f, double* g, double* rmarg, double* cmarg,
                    int* iters, double* err) {
@@ -241,27 +267,39 @@ int or_sinkhorn_pd(int d, double gamma, const uint32_t* hA, const uint32_t* hB,
     double* a = (double*)malloc(sizeof(double) * n);
     double* b = (double*)malloc(sizeof(double) * n);
     augment(d, hA, hB, a, b);
-    int rc = or_sinkhorn_w(d, gamma, a, b, max_iter, tol, g_init, cost, f, g, rmarg, cmarg, iters, err);
+    int rc = or_sinkhorn_wp(d, pw, gamma, a, b, max_iter, tol, g_init, cost, f, g, rmarg, cmarg, iters, err);
     free(a); free(b);
     return rc;
 }
 
+int or_sinkhorn_pd(int d, double gamma, const uint32_t* hA, const uint32_t* hB,
+                   int max_iter, double tol, const double* g_init,
+                   double* cost, double* f, double* g, double* rmarg, double* cmarg, int* iters, double* err) {
+    return or_sinkhorn_pdp(d, 2.0, gamma, hA, hB, max_iter, tol, g_init, cost, f, g, rmarg, cmarg, iters, err);
+}
+
 /* Alg. 1 over P pairs (histA[p], histB[p]), parallel over pairs.  Outputs are
  * per pair; f, g, rmarg, cmarg have n = d*d+1 entries per pair (may be NULL). */
-int or_sinkhorn_pd_batch(int d, double gamma, const uint32_t* hA, const uint32_t* hB, int P,
+int or_sinkhorn_pd_batchp(int d, double pw, double gamma, const uint32_t* hA, const uint32_t* hB, int P,
                          int max_iter, double tol, double* cost, double* f, double* g,
                          double* rmarg, double* cmarg, int* iters, double* err) {
     const size_t D = (size_t)d * d, n = D + 1;
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
     for (int p = 0; p < P; ++p) {
-        int rc = or_sinkhorn_pd(d, gamma, hA + p * D, hB + p * D, max_iter, tol, NULL,
+        int rc = or_sinkhorn_pdp(d, pw, gamma, hA + p * D, hB + p * D, max_iter, tol, NULL,
                                 cost ? cost + p : NULL, f ? f + p * n : NULL, g ? g + p * n : NULL,
                                 rmarg ? rmarg + p * n : NULL, cmarg ? cmarg + p * n : NULL,
                                 iters ? iters + p : NULL, err ? err + p : NULL);
         bad |= (rc != 0);
     }
     return bad ? -1 : 0;
+}
+
+int or_sinkhorn_pd_batch(int d, double gamma, const uint32_t* hA, const uint32_t* hB, int P,
+                         int max_iter, double tol, double* cost, double* f, double* g,
+                         double* rmarg, double* cmarg, int* iters, double* err) {
+    return or_sinkhorn_pd_batchp(d, 2.0, gamma, hA, hB, P, max_iter, tol, cost, f, g, rmarg, cmarg, iters, err);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -440,3 +440,66 @@ def test_ctransform_bound_exact_on_a_single_point():
     f = np.random.default_rng(0).normal(size=d * d + 1)
     m = oracle.ctransform_bound(d, 1e-2, a, bb, f)
     assert m == pytest.approx((9 - 3) ** 2 / (2 * d * d), rel=1e-12)
+
+
+# --------------------------------------------------------------------------- ground cost ||.||_p^p (NEXT-3)
+@pytest.mark.parametrize("p", [1.0, 1.5, 3.0])
+def test_cost_p_matches_geometry(p):
+    """||.||_p^p between cell corners, and the diagonal cost ||x - pi(x)||_p^p
+    with pi the orthogonal projection onto the diagonal."""
+    d = 16
+    for (i, j, k, l) in [(3, 9, 5, 12), (0, 15, 15, 15), (7, 7, 2, 11)]:
+        x, y = i * d + j, k * d + l
+        assert oracle.cost(d, x, y, p) == pytest.approx(abs(i - k) ** p / d ** p + abs(j - l) ** p / d ** p, rel=1e-14)
+        s, t = i / d, j / d
+        m = (s + t) / 2
+        assert oracle.cost(d, x, d * d, p) == pytest.approx(abs(s - m) ** p + abs(t - m) ** p, rel=1e-12)
+        assert oracle.cost(d, d * d, x, p) == oracle.cost(d, x, d * d, p)
+    assert oracle.cost(d, d * d, d * d, p) == 0.0
+
+
+@pytest.mark.parametrize("p", [1.0, 1.5])
+def test_p_empty_diagram_and_two_cells_closed_forms(p):
+    """Closed forms hold for any ground cost: against an empty diagram the plan
+    is forced (S = sum_x a_x C(x, Delta)), and one cell against one cell is the
+    2x2 problem of the p = 2 pin with the ||.||_p^p entries."""
+    d, gamma = 16, 1e-2
+    h = np.zeros((2, d, d), np.uint32)
+    h[0, 3, 9] = 2
+    h[0, 1, 4] = 1
+    r = oracle.sinkhorn_pd(d, gamma, h[0], h[1], 50, 0.0, p=p)
+    expect = 2 * oracle.cost(d, 3 * d + 9, d * d, p) + oracle.cost(d, 1 * d + 4, d * d, p)
+    assert r["cost"] == pytest.approx(expect, rel=1e-12)
+    h = np.zeros((2, d, d), np.uint32)
+    h[0, 3, 9] = 1
+    h[1, 5, 12] = 1
+    gamma = 0.2     # well-conditioned 2x2 problem (|D|/gamma of order 1)
+    r = oracle.sinkhorn_pd(d, gamma, h[0], h[1], 100000, 1e-14, p=p)
+    Cxy = oracle.cost(d, 3 * d + 9, 5 * d + 12, p)
+    CxD = oracle.cost(d, 3 * d + 9, d * d, p)
+    CyD = oracle.cost(d, 5 * d + 12, d * d, p)
+    assert r["cost"] == pytest.approx(_two_by_two(1, 1, Cxy, CxD, CyD, gamma), rel=1e-9)
+
+
+def test_p1_gamma_to_zero_matches_assignment():
+    """p = 1: as gamma -> 0 the cost tends to the optimal partial matching with
+    ||.||_1 costs (point to point sum of |db| + |dt|, point to diagonal
+    |t - s|, i.e. 2 |(t-s)/2|), by assignment on the augmented matrix."""
+    from scipy.optimize import linear_sum_assignment
+    d = 16
+    b, t, o = inputs.random_diagrams(2, nmin=6, nmax=8, seed=4, log_uniform=False)
+    h, _ = oracle.rasterize(b, t, o, d)
+    X = _snapped_points(b[o[0]:o[1]], t[o[0]:o[1]], d)
+    Y = _snapped_points(b[o[1]:o[2]], t[o[1]:o[2]], d)
+    nX, nY = len(X), len(Y)
+    M = np.zeros((nX + nY, nX + nY))
+    M[:nX, :nY] = np.abs(X[:, None, :] - Y[None, :, :]).sum(-1)
+    M[:nX, nY:] = np.abs(X[:, 1] - X[:, 0])[:, None]
+    M[nX:, :nY] = np.abs(Y[:, 1] - Y[:, 0])[None, :]
+    r_, c_ = linear_sum_assignment(M)
+    L = M[r_, c_].sum()
+    n = int(h.sum())
+    for gamma in (1e-2, 1e-3, 2e-4):
+        r = oracle.sinkhorn_pd(d, gamma, h[0], h[1], 400000, 1e-12, p=1.0)
+        assert -1e-9 <= r["cost"] - L <= 2 * gamma * n * math.log(n) + 1e-9
+    assert abs(r["cost"] - L) <= 5e-3 * max(L, 1e-3)
