@@ -101,6 +101,9 @@ typedef struct {
                           stage k = eps_stages..1 iterates at gamma * 4^k until err <= max(tol, 1e-4),
                           the potentials f, g carried over; then gamma itself to tol.  The result is the
                           same fixed point; iters counts all stages.  0 (default) = off */
+    double p;          /* ground cost ||.||_p^p, 1 <= p <= 8 (default 2, squared Euclidean): grid cost
+                          |i-k|^p/d^p + |j-l|^p/d^p, cell to diagonal 2 |(j-i)/(2d)|^p (the orthogonal
+                          projection).  p != 2: PD_FP32 engine of pd_sinkhorn_batch only */
 } pd_sinkhorn_params;
 
 /* Fill *p with defaults for (gamma, d): max_iter 20000, tol 1e-6, PD_FP32,

@@ -156,6 +156,7 @@ extern "C" void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, 
     p->absorb_every = 64;
     p->rel_log_thresh = 0.0;
     p->eps_stages = 0;
+    p->p = 2.0;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -167,7 +168,7 @@ size_t pd_carve_ws(char* base, int P, int d, int dp, double gamma, SkWS* w, int*
     auto take = [&](size_t bytes) -> char* { char* r = base ? base + off : nullptr; off += align256(bytes); return r; };
     const size_t M = (size_t)dp * dp, n = M + 1;
     SkWS t{};
-    t.d = d; t.dp = dp; t.n = (int)n; t.P = P; t.gamma = gamma;
+    t.d = d; t.dp = dp; t.n = (int)n; t.P = P; t.gamma = gamma; t.p = 2.0;
     float** fm[] = {&t.K1u, &t.K2u, &t.K1v, &t.K2v, &t.ut, &t.vt, &t.Wt, &t.Rt, &t.KDu, &t.KDv, &t.am, &t.bm};
     for (auto f : fm) *f = (float*)take(sizeof(float) * M * P);
     float** fv[] = {&t.rs_u, &t.cf_u, &t.rs_v, &t.cf_v};
@@ -203,15 +204,17 @@ size_t pd_carve_ws(char* base, int P, int d, int dp, double gamma, SkWS* w, int*
 cudaError_t pd_upload_cost_tables(const SkWS& w, double gamma, cudaStream_t s) {
     const int dp = w.dp, d = w.d;
     std::vector<float> tab(5 * dp);
+    const double pw = w.p;
     for (int m = 0; m < dp; ++m) {
         double z = (double)m / d;
-        double v = z * z / gamma, v2 = 0.5 * z * z / gamma;
+        double v = pw == 2.0 ? z * z / gamma : std::pow(z, pw) / gamma;
+        double v2 = pw == 2.0 ? 0.5 * z * z / gamma : 2.0 * std::pow(0.5 * z, pw) / gamma;
         float hi = (float)v, hi2 = (float)v2;
         tab[m] = hi;
         tab[dp + m] = (float)(v - (double)hi);
         tab[2 * dp + m] = hi2;
         tab[3 * dp + m] = (float)(v2 - (double)hi2);
-        tab[4 * dp + m] = m == 0 ? -INFINITY : (float)(2.0 * std::log(z));
+        tab[4 * dp + m] = m == 0 ? -INFINITY : (float)(pw * std::log(z));
     }
     return cudaMemcpyAsync(w.ctab, tab.data(), sizeof(float) * 5 * dp, cudaMemcpyHostToDevice, s);
 }
@@ -404,6 +407,9 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: unknown precision %d", prm->precision);
     if (prm->precision == PD_BF16 && d > 128)
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: PD_BF16 supports d <= 128");
+    if (!(prm->p >= 1.0 && prm->p <= 8.0)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: p must be in [1, 8]");
+    if (prm->p != 2.0 && prm->precision != PD_FP32)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: p != 2 needs the PD_FP32 engine");
     if (P < 0) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: P < 0");
     if (P == 0) return PD_OK;
     if (!cost || !histA || !histB || !massA || !massB) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: NULL input/cost");
@@ -426,6 +432,7 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     }
     pd_carve_ws((char*)c->ws, P, d, dp, prm->gamma, &w, &counter);
     w.histA = histA; w.histB = histB; w.massA = massA; w.massB = massB; w.pairs = pairs;
+    w.p = prm->p;
     CUDA_TRY(c, pd_upload_cost_tables(w, prm->gamma, s));
     SkRun r = make_run(prm);
     if (prm->precision == PD_FP32) {
@@ -492,6 +499,7 @@ static pd_status check_params(pd_ctx* c, const pd_sinkhorn_params* prm, const ch
     if (prm->max_iter < 1) return fail(c, PD_ERR_INVALID, "%s: max_iter must be >= 1", who);
     if (!(prm->tol >= 0)) return fail(c, PD_ERR_INVALID, "%s: tol must be >= 0", who);
     if (prm->precision != PD_FP32) return fail(c, PD_ERR_INVALID, "%s: only PD_FP32 is supported", who);
+    if (prm->p != 2.0) return fail(c, PD_ERR_INVALID, "%s: only p = 2 is supported", who);
     return PD_OK;
 }
 
@@ -524,6 +532,7 @@ extern "C" pd_status pd_sinkhorn_bounds(pd_ctx* c, const uint32_t* histA, const 
     if (prm->max_iter < 1) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: max_iter must be >= 1");
     if (!(prm->tol >= 0)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: tol must be >= 0");
     if (prm->precision != PD_FP32) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: only PD_FP32 is supported");
+    if (prm->p != 2.0) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: only p = 2 is supported");
     if (P < 0) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: P < 0");
     if (P == 0) return PD_OK;
     if (!cost || !histA || !histB || !massA || !massB)
@@ -717,7 +726,7 @@ extern "C" pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint
     if (!prm) return PD_ERR_INVALID;
     const int d = prm->d;
     if (d < 2 || d > 256 || !(prm->gamma > 0) || !std::isfinite(prm->gamma) || prm->max_iter < 1 ||
-        !(prm->tol >= 0) || prm->precision != PD_FP32 || P < 0)
+        !(prm->tol >= 0) || prm->precision != PD_FP32 || prm->p != 2.0 || P < 0)
         return PD_ERR_INVALID;
     if (P == 0) return PD_OK;
     if (!cost || !histA || !histB || !massA || !massB) return PD_ERR_INVALID;

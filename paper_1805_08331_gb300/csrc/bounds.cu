@@ -30,13 +30,13 @@ static __device__ void ct_lines(const int* __restrict__ rpin, const int* __restr
 // rows[r] of c_{j, cols[c]} - in(i, j).
 template <class In>
 static __device__ void ct_rows(const int* __restrict__ rpin, const int* __restrict__ listin, In in, double* A, int d,
-                               int dp, const int* rows, const int* cols, int nr, int nc) {
+                               int dp, const int* rows, const int* cols, int nr, int nc, double pw) {
     for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
         const int r = e / nc, c = e - r * nc, i = rows[r], l = cols[c];
         double m = INFINITY;
         for (int q = rpin[i]; q < rpin[i + 1]; ++q) {
             const int cell = listin[q];
-            m = fmin(m, pd_c1(cell % dp, l, d) - in(cell));
+            m = fmin(m, pd_c1p(cell % dp, l, d, pw) - in(cell));
         }
         A[(size_t)r * nc + c] = m;
     }
@@ -46,21 +46,21 @@ static __device__ void ct_rows(const int* __restrict__ rpin, const int* __restri
 // Stage 2 at one output cell (k, l): min over rows of c_{rows[r], k} + A[r][colpos[l]],
 // and the input Delta term cD(k, l) - inD when the input side has a Delta mass.
 static __device__ __forceinline__ double ct_cell(int cell, const double* A, int d, int dp, const int* rows,
-                                                 const int* colpos, int nr, int nc, double inD, bool hasD) {
+                                                 const int* colpos, int nr, int nc, double inD, bool hasD, double pw) {
     const int k = cell / dp, l = cell % dp, c = colpos[l];
-    double m = hasD ? pd_cdiag(k, l, d) - inD : INFINITY;
-    for (int r = 0; r < nr; ++r) m = fmin(m, pd_c1(rows[r], k, d) + A[(size_t)r * nc + c]);
+    double m = hasD ? pd_cdiagp(k, l, d, pw) - inD : INFINITY;
+    for (int r = 0; r < nr; ++r) m = fmin(m, pd_c1p(rows[r], k, d, pw) + A[(size_t)r * nc + c]);
     return m;
 }
 
 // Delta entry of a transform: min( min over the input support of cD(x) - in(x), -inD ).
 template <class In>
 static __device__ double ct_delta(const int* __restrict__ listin, int nin, In in, double inD, bool hasD, int d, int dp,
-                                  double* shd) {
+                                  double* shd, double pw) {
     double m = INFINITY;
     for (int e = threadIdx.x; e < nin; e += blockDim.x) {
         const int cell = listin[e];
-        m = fmin(m, pd_cdiag(cell / dp, cell % dp, d) - in(cell));
+        m = fmin(m, pd_cdiagp(cell / dp, cell % dp, d, pw) - in(cell));
     }
     m = -block_max(-m, shd, (double)-INFINITY);
     if (hasD) m = fmin(m, -inD);
@@ -91,25 +91,25 @@ __global__ void __launch_bounds__(256) sk_ctransform_kernel(SkWS w, double* __re
     // alpha^c on the b support and its Delta entry
     ct_lines(q.rpa, q.cpb, d, rows, cols, colpos, nrc);
     int nr = nrc[0], nc = nrc[1];
-    ct_rows(q.rpa, q.sa, alpha, A, d, dp, rows, cols, nr, nc);
+    ct_rows(q.rpa, q.sa, alpha, A, d, dp, rows, cols, nr, nc, w.p);
     double sum = 0.0;
     for (int e = t; e < nb; e += blockDim.x) {
         const int cell = q.sb[e];
-        const double v = ct_cell(cell, A, d, dp, rows, colpos, nr, nc, alphaD, hasA);
+        const double v = ct_cell(cell, A, d, dp, rows, colpos, nr, nc, alphaD, hasA, w.p);
         ac[cell] = v;
         sum += exp(q.lb[cell]) * v;
     }
-    const double acD = hasB ? ct_delta(q.sa, na, alpha, alphaD, hasA, d, dp, shd) : 0.0;
+    const double acD = hasB ? ct_delta(q.sa, na, alpha, alphaD, hasA, d, dp, shd, w.p) : 0.0;
     __syncthreads();
     // alpha^cc on the a support (summed with the weights a) and its Delta entry
     ct_lines(q.rpb, q.cpa, d, rows, cols, colpos, nrc);
     nr = nrc[0]; nc = nrc[1];
-    ct_rows(q.rpb, q.sb, acf, A, d, dp, rows, cols, nr, nc);
+    ct_rows(q.rpb, q.sb, acf, A, d, dp, rows, cols, nr, nc, w.p);
     for (int e = t; e < na; e += blockDim.x) {
         const int cell = q.sa[e];
-        sum += exp(q.la[cell]) * ct_cell(cell, A, d, dp, rows, colpos, nr, nc, acD, hasB);
+        sum += exp(q.la[cell]) * ct_cell(cell, A, d, dp, rows, colpos, nr, nc, acD, hasB, w.p);
     }
-    const double accD = hasA ? ct_delta(q.sb, nb, acf, acD, hasB, d, dp, shd) : 0.0;
+    const double accD = hasA ? ct_delta(q.sb, nb, acf, acD, hasB, d, dp, shd, w.p) : 0.0;
     const double s = block_sum(sum, shd);
     if (t == 0) lower[p] = s + (hasA ? aD * accD : 0.0) + (hasB ? bD * acD : 0.0);
 }

@@ -21,6 +21,18 @@ __device__ __forceinline__ double pd_cdiag(int i, int j, int d) {
     return 0.5 * t * t;
 }
 
+// The same costs for a ground cost ||.||_p^p (p >= 1): c_ik = |i-k|^p / d^p,
+// and the cell-to-diagonal cost ||x - pi(x)||_p^p = 2 |(j-i) / (2d)|^p with pi
+// the orthogonal projection onto the diagonal.  p = 2 is pd_c1 / pd_cdiag.
+__device__ __forceinline__ double pd_c1p(int i, int k, int d, double p) {
+    if (p == 2.0) return pd_c1(i, k, d);
+    return pow(fabs((double)(i - k)) / (double)d, p);
+}
+__device__ __forceinline__ double pd_cdiagp(int i, int j, int d, double p) {
+    if (p == 2.0) return pd_cdiag(i, j, d);
+    return 2.0 * pow(fabs((double)(j - i)) / (2.0 * (double)d), p);
+}
+
 // exp of an FP64 exponent evaluated in FP32 after clamping to the finite FP32
 // range; entries below ~1e-38 become 0 and large ones saturate (never inf).
 __device__ __forceinline__ float pd_exp_clamped(double arg) {

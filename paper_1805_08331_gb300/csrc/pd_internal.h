@@ -39,6 +39,7 @@ enum { ST_ACTIVE = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_RANGE = 3, ST_INVALID
 struct SkWS {
     int d, dp, n, P;
     double gamma;
+    double p;                       // ground cost ||.||_p^p (2: squared Euclidean)
     // FP32 [P][dp*dp]
     float *K1u, *K2u, *K1v, *K2v;   // absorbed separable kernel factors (u- and v-updates)
     float *ut, *vt;                 // residual scalings on the grid (0 off support)
@@ -60,7 +61,7 @@ struct SkWS {
     double *la, *lb;                // [P][dp*dp] log a, log b on the supports (FP64)
     int *rpa, *rpb, *cpa, *cpb;     // [P][dp+1] row / column pointers of the support lists
     int *cia, *cib;                 // [P][dp*dp] row indices of the column-major support lists
-    float* ctab;                    // [2*dp] hi / lo FP32 split of c_m/gamma, m = 0..dp-1
+    float* ctab;                    // [5*dp] hi / lo FP32 splits of c_m/gamma and cD_m/gamma, log c_m
     int* order_buf;                 // [P] launch order of the pairs (filled by the host)
     const int* order;               // NULL: CTA b runs pair b; else CTA b runs pair order[b]
     // inputs: integer histograms (histA/massA, histB/massB) or, when wA / wB is

@@ -516,9 +516,11 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
         float2* cdt = smp<float2>(K.cdt);
         for (int m = t; m < 2 * d - 1; m += NT) {
             const double z = (double)(m - (d - 1));
-            ct[m] = l2_split(z * z * sc2, gsc);
+            ct[m] = l2_split(w.p == 2.0 ? z * z * sc2 : pd_c1p(m, d - 1, d, w.p) * (LOG2E / w.gamma), gsc);
         }
-        for (int m = t; m < d; m += NT) cdt[m] = l2_split(0.5 * (double)m * (double)m * sc2, gsc);
+        for (int m = t; m < d; m += NT)
+            cdt[m] = l2_split(w.p == 2.0 ? 0.5 * (double)m * (double)m * sc2 : pd_cdiagp(0, m, d, w.p) * (LOG2E / w.gamma),
+                              gsc);
     }
     if (t == 0) range_flag = 0;
     __syncthreads();

@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_finalize_kernel(SkWS w, double* 
                 const double lu = q.la[c] + q.phi[c];
                 if (m1 > -INFINITY) cs += exp(lu + (double)m1 + (double)log_acc(t1));
                 if (m2 > -INFINITY) cs += exp(lu + (double)m2 + (double)log_acc(t2));
-                const double cd = pd_cdiag(i, j, d);
+                const double cd = pd_cdiagp(i, j, d, w.p);
                 if (lBD > -INFINITY && cd > 0) cs += exp(lu + lBD + psiD - cd / gamma) * cd;
                 rowD += exp(lu + lBD + psiD - cd / gamma);
                 if (row_marg) row_marg[(size_t)p * n_out + i * d + j] = (float)exp(lu - phip);
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_finalize_kernel(SkWS w, double* 
     double csb = 0.0, colD = 0.0;
     for (int e = t; e < nb; e += blockDim.x) {
         int c = q.sb[e], k = c / dp, l = c % dp;
-        double cd = pd_cdiag(k, l, d);
+        double cd = pd_cdiagp(k, l, d, w.p);
         double lv = q.lb[c] + q.psi[c];
         if (lAD > -INFINITY && cd > 0) csb += exp(lv + lAD + phiD - cd / gamma) * cd;
         colD += exp(lv + lAD + phiD - cd / gamma);
@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(T_CTA) sk_round_bound_kernel(SkWS w) {
             const int c = q.sb[e], k = c / dp, l = c % dp;
             const double ec = exp(q.lb[c]) * fmax(0.0, -expm1(q.psi[c] - S2[c]));
             ec_sum += ec;
-            ec_cd += ec * pd_cdiag(k, l, d);
+            ec_cd += ec * pd_cdiagp(k, l, d, w.p);
             atomicAdd(&sums[2][k], ec);
             atomicAdd(&sums[3][l], ec);
             q.psi[c] = fmin(q.psi[c], S2[c]);
@@ -855,7 +855,7 @@ __global__ void __launch_bounds__(T_CTA) sk_round_bound_kernel(SkWS w) {
         for (int e = t; e < na; e += blockDim.x) {
             const int c = q.sa[e], i = c / dp, j = c % dp;
             const double er = exp(q.la[c]) * fmax(0.0, -expm1(q.phi[c] - S1[c]));
-            er_cd += er * pd_cdiag(i, j, d);
+            er_cd += er * pd_cdiagp(i, j, d, w.p);
             atomicAdd(&sums[0][i], er);
             atomicAdd(&sums[1][j], er);
         }
@@ -866,7 +866,7 @@ __global__ void __launch_bounds__(T_CTA) sk_round_bound_kernel(SkWS w) {
     double bil = 0.0;
     for (int e = t; e < d * d; e += blockDim.x) {
         const int i = e / d, k = e % d;
-        bil += pd_c1(i, k, d) * (sums[0][i] * sums[2][k] + sums[1][i] * sums[3][k]);
+        bil += pd_c1p(i, k, d, w.p) * (sums[0][i] * sums[2][k] + sums[1][i] * sums[3][k]);
     }
     bil = block_sum(bil, shd);
     ec_sum = block_sum(ec_sum, shd);

@@ -168,6 +168,37 @@ def test_gamma_continuation_same_fixed_point(ctx, stages, continuation_case):
     assert rel_plain.max() <= 3e-5 and rel_eps.max() <= 3e-5, (rel_plain, rel_eps)
 
 
+@pytest.mark.parametrize("d,gamma,pw,T", [(32, 1e-2, 1.0, 300), (64, 5e-3, 1.5, 200), (128, 1e-3, 1.0, 150),
+                                             (100, 2e-3, 3.0, 150)])
+def test_ground_cost_p_fixed_iterations(ctx, d, gamma, pw, T):
+    """NEXT-3: ground cost ||.||_p^p (separable on the grid, orthogonal
+    projection to the diagonal) in the PD_FP32 engine: same iterates as the
+    oracle with the explicit p-cost after T iterations (relative cost 1e-6)."""
+    b, t, o = inputs.random_diagrams(6, nmin=30, nmax=300, seed=d + int(10 * pw))
+    h, _ = oracle.rasterize(b, t, o, d)
+    ref = oracle.sinkhorn_pd_batch(d, gamma, h[0::2], h[1::2], T, 0.0, p=pw)
+    prm = api.pd_sinkhorn_default_params(gamma, d, max_iter=T, tol=0.0, p=pw)
+    out = api.pd_sinkhorn_batch(ctx, hists_to_gpu(h[0::2]), dev(masses(h[0::2]).view(np.int32)),
+                                hists_to_gpu(h[1::2]), dev(masses(h[1::2]).view(np.int32)), prm)
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    assert np.all(g["iters"] == T)
+    rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
+    assert rel.max() <= 1e-6, rel
+
+
+def test_ground_cost_p_rejected_where_unsupported(ctx):
+    h = np.zeros((2, 8, 8), np.uint32)
+    h[:, 1, 2] = 1
+    hh, mm = hists_to_gpu(h), dev(masses(h).view(np.int32))
+    for kw in ({"p": 0.5}, {"p": 9.0}, {"p": 1.0, "precision": api.PD_BF16}, {"p": 1.0, "precision": api.PD_FP32_DENSE}):
+        prm = api.pd_sinkhorn_default_params(1e-2, 8, **kw)
+        with pytest.raises(api.PdError):
+            api.pd_sinkhorn_batch(ctx, hh, mm, hh, mm, prm)
+    prm = api.pd_sinkhorn_default_params(1e-2, 8, p=1.0)
+    with pytest.raises(api.PdError):
+        api.pd_sinkhorn_bounds(ctx, hh, mm, hh, mm, prm)
+
+
 def test_pairs_index_and_edge_cases(ctx):
     d, gamma = 32, 1e-2
     b, t, o = inputs.random_diagrams(3, nmin=5, nmax=30, seed=3)
