@@ -7,7 +7,7 @@ nothing from it.  The arithmetic lives in ``pd_oracle.c`` (plain C, FP64);
 this module builds it with gcc and marshals numpy arrays through ctypes.
 """
 from .oracle import (build, rasterize, cost, sinkhorn_w, sinkhorn_pd, sinkhorn_pd_batch,
-                     barycenter, kmeans, num_threads, augment, round_bound, ctransform_bound)
+                     barycenter, kmeans, num_threads, augment, round_bound, ctransform_bound, sharpen)
 
 __all__ = ["build", "rasterize", "cost", "sinkhorn_w", "sinkhorn_pd", "sinkhorn_pd_batch",
-           "barycenter", "kmeans", "num_threads", "augment", "round_bound", "ctransform_bound"]
+           "barycenter", "kmeans", "num_threads", "augment", "round_bound", "ctransform_bound", "sharpen"]

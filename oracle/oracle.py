@@ -60,6 +60,11 @@ def _load():
             lib.or_barycenter.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                           _dp, _dp, _dp]
+            lib.or_barycenter_s.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            _dp, _dp, _dp, ctypes.c_int]
+            lib.or_sharpen.argtypes = [ctypes.c_int, _dp, ctypes.c_double]
+            lib.or_sharpen.restype = ctypes.c_double
             lib.or_kmeans.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_uint64, _i32p, _dp, _dp]
@@ -184,15 +189,24 @@ def sinkhorn_pd_batch(d, gamma, hA, hB, max_iter, tol, want_potentials=False, wa
     return dict(cost=cost_, iters=it, err=er, f=f, g=g, rmarg=rm, cmarg=cm)
 
 
-def barycenter(d, gamma, hists, lam, outer_iters, max_iter, tol, z_init=None):
-    """Alg. 2.  hists: uint32 [N,d,d].  Returns (z [d,d], energy [outer_iters])."""
+def sharpen(d, z, H0):
+    """Entropic sharpening of z (d x d) to entropy H0; returns (z', beta)."""
+    z = np.ascontiguousarray(z, dtype=np.float64).ravel().copy()
+    beta = _load().or_sharpen(d, _ptr(z, _dp), float(H0))
+    return z.reshape(d, d), beta
+
+
+def barycenter(d, gamma, hists, lam, outer_iters, max_iter, tol, z_init=None, sharpen=False):
+    """Alg. 2 (optionally with entropic sharpening after every step).
+    hists: uint32 [N,d,d].  Returns (z [d,d], energy [outer_iters])."""
     hists = np.ascontiguousarray(hists, dtype=np.uint32)
     N = hists.shape[0]
     zi = None if z_init is None else np.ascontiguousarray(z_init, dtype=np.float64).ravel()
     z = np.empty(d * d)
     e = np.empty(outer_iters)
-    rc = _load().or_barycenter(d, gamma, _ptr(hists, _u32p), N, float(lam), int(outer_iters),
-                               int(max_iter), float(tol), _ptr(zi, _dp), _ptr(z, _dp), _ptr(e, _dp))
+    rc = _load().or_barycenter_s(d, gamma, _ptr(hists, _u32p), N, float(lam), int(outer_iters),
+                                 int(max_iter), float(tol), _ptr(zi, _dp), _ptr(z, _dp), _ptr(e, _dp),
+                                 1 if sharpen else 0)
     if rc != 0:
         raise ValueError("or_barycenter failed")
     return z.reshape(d, d), e

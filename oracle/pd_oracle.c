@@ -32,6 +32,9 @@
  *                        update.
  *   or_kmeans         -- Sec. 5 k-means: assignment by Alg. 1 cost, centroid
  *                        update by Alg. 2.
+ *   or_sharpen        -- entropic sharpening of a measure (Solomon et al., the
+ *                        extension the paper names for smeared barycenters);
+ *                        or_barycenter_s applies it after every Alg. 2 step.
  *   or_round_bound    -- the rounding algorithm of the supplementary (Altschuler
  *                        et al.) applied to the plan P(f, g), written out on the
  *                        explicit dense matrices, and the transport cost of the
@@ -316,9 +319,48 @@ int or_sinkhorn_pd_batch(int d, double gamma, const uint32_t* hA, const uint32_t
  *   z <- z * exp(-lambda * grad) on the cells where z > 0.
  * energy[t] = (1/N) sum_i <P_i, C_i> of the step-t plans (energy of z_t).
  * Outputs z_out (d*d) and energy (outer_iters entries, may be NULL).        */
-int or_barycenter(int d, double gamma, const uint32_t* hists, int N, double lambda,
-                  int outer_iters, int max_iter, double tol, const double* z_init,
-                  double* z_out, double* energy) {
+/* Entropy of the normalised measure w^beta / sum w^beta, w = z / |z| (z >= 0,
+ * zeros skipped): H(beta) = log S - beta T / S with S = sum w^beta,
+ * T = sum w^beta log w. */
+static double sharp_entropy(const double* z, int D, double zm, double beta) {
+    or_ksum S = {0, 0}, T = {0, 0};
+    for (int x = 0; x < D; ++x) {
+        if (!(z[x] > 0)) continue;
+        const double lw = log(z[x] / zm);
+        const double wb = exp(beta * lw);
+        ks_add(&S, wb);
+        ks_add(&T, wb * lw);
+    }
+    return log(ks_val(&S)) - beta * ks_val(&T) / ks_val(&S);
+}
+
+/* Entropic sharpening (Solomon et al., the reference of the paper's Sec. 4
+ * remark on smeared barycenters): when the entropy of the normalised measure
+ * z / |z| exceeds H0, z is replaced by |z| w^beta / sum w^beta with the beta >= 1
+ * for which that entropy equals H0 (the entropy decreases with beta; bisection
+ * in FP64).  Returns beta (1 when no sharpening was needed). */
+double or_sharpen(int d, double* z, double H0) {
+    const int D = d * d;
+    double zm = 0;
+    for (int x = 0; x < D; ++x) zm += z[x];
+    if (!(zm > 0) || !(sharp_entropy(z, D, zm, 1.0) > H0)) return 1.0;
+    double lo = 1.0, hi = 2.0;
+    while (sharp_entropy(z, D, zm, hi) > H0 && hi < 1e6) { lo = hi; hi *= 2.0; }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sharp_entropy(z, D, zm, mid) > H0) lo = mid; else hi = mid;
+    }
+    const double beta = 0.5 * (lo + hi);
+    or_ksum S = {0, 0};
+    for (int x = 0; x < D; ++x) if (z[x] > 0) ks_add(&S, exp(beta * log(z[x] / zm)));
+    const double Sv = ks_val(&S);
+    for (int x = 0; x < D; ++x) if (z[x] > 0) z[x] = zm * exp(beta * log(z[x] / zm)) / Sv;
+    return beta;
+}
+
+int or_barycenter_s(int d, double gamma, const uint32_t* hists, int N, double lambda,
+                    int outer_iters, int max_iter, double tol, const double* z_init,
+                    double* z_out, double* energy, int sharpen) {
     const int D = d * d, n = D + 1;
     if (N <= 0 || d < 2) return -1;
     double* z = (double*)malloc(sizeof(double) * D);
@@ -334,6 +376,17 @@ int or_barycenter(int d, double gamma, const uint32_t* hists, int N, double lamb
     double* fs = (double*)calloc((size_t)N * n, sizeof(double));
     double* costs = (double*)calloc(N, sizeof(double));
     int bad = 0;
+    /* sharpening target: the largest entropy among the normalised input histograms */
+    double H0 = -INFINITY;
+    if (sharpen) {
+        double* w = (double*)malloc(sizeof(double) * D);
+        for (int i = 0; i < N; ++i) {
+            double m = 0;
+            for (int x = 0; x < D; ++x) { w[x] = hists[(size_t)i * D + x]; m += w[x]; }
+            if (m > 0) H0 = fmax(H0, sharp_entropy(w, D, m, 1.0));
+        }
+        free(w);
+    }
     for (int t = 0; t < outer_iters; ++t) {
         double zm = 0;
         for (int x = 0; x < D; ++x) zm += z[x];
@@ -365,6 +418,7 @@ int or_barycenter(int d, double gamma, const uint32_t* hists, int N, double lamb
             double grad = ks_val(&s) / N;
             z[x] *= exp(-lambda * grad);
         }
+        if (sharpen) or_sharpen(d, z, H0);
     }
     memcpy(z_out, z, sizeof(double) * D);
     free(z); free(gs); free(fs); free(costs);
@@ -372,6 +426,13 @@ int or_barycenter(int d, double gamma, const uint32_t* hists, int N, double lamb
 }
 
 /* ---------------------------------------------------------------------- */
+/* Alg. 2 without sharpening. */
+int or_barycenter(int d, double gamma, const uint32_t* hists, int N, double lambda,
+                  int outer_iters, int max_iter, double tol, const double* z_init,
+                  double* z_out, double* energy) {
+    return or_barycenter_s(d, gamma, hists, N, lambda, outer_iters, max_iter, tol, z_init, z_out, energy, 0);
+}
+
 /* splitmix64 (Steele, Lea & Flood 2014), used for the k-means seeding. */
 static uint64_t splitmix64(uint64_t* s) {
     uint64_t z = (*s += 0x9E3779B97F4A7C15ull);

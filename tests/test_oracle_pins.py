@@ -503,3 +503,48 @@ def test_p1_gamma_to_zero_matches_assignment():
         r = oracle.sinkhorn_pd(d, gamma, h[0], h[1], 400000, 1e-12, p=1.0)
         assert -1e-9 <= r["cost"] - L <= 2 * gamma * n * math.log(n) + 1e-9
     assert abs(r["cost"] - L) <= 5e-3 * max(L, 1e-3)
+
+
+# --------------------------------------------------------------------------- entropic sharpening (NEXT-2)
+def _entropy(w):
+    w = np.asarray(w, dtype=np.float64).ravel()
+    w = w[w > 0] / w.sum()
+    return float(-(w * np.log(w)).sum())
+
+
+def test_sharpen_hits_target_entropy_as_a_power():
+    """Sharpening replaces z by |z| w^beta / sum w^beta (w = z/|z|): the result
+    has the target entropy and the same mass and support, and it is a power of
+    z (log z'_x - log z'_y = beta (log z_x - log z_y) for every pair of cells)."""
+    d = 16
+    rng = np.random.default_rng(0)
+    z = np.zeros((d, d))
+    iu = np.triu_indices(d)
+    z[iu] = rng.random(len(iu[0])) + 0.05
+    H = _entropy(z)
+    H0 = H - 0.7
+    zs, beta = oracle.sharpen(d, z, H0)
+    assert beta > 1.0
+    assert _entropy(zs) == pytest.approx(H0, abs=1e-10)
+    assert zs.sum() == pytest.approx(z.sum(), rel=1e-12)
+    assert np.array_equal(zs > 0, z > 0)
+    lz, lzs = np.log(z[iu]), np.log(zs[iu])
+    assert np.allclose(lzs - lzs[0], beta * (lz - lz[0]), atol=1e-9)
+    # already below the target: unchanged
+    z2, b2 = oracle.sharpen(d, z, H + 0.1)
+    assert b2 == 1.0 and np.array_equal(z2, z)
+
+
+def test_sharpened_barycenter_entropy_bounded_and_energy_close():
+    """Alg. 2 with sharpening after every step: z's entropy never exceeds the
+    largest input entropy, while the plain barycenter's does (smearing), and the
+    sharpened barycenter is more concentrated (larger largest cell share)."""
+    d, gamma = 16, 1e-2
+    b, t, o, _ = inputs.mode_diagrams(4, 1, 20, 30, sigma=0.04, seed=3)
+    h, _ = oracle.rasterize(b, t, o, d)
+    H0 = max(_entropy(x) for x in h)
+    z0, _ = oracle.barycenter(d, gamma, h, 2.0, 6, 300, 0.0)
+    zs, _ = oracle.barycenter(d, gamma, h, 2.0, 6, 300, 0.0, sharpen=True)
+    assert _entropy(z0) > H0
+    assert _entropy(zs) <= H0 + 1e-9
+    assert (zs / zs.sum()).max() > (z0 / z0.sum()).max()
