@@ -320,16 +320,18 @@ int or_sinkhorn_pd_batch(int d, double gamma, const uint32_t* hA, const uint32_t
  * energy[t] = (1/N) sum_i <P_i, C_i> of the step-t plans (energy of z_t).
  * Outputs z_out (d*d) and energy (outer_iters entries, may be NULL).        */
 /* Entropy of the normalised measure w^beta / sum w^beta, w = z / |z| (z >= 0,
- * zeros skipped): H(beta) = log S - beta T / S with S = sum w^beta,
- * T = sum w^beta log w. */
-static double sharp_entropy(const double* z, int D, double zm, double beta) {
+ * zeros skipped).  The powers are taken of v = z / max z (the normalised
+ * measure is the same, since w and v differ by a constant factor), so the
+ * largest term is 1 and the sum cannot underflow however large beta is:
+ * H(beta) = log S - beta T / S with S = sum v^beta, T = sum v^beta log v. */
+static double sharp_entropy(const double* z, int D, double zmax, double beta) {
     or_ksum S = {0, 0}, T = {0, 0};
     for (int x = 0; x < D; ++x) {
         if (!(z[x] > 0)) continue;
-        const double lw = log(z[x] / zm);
-        const double wb = exp(beta * lw);
-        ks_add(&S, wb);
-        ks_add(&T, wb * lw);
+        const double lv = log(z[x] / zmax);
+        const double vb = exp(beta * lv);
+        ks_add(&S, vb);
+        ks_add(&T, vb * lv);
     }
     return log(ks_val(&S)) - beta * ks_val(&T) / ks_val(&S);
 }
@@ -341,20 +343,20 @@ static double sharp_entropy(const double* z, int D, double zm, double beta) {
  * in FP64).  Returns beta (1 when no sharpening was needed). */
 double or_sharpen(int d, double* z, double H0) {
     const int D = d * d;
-    double zm = 0;
-    for (int x = 0; x < D; ++x) zm += z[x];
-    if (!(zm > 0) || !(sharp_entropy(z, D, zm, 1.0) > H0)) return 1.0;
+    double zm = 0, zmax = 0;
+    for (int x = 0; x < D; ++x) { zm += z[x]; zmax = fmax(zmax, z[x]); }
+    if (!(zm > 0) || !(sharp_entropy(z, D, zmax, 1.0) > H0)) return 1.0;
     double lo = 1.0, hi = 2.0;
-    while (sharp_entropy(z, D, zm, hi) > H0 && hi < 1e6) { lo = hi; hi *= 2.0; }
+    while (sharp_entropy(z, D, zmax, hi) > H0 && hi < 1e6) { lo = hi; hi *= 2.0; }
     for (int it = 0; it < 200; ++it) {
         const double mid = 0.5 * (lo + hi);
-        if (sharp_entropy(z, D, zm, mid) > H0) lo = mid; else hi = mid;
+        if (sharp_entropy(z, D, zmax, mid) > H0) lo = mid; else hi = mid;
     }
     const double beta = 0.5 * (lo + hi);
     or_ksum S = {0, 0};
-    for (int x = 0; x < D; ++x) if (z[x] > 0) ks_add(&S, exp(beta * log(z[x] / zm)));
+    for (int x = 0; x < D; ++x) if (z[x] > 0) ks_add(&S, exp(beta * log(z[x] / zmax)));
     const double Sv = ks_val(&S);
-    for (int x = 0; x < D; ++x) if (z[x] > 0) z[x] = zm * exp(beta * log(z[x] / zm)) / Sv;
+    for (int x = 0; x < D; ++x) if (z[x] > 0) z[x] = zm * exp(beta * log(z[x] / zmax)) / Sv;
     return beta;
 }
 
@@ -383,7 +385,9 @@ int or_barycenter_s(int d, double gamma, const uint32_t* hists, int N, double la
         for (int i = 0; i < N; ++i) {
             double m = 0;
             for (int x = 0; x < D; ++x) { w[x] = hists[(size_t)i * D + x]; m += w[x]; }
-            if (m > 0) H0 = fmax(H0, sharp_entropy(w, D, m, 1.0));
+            double mx = 0;
+            for (int x = 0; x < D; ++x) mx = fmax(mx, w[x]);
+            if (m > 0) H0 = fmax(H0, sharp_entropy(w, D, mx, 1.0));
         }
         free(w);
     }

@@ -535,6 +535,22 @@ def test_sharpen_hits_target_entropy_as_a_power():
     assert b2 == 1.0 and np.array_equal(z2, z)
 
 
+def test_sharpen_large_beta_reaches_target():
+    """A nearly uniform measure sharpened far below its entropy needs a large
+    beta (here > 100): the result still has exactly the target entropy, i.e.
+    the powers do not underflow on the way."""
+    d = 32
+    rng = np.random.default_rng(1)
+    z = np.zeros((d, d))
+    iu = np.triu_indices(d)
+    z[iu] = 0.014 + 0.038 * rng.random(len(iu[0]))
+    H0 = 2.97
+    zs, beta = oracle.sharpen(d, z, H0)
+    assert beta > 50
+    assert _entropy(zs) == pytest.approx(H0, abs=1e-9)
+    assert zs.sum() == pytest.approx(z.sum(), rel=1e-12)
+
+
 def test_sharpened_barycenter_entropy_bounded_and_energy_close():
     """Alg. 2 with sharpening after every step: z's entropy never exceeds the
     largest input entropy, while the plain barycenter's does (smearing), and the
