@@ -104,6 +104,11 @@ typedef struct {
     double p;          /* ground cost ||.||_p^p, 1 <= p <= 8 (default 2, squared Euclidean): grid cost
                           |i-k|^p/d^p + |j-l|^p/d^p, cell to diagonal 2 |(j-i)/(2d)|^p (the orthogonal
                           projection).  p != 2: PD_FP32 engine of pd_sinkhorn_batch only */
+    int bary_sharpen;  /* pd_barycenter only: 1 = entropic sharpening after every Alg. 2 step (the
+                          extension the paper names for smeared barycenters, after Solomon et al.): when
+                          the entropy of z/|z| exceeds the largest entropy of the normalised input
+                          histograms, z <- |z| w^beta / sum w^beta (w = z/|z|), beta >= 1 chosen to meet
+                          it.  0 (default) = off */
 } pd_sinkhorn_params;
 
 /* Fill *p with defaults for (gamma, d): max_iter 20000, tol 1e-6, PD_FP32,

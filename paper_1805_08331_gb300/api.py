@@ -43,7 +43,7 @@ class SinkhornParams(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("d", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int), ("refine_iters", ctypes.c_int),
                 ("absorb_tau", ctypes.c_double), ("absorb_every", ctypes.c_int), ("rel_log_thresh", ctypes.c_double),
-                ("eps_stages", ctypes.c_int), ("p", ctypes.c_double)]
+                ("eps_stages", ctypes.c_int), ("p", ctypes.c_double), ("bary_sharpen", ctypes.c_int)]
 
 
 class ServeConfig(ctypes.Structure):

@@ -157,6 +157,7 @@ extern "C" void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, 
     p->rel_log_thresh = 0.0;
     p->eps_stages = 0;
     p->p = 2.0;
+    p->bary_sharpen = 0;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -586,6 +587,7 @@ extern "C" pd_status pd_barycenter(pd_ctx* c, const uint32_t* hist, const uint32
         }
         a.take<double>(D); a.take<double>(1); a.take<double>((size_t)N * n1); a.take<double>((size_t)N * n1);
         a.take<double>(N); a.take<int32_t>(2 * (size_t)N); a.take<int32_t>(N); a.take<float>(N); a.take<int32_t>(N);
+        a.take<unsigned long long>(1);
         if (pass == 0) continue;
     }
     a.off = 0;
@@ -598,10 +600,12 @@ extern "C" pd_status pd_barycenter(pd_ctx* c, const uint32_t* hist, const uint32
     int32_t* iters = a.take<int32_t>(N);
     float* err = a.take<float>(N);
     int32_t* status = a.take<int32_t>(N);
+    unsigned long long* H0bits = a.take<unsigned long long>(1);
     SkWS w;
     int* counter;
     st = sinkhorn_ws(c, N, prm, &w, &counter, s);
     if (st != PD_OK) return st;
+    if (prm->bary_sharpen) CUDA_TRY(c, outer_input_entropy(hist, N, d, H0bits, s));
     if (z_init) CUDA_TRY(c, cudaMemcpyAsync(z, z_init, sizeof(double) * D, cudaMemcpyDeviceToDevice, s));
     else CUDA_TRY(c, outer_bary_init_uniform(z, mass, N, d, s));
     CUDA_TRY(c, outer_owner_pairs(nullptr, N, pairs, s));
@@ -616,6 +620,7 @@ extern "C" pd_status pd_barycenter(pd_ctx* c, const uint32_t* hist, const uint32
         if (st != PD_OK) return st;
         if (energy) CUDA_TRY(c, outer_mean(cost, N, energy + t, s));
         CUDA_TRY(c, outer_bary_step(z, zmass, f, g, nullptr, N, 1, d, prm->gamma, lambda, s));
+        if (prm->bary_sharpen) CUDA_TRY(c, outer_sharpen(z, 1, d, H0bits, s));
     }
     CUDA_TRY(c, cudaMemcpyAsync(z_out, z, sizeof(double) * D, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -637,6 +642,7 @@ extern "C" pd_status pd_kmeans(pd_ctx* c, const uint32_t* hist, const uint32_t* 
     if (!c) return PD_ERR_INVALID;
     c->err.clear();
     pd_status st = check_params(c, prm, "pd_kmeans");
+    if (st == PD_OK && prm->bary_sharpen) return fail(c, PD_ERR_INVALID, "pd_kmeans: bary_sharpen is not supported");
     if (st != PD_OK) return st;
     if (N < 1 || k < 1 || k > N || !hist || !mass || !assign || !centroids)
         return fail(c, PD_ERR_INVALID, "pd_kmeans: need 1 <= k <= N and non-NULL hist, mass, assign, centroids");

@@ -156,3 +156,82 @@ cudaError_t outer_owner_pairs(const int32_t* owner, int N, int32_t* pairs, cudaS
     owner_pairs_kernel<<<(N + 255) / 256, 256, 0, s>>>(owner, N, pairs);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Entropic sharpening (Solomon et al.; the paper's Sec. 4 names it as the way
+// to spikier barycenters).  The target entropy H0 is the largest entropy of
+// the normalised input histograms; a measure z whose normalised entropy exceeds
+// H0 becomes |z| w^beta / sum w^beta (w = z / |z|) with the beta >= 1 at which
+// that entropy equals H0 (it decreases with beta; bisection, FP64).
+
+// H0 = max over the input histograms of log m - (sum h log h) / m  (one block per diagram)
+__global__ void input_entropy_kernel(const uint32_t* __restrict__ hist, int d, unsigned long long* __restrict__ H0bits) {
+    __shared__ double sh[32];
+    const int D = d * d;
+    const uint32_t* h = hist + (size_t)blockIdx.x * D;
+    double m = 0.0, s = 0.0;
+    for (int x = threadIdx.x; x < D; x += blockDim.x) {
+        const double v = (double)h[x];
+        if (v > 0) { m += v; s += v * log(v); }
+    }
+    m = block_sum(m, sh);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0 && m > 0) {
+        const double H = fmax(log(m) - s / m, 0.0);   // >= 0, so its bits order like the values
+        atomicMax(H0bits, (unsigned long long)__double_as_longlong(H));
+    }
+}
+
+// entropy of w^beta / sum w^beta with w = z / |z|, from the powers of v = z / zmax
+// (the same normalised measure; the largest term is 1, so the sum cannot
+// underflow for large beta).  Block reduction; every thread gets the value.
+__device__ double sharp_entropy(const double* z, int D, double zmax, double beta, double* sh) {
+    double S = 0.0, T = 0.0;
+    for (int x = threadIdx.x; x < D; x += blockDim.x) {
+        if (!(z[x] > 0)) continue;
+        const double lv = log(z[x] / zmax);
+        const double vb = exp(beta * lv);
+        S += vb;
+        T += vb * lv;
+    }
+    S = block_sum(S, sh);
+    T = block_sum(T, sh);
+    return log(S) - beta * T / S;
+}
+
+// one block per measure c: sharpen z_c in place when its entropy exceeds H0
+__global__ void sharpen_kernel(double* __restrict__ z, int d, const unsigned long long* __restrict__ H0bits) {
+    __shared__ double sh[32];
+    const int D = d * d;
+    double* zc = z + (size_t)blockIdx.x * D;
+    const double H0 = __longlong_as_double((long long)*H0bits);
+    double zm = 0.0, zmax = 0.0;
+    for (int x = threadIdx.x; x < D; x += blockDim.x) { zm += zc[x]; zmax = fmax(zmax, zc[x]); }
+    zm = block_sum(zm, sh);
+    zmax = block_max(zmax, sh, 0.0);
+    if (!(zm > 0) || !(sharp_entropy(zc, D, zmax, 1.0, sh) > H0)) return;
+    double lo = 1.0, hi = 2.0;
+    while (sharp_entropy(zc, D, zmax, hi, sh) > H0 && hi < 1e6) { lo = hi; hi *= 2.0; }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sharp_entropy(zc, D, zmax, mid, sh) > H0) lo = mid; else hi = mid;
+    }
+    const double beta = 0.5 * (lo + hi);
+    double S = 0.0;
+    for (int x = threadIdx.x; x < D; x += blockDim.x)
+        if (zc[x] > 0) S += exp(beta * log(zc[x] / zmax));
+    S = block_sum(S, sh);
+    for (int x = threadIdx.x; x < D; x += blockDim.x)
+        if (zc[x] > 0) zc[x] = zm * exp(beta * log(zc[x] / zmax)) / S;
+}
+
+cudaError_t outer_input_entropy(const uint32_t* hist, int N, int d, unsigned long long* H0bits, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(H0bits, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    input_entropy_kernel<<<N, 256, 0, s>>>(hist, d, H0bits);
+    return cudaGetLastError();
+}
+cudaError_t outer_sharpen(double* z, int k, int d, const unsigned long long* H0bits, cudaStream_t s) {
+    sharpen_kernel<<<k, 256, 0, s>>>(z, d, H0bits);
+    return cudaGetLastError();
+}

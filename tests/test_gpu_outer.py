@@ -34,6 +34,26 @@ def test_barycenter_matches_oracle(ctx, d, gamma, lam, steps, T):
     assert abs(z.sum() - z_ref.sum()) <= 1e-6 * z_ref.sum()
 
 
+@pytest.mark.parametrize("d,gamma,lam,steps,T", [(16, 1e-2, 2.0, 5, 200), (32, 5e-3, 5.0, 4, 300)])
+def test_sharpened_barycenter_matches_oracle(ctx, d, gamma, lam, steps, T):
+    """NEXT-2 entropic sharpening after every Alg. 2 step (target: the largest
+    input entropy): same outer iterates as the oracle, and z's entropy stays at
+    or below the target."""
+    b, t, o, _ = inputs.mode_diagrams(4, 1, 15, 30, sigma=0.04, seed=d)
+    h, m = oracle.rasterize(b, t, o, d)
+    z_ref, e_ref = oracle.barycenter(d, gamma, h, lam, steps, T, 0.0, sharpen=True)
+    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=T, tol=0.0, bary_sharpen=1)
+    z, e = api.pd_barycenter(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), p, lam, steps)
+    torch.cuda.synchronize()
+    z, e = z.cpu().numpy(), e.cpu().numpy()
+    assert np.allclose(e, e_ref, rtol=1e-6, atol=0)
+    assert np.allclose(z, z_ref, rtol=1e-5, atol=1e-9 * z_ref.max())
+    w = z[z > 0] / z.sum()
+    H = -(w * np.log(w)).sum()
+    H0 = max(-(x[x > 0] / x.sum() * np.log(x[x > 0] / x.sum())).sum() for x in h.astype(np.float64))
+    assert H <= H0 + 1e-9
+
+
 def test_barycenter_from_given_start_and_zero_steps(ctx):
     d, gamma = 16, 1e-2
     b, t, o = inputs.random_diagrams(3, nmin=10, nmax=10, seed=1)
@@ -71,3 +91,6 @@ def test_outer_loops_reject_bad_arguments(ctx):
         api.pd_barycenter(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), p, -1.0, 3)
     with pytest.raises(api.PdError):
         api.pd_kmeans(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), 3, p, 1.0, 2, 1)
+    ps = api.pd_sinkhorn_default_params(1e-2, 8, bary_sharpen=1)
+    with pytest.raises(api.PdError):
+        api.pd_kmeans(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), 1, ps, 1.0, 1, 1)
