@@ -318,7 +318,6 @@ def run_ours(args):
         it = outs["iters"].cpu().numpy()
         cells += float(it.sum()) * 2 * (d * d + 1)
         iters_in_iter_kernel += int(np.maximum(it - 1, 0).sum())
-        pair_launches += float(len(it))   # each pair is loaded once by the launch that runs it to its stop
         lse_terms += float((it * terms).sum())
     torch.cuda.synchronize()
     barrier(ws)
@@ -375,7 +374,11 @@ def run_ours(args):
         src = f"{pk_kind} sm_max_mhz x 152 SMs x 16 MUFU ex2/clk (one exponential per log-sum-exp term)"
     traffic = None
     if precision == api.PD_FP32 and iter_launches:
-        # pair-launches: every pair is loaded once per launch it runs in
+        # pair loads: the first launch of a step loads every pair; the
+        # drain-time hand-overs reload at most 2 x 152 pairs (512-thread CTAs)
+        # and then at most 152 (1024-thread CTAs)
+        per_step = iter_launches / max(args.steps, 1)
+        pair_launches = args.steps * (P + (2 * NUM_SMS if per_step >= 2 else 0) + (NUM_SMS if per_step >= 3 else 0))
         traffic = LSE2_DRAM_BYTES_PER_PAIR_LAUNCH * pair_launches / iter_launches
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak if peak else None, "traffic": traffic, "kernel": kname, "peak_source": src,

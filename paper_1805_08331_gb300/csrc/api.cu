@@ -194,7 +194,7 @@ size_t pd_carve_ws(char* base, int P, int d, int dp, double gamma, SkWS* w, int*
     t.ctab = (float*)take(sizeof(float) * 5 * dp);
     t.order_buf = (int*)take(sizeof(int) * P);
     t.order = nullptr;
-    *counter = (int*)take(sizeof(int) * 4);
+    *counter = (int*)take(sizeof(int) * 8);
     if (w) *w = t;
     return off;
 }
@@ -260,7 +260,7 @@ static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* r
 // variant for the pairs whose supports do not fit on chip, then the FP64
 // global-memory kernel for the pairs too large for that or whose potentials
 // left the base-2 range, until
-// no pair is active.  counter: 4 device ints; hbuf: 4 host ints; c (may be
+// no pair is active.  counter: 8 device ints; hbuf: 4 host ints; c (may be
 // NULL) receives the per-launch profile records.
 static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hbuf, cudaStream_t s) {
     cudaError_t e;
@@ -291,7 +291,8 @@ static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hb
         w.order = w.order_buf;
     }
     // a pair can spend one round in each of the two hand-overs between kernels
-    const int max_rounds = r.max_iter / n_inner + 4;
+    // and one in each of the two widenings below
+    const int max_rounds = r.max_iter / n_inner + 6;
     const int gbits = sk_lse2_grid_bits(w.gamma);
     size_t smem = 0;
     if (gbits >= 0) {
@@ -323,11 +324,21 @@ static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hb
     int active = w.P;
     bool any_gm = false, any_old = false;
     for (int round = 0; round < max_rounds; ++round) {
-        if ((e = cudaMemsetAsync(counter, 0, 4 * sizeof(int), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(counter, 0, 8 * sizeof(int), s)) != cudaSuccess) return e;
         {
             ProfScope ps(c, PD_K_ITER, s);
             const int threads = fixed_threads ? fixed_threads : (active > 2 * nsm ? 256 : (active > nsm ? 512 : 1024));
-            e = gbits >= 0 ? sk_launch_lse2(w, r, n_inner, counter, smem, gbits, threads, s)
+            // Widening: a pair alone on an SM iterates ~2x faster in a
+            // 512/1024-thread CTA than in a 256-thread CTA sharing the SM, so
+            // once no more than 2 (1) pairs per SM are left the launch hands
+            // them over to 512 (1024)-thread CTAs.
+            SkRun rl = r;
+            rl.exit_at = 0;
+            if (!fixed_threads && gbits >= 0 && n_inner == r.max_iter) {
+                if (threads == 256) rl.exit_at = active - 2 * nsm;
+                else if (threads == 512) rl.exit_at = active - nsm;
+            }
+            e = gbits >= 0 ? sk_launch_lse2(w, rl, n_inner, counter, smem, gbits, threads, s)
                            : sk_launch_lse_smem(w, r, n_inner, counter, counter + 1, s);
             if (e != cudaSuccess) return e;
         }

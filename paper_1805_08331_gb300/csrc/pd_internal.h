@@ -83,6 +83,11 @@ struct SkRun {
     double rel_thresh;   // relevance threshold (log) for the intermediate fits
     int pot_support_only; // finalize: potentials on the supports and Delta only
     int eps_stages;       // gamma-continuation stages before the target gamma (PD_FP32)
+    // on-chip base-2 kernel: once counter[4] (pairs of the launch that stopped
+    // or moved tier) reaches exit_at, the pairs still iterating save their
+    // state and return, so that the host relaunches them in wider CTAs
+    // (0: never)
+    int exit_at;
 };
 
 cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s);

@@ -189,7 +189,13 @@ struct L2Consts {
     uint32_t L1;     // float2 [nr][32] stage-1 (max, sum), swizzled columns
     int d;
     float gsc, ginv, lim;
+    float escale;    // 2^40 / total mass (marginal-error terms in fixed point)
 };
+
+// Lanes of the Delta-output sum: a fixed partition (thread t < L2_DLANES sums
+// the input cells t, t + L2_DLANES, ...), so the sum, like every other sum of
+// the kernel, is the same for every CTA width.
+#define L2_DLANES 256
 
 // Lanes per output cell in stage 2 (NT / 4 cells per pass).  Wider groups
 // measured slower: the per-cell epilogue runs on one lane of the group.
@@ -204,9 +210,12 @@ __device__ __forceinline__ int l2_lidx(int r, int cc) {
 }
 
 // New potential -(shift + log2 tot) as a (grid, rest) pair; err term
-// w |exp(old - new) - 1| added when want_err.  Returns false if out of range.
+// w |exp(old - new) - 1| added when want_err, in units of 2^-40 of the total
+// mass as a 64-bit integer: integer sums are exact, so err_t does not depend
+// on which thread adds which cell (terms above 2^4 of the mass saturate, a
+// non-finite term sets errbad).  Returns false if out of range.
 __device__ __forceinline__ bool l2_update(float tot, float shift, float Ms, float2 po, float wgt, bool want_err,
-                                          const L2Consts& K, float& errs, float2& pn) {
+                                          const L2Consts& K, long long& errq, bool& errbad, float2& pn) {
     if (!(tot > 0.f && isfinite(tot) && isfinite(shift))) return false;
     int ex;
     const float l = l2_log2(tot, ex);
@@ -216,18 +225,20 @@ __device__ __forceinline__ bool l2_update(float tot, float shift, float Ms, floa
         // old - new = po.y + log2(tot) (+ po.x + shift, zero unless the exact path ran)
         const float ev = (shift == Ms) ? (tot - 1.f) + tot * expm1f(po.y * 0.69314718f)
                                        : tot * exp2f((po.x + shift) + po.y) - 1.f;
-        errs += wgt * fabsf(ev);
+        const float term = wgt * fabsf(ev);
+        const float v = term * K.escale;
+        errbad |= !isfinite(term);
+        errq += v <= 0x1p44f ? llrintf(v) : (1ll << 44);
     }
     return fabsf(pn.x) < K.lim;
 }
 
 // One half-step: out.pot <- -LSE over the input side.  Adds the marginal-error
-// terms of `out` to errs when want_err.  Sets *range_flag if a potential left
+// terms of `out` to errq when want_err.  Sets *range_flag if a potential left
 // the exact range (the pair then moves to the FP64 kernel).
 template <int NT, bool GM>
-static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool want_err, float& errs,
-                               float* redD, int* range_flag, unsigned char* gb) {
-    constexpr int NW = NT / 32;
+static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool want_err, long long& errq,
+                               bool& errbad, float* redD, int* range_flag, unsigned char* gb) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int d = K.d;
     const int in_n = in.n, in_nr = in.nr;
@@ -244,20 +255,20 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
     const float MsD = -out.potD.x;
     {
         float sD = 0.f;
-        if (doD) {
-            for (int q = t; q < in_n; q += NT) {
+        if (doD && t < L2_DLANES) {
+            for (int q = t; q < in_n; q += L2_DLANES) {
                 const float2 h = in_hin[q];
                 const float2 c = cdt[abs((int)in_col[q] - (int)in_row[q])];
                 sD += l2_ex2(((h.x - c.x) - MsD) + (h.y - c.y));
             }
         }
         sD = warp_sum(sD);
-        if (lane == 0) redD[wid] = sD;
+        if (lane == 0 && wid < L2_DLANES / 32) redD[wid] = sD;
     }
     __syncthreads();
     if (t == 0 && doD) {
         float tot = 0.f;
-        for (int q = 0; q < NW; ++q) tot += redD[q];
+        for (int q = 0; q < L2_DLANES / 32; ++q) tot += redD[q];
         const float2 hD = in.hinD;
         if (hD.x > -INFINITY) tot += exp2f((hD.x - MsD) + hD.y);
         float shift = MsD;
@@ -274,7 +285,7 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
             }
         }
         float2 pn;
-        if (l2_update(tot, shift, MsD, out.potD, out.wD, want_err, K, errs, pn)) {
+        if (l2_update(tot, shift, MsD, out.potD, out.wD, want_err, K, errq, errbad, pn)) {
             out.potD = pn;
             out.hinD = make_float2(out.lwD.x + pn.x, out.lwD.y + pn.y);
         } else {
@@ -392,7 +403,8 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
                 }
                 if (live && g == 0) {
                     float2 pn;
-                    if (l2_update(tot, shift, Ms, po, sdp<float, GM>(gb, out.w)[qo], want_err, K, errs, pn)) {
+                    if (l2_update(tot, shift, Ms, po, sdp<float, GM>(gb, out.w)[qo], want_err, K, errq, errbad,
+                                  pn)) {
                         out_pot[qo] = pn;
                         const float2 lw = sdp<float2, GM>(gb, out.lw)[qo];
                         sdp<float2, GM>(gb, out.hin)[qo] = make_float2(lw.x + pn.x, lw.y + pn.y);
@@ -412,16 +424,22 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
 // arrays in the pair's FP64 scratch L64 (gcap bytes); a pair whose arrays
 // exceed it moves to IC_BIG = 2 (the FP64 global-memory kernel), as does any
 // pair whose potentials leave the exact range.  counter[0]: pairs still
-// active; counter[1]: pairs moved to 1; counter[3]: pairs moved to 2.
+// active; counter[1]: pairs moved to 1; counter[3]: pairs moved to 2;
+// counter[4] (r.exit_at > 0, on-chip variant): pairs of this launch that
+// stopped or moved.  Once it reaches r.exit_at, the pairs still iterating
+// leave at their next 16-iteration check with their state saved (they stay
+// active and the host runs them on in wider CTAs).
 template <int NT, bool GM>
 __global__ void __launch_bounds__(NT, (NT <= 256 ? 3 : (NT <= 512 ? 2 : 1)))
 sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t gcap, int gbits) {
     constexpr int NW = NT / 32;
     __shared__ L2Side S[2];
-    __shared__ float redD[NW], redE[NW];
+    __shared__ float redD[NW];
+    __shared__ long long redE[NW];
     __shared__ int wcnt[NW > L2_MAXCH ? NW : L2_MAXCH];
     __shared__ int cnt[4];
-    __shared__ int range_flag, fits;
+    __shared__ int range_flag, fits, leave;
+    const bool can_leave = !GM && r.exit_at > 0;
     const int p = w.order ? w.order[blockIdx.x] : blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
     PairPtrs q = pair_ptrs(w, p);
     if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG] != (GM ? 1 : 0)) return;
@@ -437,7 +455,12 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     }
     __syncthreads();
     if (!fits) {
-        if (t == 0) { q.ic[IC_BIG] = GM ? 2 : 1; atomicAdd(&counter[GM ? 3 : 1], 1); atomicAdd(&counter[0], 1); }
+        if (t == 0) {
+            q.ic[IC_BIG] = GM ? 2 : 1;
+            atomicAdd(&counter[GM ? 3 : 1], 1);
+            atomicAdd(&counter[0], 1);
+            if (can_leave) atomicAdd(&counter[4], 1);
+        }
         return;
     }
     unsigned char* gb = GM ? reinterpret_cast<unsigned char*>(q.L64) : nullptr;
@@ -529,28 +552,32 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     K.d = d;
     K.gsc = (float)gsc; K.ginv = (float)(1.0 / gsc);
     K.lim = (float)ldexp(1.0, 21 - gbits);   // |potential| bound keeping every sum of grid words exact
-    const float inv_total = (float)(1.0 / q.sc[SC_TOTAL]);
+    K.escale = q.sc[SC_TOTAL] > 0 ? (float)(ldexp(1.0, 40) / q.sc[SC_TOTAL]) : 0.f;
     const float tolf = (float)r.tol;
     int iters = q.ic[IC_ITERS];
     float errf = (float)q.sc[SC_ERR];
     int status = ST_ACTIVE;
     bool moved = false;
     for (int it = 0; it < n_inner; ++it) {
-        float errs = 0.f;
-        l2_half<NT, GM>(S[1], S[0], K, false, errs, redD, &range_flag, gb);   // u-update: phi from psi
-        errs = 0.f;
-        l2_half<NT, GM>(S[0], S[1], K, true, errs, redD, &range_flag, gb);    // v-update: psi from phi, err_t
-        errs = warp_sum(errs);
-        if (lane == 0) redE[wid] = errs;
-        __syncthreads();
-        float e = 0.f;
+        long long errq = 0;
+        bool errbad = false;
+        l2_half<NT, GM>(S[1], S[0], K, false, errq, errbad, redD, &range_flag, gb);   // u-update: phi from psi
+        l2_half<NT, GM>(S[0], S[1], K, true, errq, errbad, redD, &range_flag, gb);    // v-update: psi from phi, err_t
+        errq = warp_sum(errq);
+        if (lane == 0) redE[wid] = errq;
+        // written next to redE and read after the same barrier (the next write
+        // is behind the barriers of the next iteration's half-steps)
+        if (t == 0) leave = can_leave && (it & 15) == 15 && *(volatile int*)&counter[4] >= r.exit_at;
+        const int bad = __syncthreads_or(errbad);
+        long long e = 0;
         for (int k = 0; k < NW; ++k) e += redE[k];
-        errf = e * inv_total;
+        errf = bad ? INFINITY : (float)((double)e * 0x1p-40);
         ++iters;
         if (range_flag) { moved = true; break; }
         if (r.tol > 0 && errf <= tolf) { status = ST_CONVERGED; break; }
         if (iters >= r.max_iter) { status = ST_MAXITER; break; }
         if (!isfinite(errf)) { status = ST_RANGE; break; }
+        if (leave) break;   // status stays ST_ACTIVE: relaunched in a wider CTA
     }
     // ---- store the potentials (FP64, natural units)
     const double LN2 = 0.6931471805599453;
@@ -574,6 +601,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
             q.ic[IC_STATUS] = status;
             if (status == ST_ACTIVE) atomicAdd(&counter[0], 1);
         }
+        if (can_leave && (moved || status != ST_ACTIVE)) atomicAdd(&counter[4], 1);
     }
 }
 

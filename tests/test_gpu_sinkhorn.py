@@ -88,6 +88,35 @@ def test_small_gamma_fixed_iterations(ctx, d, gamma):
     assert rel.max() <= 1e-6, rel
 
 
+def test_cta_width_and_widening_leave_results_bitwise_equal(ctx, monkeypatch):
+    """The base-2 kernel sums in the same order at 256, 512 and 1024 threads
+    per pair (stage-1 and stage-2 sums are per element or per 4-lane group,
+    the Delta sum has a fixed 256-lane partition, the marginal error is an
+    exact fixed-point sum), so costs, potentials, errors and iteration counts
+    are bitwise equal across CTA widths, and handing the last pairs of a
+    launch to wider CTAs (which pairs depends on timing) changes no result."""
+    d, gamma, P = 32, 1e-2, 400
+    b, t, o = inputs.random_diagrams(2 * P, nmin=10, nmax=150, seed=77)
+    h, _ = oracle.rasterize(b, t, o, d)
+    runs = {}
+    for thr in ("256", "512", "1024", None):
+        if thr:
+            monkeypatch.setenv("PD_LSE2_THREADS", thr)
+        else:
+            monkeypatch.delenv("PD_LSE2_THREADS", raising=False)
+        ctx.profile_enable(True)
+        before = ctx.profile_read().get("iter", (0.0, 0))[1]
+        runs[thr] = _solve(ctx, h[0::2], h[1::2], d, gamma, 3000, 1e-6, want_potentials=True)
+        runs[thr]["launches"] = ctx.profile_read().get("iter", (0.0, 0))[1] - before
+        ctx.profile_enable(False)
+    ref = runs["256"]
+    assert ref["launches"] == 1 and len(set(ref["iters"].tolist())) > 50   # one launch; varied stops
+    assert runs[None]["launches"] > 1                                      # the widening ran
+    for thr, r in runs.items():
+        for k in ("cost", "iters", "err", "status", "f", "g"):
+            assert np.array_equal(r[k], ref[k]), (thr, k)
+
+
 @pytest.mark.parametrize("tier", ["gm", "fp64"])
 def test_kernel_tiers_match_oracle(ctx, tier, monkeypatch):
     """Every pair forced into the global-memory variant of the base-2 kernel
