@@ -197,6 +197,41 @@ pd_status pd_barycenter(pd_ctx* ctx, const uint32_t* hist, const uint32_t* mass,
                         const double* z_init, double* z_out, double* energy, pd_stream stream);
 
 /*
+ * pd_barycenter_grad / pd_barycenter_apply -- one Alg. 2 step split at its only
+ * exchange: the gradient of the smoothed energy (gradient proposition of
+ * Sec. 4) is a sum over the diagrams, so a batch of diagrams sharded across
+ * processes (one GPU each) computes per-shard sums, adds them across the
+ * shards (an all-reduce of k*d*d + 2k doubles), and applies the same update
+ * everywhere.  With one shard the two calls give bitwise the step of
+ * pd_barycenter (k = 1) or of pd_kmeans' centroid update.
+ *
+ * pd_barycenter_grad solves this shard's N pairs (z_c + R a_n, a_n + R z_c),
+ * c = owner[n], with the PD_FP32 engine and writes, for every measure c and
+ * cell x:
+ *   gsum[c][x] = sum over the shard's n with owner[n] = c of f_n(x) + g_n(Delta)
+ *                (in diagram order; 0 where z_c(x) <= 0),
+ *   count[c]   = the number of those n,
+ *   cost_sum[c]= the sum of their transport costs <P_n, C>.
+ *   hist, mass : uint32 [N][d][d], uint32 [N] (device): this shard's diagrams
+ *   k, z       : number of measures; double [k][d*d] (device, read only)
+ *   owner      : int32 [N] (device) or NULL (every n belongs to measure 0)
+ *   g_warm     : double [N][d*d+1] (device) or NULL: the pairs' potentials g,
+ *                written on return; read as the warm start when warm != 0
+ *   gsum       : double [k][d*d]; count, cost_sum: double [k] (device, output)
+ *   params     : as pd_barycenter (PD_FP32; bary_sharpen must be 0)
+ * pd_barycenter_apply updates z in place with the summed values:
+ *   z_c(x) <- z_c(x) exp(-lambda (gamma log z_c(x) + gamma log|z_c| + gsum[c][x] / count[c]))
+ * where z_c(x) > 0 and count[c] > 0 (measures with count 0 are unchanged).
+ * Both synchronise `stream`.  Errors: PD_ERR_INVALID, PD_ERR_OOM, PD_ERR_CUDA.
+ */
+pd_status pd_barycenter_grad(pd_ctx* ctx, const uint32_t* hist, const uint32_t* mass, int N, int k,
+                             const pd_sinkhorn_params* params, const double* z, const int32_t* owner,
+                             double* g_warm, int warm, double* gsum, double* count, double* cost_sum,
+                             pd_stream stream);
+pd_status pd_barycenter_apply(pd_ctx* ctx, double* z, int k, int d, const double* gsum, const double* count,
+                              double gamma, double lambda, pd_stream stream);
+
+/*
  * pd_kmeans -- k-means on persistence diagrams (Sec. 5): centroids start as k
  * distinct input histograms drawn by splitmix64(seed) (draw r mod N, repeats
  * skipped).  Each round assigns every diagram n to argmin_c <P, C> of the pair

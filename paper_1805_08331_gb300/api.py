@@ -25,7 +25,8 @@ EXPORTED = ["pd_abi_version", "pd_ctx_create", "pd_ctx_destroy", "pd_last_error"
             "pd_sinkhorn_default_params", "pd_sinkhorn_batch", "pd_profile_enable", "pd_profile_read",
             "pd_sinkhorn_batch_noalloc", "pd_barycenter", "pd_kmeans", "pd_serve_default_config",
             "pd_serve_create", "pd_serve_load_centroids", "pd_serve_submit", "pd_serve_poll", "pd_serve_wait",
-            "pd_serve_inject_failure", "pd_serve_destroy", "pd_sinkhorn_bounds"]
+            "pd_serve_inject_failure", "pd_serve_destroy", "pd_sinkhorn_bounds", "pd_barycenter_grad",
+            "pd_barycenter_apply"]
 PD_Q_DISTANCE, PD_Q_NEAREST = 0, 1
 SERVE_D = (32, 64, 128, 256)
 PD_K_RASTER, PD_K_SETUP, PD_K_LOGSTEP, PD_K_ABSORB, PD_K_ITER, PD_K_FINALIZE, PD_K_COUNT = 0, 1, 2, 3, 4, 5, 16
@@ -107,6 +108,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                       ctypes.c_int, _vp, _vp, _vp, _vp]
         lib.pd_kmeans.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SinkhornParams),
                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _vp, _vp, _vp, _vp]
+        lib.pd_barycenter_grad.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SinkhornParams),
+                                           _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+        lib.pd_barycenter_apply.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double,
+                                            ctypes.c_double, _vp]
         lib.pd_serve_default_config.argtypes = [ctypes.POINTER(ServeConfig)]
         lib.pd_serve_default_config.restype = None
         lib.pd_serve_create.argtypes = [_vp, ctypes.POINTER(ServeConfig), ctypes.POINTER(_vp)]
@@ -255,6 +260,33 @@ def pd_barycenter(ctx: Context, hist, mass, params: SinkhornParams, lam: float, 
     ctx.check(ctx.lib.pd_barycenter(ctx.handle, _ptr(hist), _ptr(mass), int(hist.shape[0]), ctypes.byref(params),
                                     float(lam), int(outer_iters), _ptr(z_init), _ptr(z), _ptr(e), _stream(stream)))
     return z, e[:outer_iters]
+
+
+def pd_barycenter_grad(ctx: Context, hist, mass, params: SinkhornParams, z, k: int = 1, owner=None, g_warm=None,
+                       warm: bool = False, stream=None):
+    """Per-shard half of an Alg. 2 step (see include/pd_ot.h).  z: float64
+    CUDA tensor [k, d, d] (or [d, d] for k = 1); owner: int32 [N] or None;
+    g_warm: float64 [N, d*d+1] or None (written; read when warm).  Returns
+    (gsum [k, d*d], count [k], cost_sum [k]) float64 CUDA tensors."""
+    import torch
+    d, N = params.d, int(hist.shape[0])
+    gsum = torch.empty((k, d * d), dtype=torch.float64, device=hist.device)
+    count = torch.empty(k, dtype=torch.float64, device=hist.device)
+    csum = torch.empty(k, dtype=torch.float64, device=hist.device)
+    ctx.check(ctx.lib.pd_barycenter_grad(ctx.handle, _ptr(hist), _ptr(mass), N, int(k), ctypes.byref(params), _ptr(z),
+                                         _ptr(owner), _ptr(g_warm), 1 if warm else 0, _ptr(gsum), _ptr(count),
+                                         _ptr(csum), _stream(stream)))
+    return gsum, count, csum
+
+
+def pd_barycenter_apply(ctx: Context, z, gsum, count, gamma: float, lam: float, stream=None):
+    """Second half of the step: z (float64 [k, d, d] or [d, d], updated in
+    place) from the summed gsum [k, d*d] and count [k]."""
+    k = int(count.shape[0])
+    d = int(z.shape[-1])
+    ctx.check(ctx.lib.pd_barycenter_apply(ctx.handle, _ptr(z), k, d, _ptr(gsum), _ptr(count), float(gamma),
+                                          float(lam), _stream(stream)))
+    return z
 
 
 def pd_kmeans(ctx: Context, hist, mass, k: int, params: SinkhornParams, lam: float, rounds: int, bary_steps: int,

@@ -638,6 +638,74 @@ extern "C" pd_status pd_barycenter(pd_ctx* c, const uint32_t* hist, const uint32
     return PD_OK;
 }
 
+// Sharded Alg. 2 step, first half: solve this shard's pairs
+// (z_owner[n] + R a_n, a_n + R z_owner[n]) and sum their gradient terms per
+// measure (the caller adds the sums of all shards, then calls
+// pd_barycenter_apply).
+extern "C" pd_status pd_barycenter_grad(pd_ctx* c, const uint32_t* hist, const uint32_t* mass, int N, int k,
+                                        const pd_sinkhorn_params* prm, const double* z, const int32_t* owner,
+                                        double* g_warm, int warm, double* gsum, double* count, double* cost_sum,
+                                        pd_stream stream) {
+    if (!c) return PD_ERR_INVALID;
+    c->err.clear();
+    pd_status st = check_params(c, prm, "pd_barycenter_grad");
+    if (st == PD_OK && prm->bary_sharpen)
+        return fail(c, PD_ERR_INVALID, "pd_barycenter_grad: bary_sharpen is not supported (sharpening is not part of the sharded step)");
+    if (st != PD_OK) return st;
+    if (N < 1 || k < 1 || !hist || !mass || !z || !gsum || !count || !cost_sum || (warm && !g_warm))
+        return fail(c, PD_ERR_INVALID, "pd_barycenter_grad: need N >= 1, k >= 1, non-NULL hist, mass, z, gsum, count, "
+                                       "cost_sum, and g_warm when warm");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const int d = prm->d, n1 = d * d + 1;
+    Arena a{nullptr, 0};
+    auto layout = [&](Arena& ar, double** f, double** g, double** cost, int32_t** pairs, int32_t** iters, float** err,
+                      int32_t** status) {
+        *f = ar.take<double>((size_t)N * n1); *g = ar.take<double>(g_warm ? 0 : (size_t)N * n1);
+        *cost = ar.take<double>(N); *pairs = ar.take<int32_t>(2 * (size_t)N); *iters = ar.take<int32_t>(N);
+        *err = ar.take<float>(N); *status = ar.take<int32_t>(N);
+    };
+    double *f, *g, *cost; int32_t *pairs, *iters, *status; float* err;
+    layout(a, &f, &g, &cost, &pairs, &iters, &err, &status);
+    st = ensure_buffer(c, &c->ws2, &c->ws2_bytes, a.off, s);
+    if (st != PD_OK) return st;
+    a = Arena{(char*)c->ws2, 0};
+    layout(a, &f, &g, &cost, &pairs, &iters, &err, &status);
+    if (g_warm) g = g_warm;
+    SkWS w;
+    int* counter;
+    st = sinkhorn_ws(c, N, prm, &w, &counter, s);
+    if (st != PD_OK) return st;
+    CUDA_TRY(c, outer_owner_pairs(owner, N, pairs, s));
+    w.histA = nullptr; w.massA = nullptr; w.wA = z;            // a side: z_c + R a_n
+    w.histB = hist; w.massB = mass; w.wB = nullptr;            // b side: a_n + R z_c
+    w.pairs = pairs;
+    SkRun r = make_run(prm);
+    r.pot_support_only = 1;
+    st = lse_solve(c, w, r, warm ? g : nullptr, cost, nullptr, nullptr, f, g, iters, err, status, counter, s);
+    if (st != PD_OK) return st;
+    CUDA_TRY(c, outer_bary_grad(z, f, g, owner, N, k, d, gsum, count, s));
+    CUDA_TRY(c, outer_cost_sum(cost, owner, N, k, cost_sum, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+// Sharded Alg. 2 step, second half: z_c <- z_c exp(-lambda grad_c) from the
+// summed per-shard values.
+extern "C" pd_status pd_barycenter_apply(pd_ctx* c, double* z, int k, int d, const double* gsum, const double* count,
+                                         double gamma, double lambda, pd_stream stream) {
+    if (!c) return PD_ERR_INVALID;
+    c->err.clear();
+    if (!z || !gsum || !count || k < 1 || d < 2 || d > 256 || !(gamma > 0) || !(lambda > 0))
+        return fail(c, PD_ERR_INVALID, "pd_barycenter_apply: need z, gsum, count, k >= 1, 2 <= d <= 256, "
+                                       "gamma > 0, lambda > 0");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, outer_bary_apply(z, gsum, count, k, d, gamma, lambda, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
 // splitmix64 (Steele, Lea & Flood, OOPSLA 2014).
 static uint64_t splitmix64_next(uint64_t* st) {
     uint64_t z = (*st += 0x9E3779B97F4A7C15ull);

@@ -35,6 +35,29 @@ __global__ void measure_mass_kernel(const double* __restrict__ z, int d, double*
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
+// Gradient of measure c at cell x, split as
+//     mean_i grad_i(x) = gamma log z_c(x) + gamma log|z_c| + (sum_i (f_i(x) + g_i(Delta))) / m,
+// the sum over the m diagrams i owned by c taken in diagram order.  The one-GPU
+// step and the sharded form (per-shard sums added across ranks, then applied)
+// use these same two helpers.
+__device__ __forceinline__ double bary_fg_sum(const double* __restrict__ f, const double* __restrict__ g,
+                                              const int32_t* __restrict__ owner, int N, int c, int x, int D,
+                                              int& m) {
+    const int n1 = D + 1;
+    double s = 0.0;
+    m = 0;
+    for (int i = 0; i < N; ++i) {
+        if (owner && owner[i] != c) continue;
+        s += f[(size_t)i * n1 + x] + g[(size_t)i * n1 + D];
+        ++m;
+    }
+    return s;
+}
+__device__ __forceinline__ double bary_update(double zx, double zmass, double fgsum, double m, double gamma,
+                                              double lambda) {
+    return zx * exp(-lambda * ((gamma * log(zx) + gamma * log(zmass)) + fgsum / m));
+}
+
 // Multiplicative gradient step for k measures at once.  Diagram n belongs to
 // measure owner[n] (owner == NULL: all to measure 0); f, g are the potentials of
 // the pair (z_owner[n] + R a_n, a_n + R z_owner[n]) with n = d*d+1 entries per pair.
@@ -43,22 +66,66 @@ __global__ void bary_step_kernel(double* __restrict__ z, const double* __restric
                                  const double* __restrict__ f, const double* __restrict__ g,
                                  const int32_t* __restrict__ owner, int N, int k, int d, double gamma,
                                  double lambda) {
-    const int D = d * d, n1 = D + 1;
+    const int D = d * d;
     const int64_t tot = (int64_t)k * D;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(e / D), x = (int)(e % D);
         double* zc = z + (size_t)c * D;
         const double zx = zc[x];
         if (!(zx > 0.0)) continue;
-        const double base = gamma * log(zx) + gamma * log(zmass[c]);
-        double s = 0.0;
-        int m = 0;
-        for (int i = 0; i < N; ++i) {
-            if (owner && owner[i] != c) continue;
-            s += base + f[(size_t)i * n1 + x] + g[(size_t)i * n1 + D];
-            ++m;
+        int m;
+        const double s = bary_fg_sum(f, g, owner, N, c, x, D, m);
+        if (m > 0) zc[x] = bary_update(zx, zmass[c], s, (double)m, gamma, lambda);
+    }
+}
+
+// Sharded form, first half: gsum[c][x] = sum over this shard's diagrams owned
+// by c of f_i(x) + g_i(Delta) (0 where z_c(x) <= 0), count[c] = their number.
+__global__ void bary_grad_kernel(const double* __restrict__ z, const double* __restrict__ f,
+                                 const double* __restrict__ g, const int32_t* __restrict__ owner, int N, int k,
+                                 int d, double* __restrict__ gsum, double* __restrict__ count) {
+    const int D = d * d;
+    const int64_t tot = (int64_t)k * D;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / D), x = (int)(e % D);
+        int m;
+        const double sum = z[e] > 0.0 ? bary_fg_sum(f, g, owner, N, c, x, D, m) : 0.0;
+        gsum[e] = sum;
+        if (x == 0) {
+            int mc = 0;
+            for (int i = 0; i < N; ++i) mc += (!owner || owner[i] == c);
+            count[c] = (double)mc;
         }
-        if (m > 0) zc[x] = zx * exp(-lambda * (s / m));
+    }
+}
+
+// Sharded form, second half (one block of 512 threads per measure): |z_c| in
+// the same order as measure_mass_kernel, then the multiplicative update from
+// the summed gsum and count.
+__global__ void bary_apply_kernel(double* __restrict__ z, const double* __restrict__ gsum,
+                                  const double* __restrict__ count, int d, double gamma, double lambda) {
+    __shared__ double sh[32];
+    const int D = d * d, c = blockIdx.x;
+    double* zc = z + (size_t)c * D;
+    double s = 0.0;
+    for (int x = threadIdx.x; x < D; x += blockDim.x) s += zc[x];
+    const double zmass = block_sum(s, sh);
+    const double m = count[c];
+    if (!(m > 0.0)) return;
+    for (int x = threadIdx.x; x < D; x += blockDim.x) {
+        const double zx = zc[x];
+        if (zx > 0.0) zc[x] = bary_update(zx, zmass, gsum[(size_t)c * D + x], m, gamma, lambda);
+    }
+}
+
+// cost_sum[c] = sum of cost[n] over the diagrams n owned by c (diagram order).
+__global__ void cost_sum_kernel(const double* __restrict__ cost, const int32_t* __restrict__ owner, int N, int k,
+                                double* __restrict__ out) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < k; c += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < N; ++i)
+            if (!owner || owner[i] == c) s += cost[i];
+        out[c] = s;
     }
 }
 
@@ -134,6 +201,23 @@ cudaError_t outer_bary_step(double* z, const double* zmass, const double* f, con
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
     bary_step_kernel<<<blocks, 256, 0, s>>>(z, zmass, f, g, owner, N, k, d, gamma, lambda);
+    return cudaGetLastError();
+}
+cudaError_t outer_bary_grad(const double* z, const double* f, const double* g, const int32_t* owner, int N, int k,
+                            int d, double* gsum, double* count, cudaStream_t s) {
+    int64_t tot = (int64_t)k * d * d;
+    int blocks = (int)((tot + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    bary_grad_kernel<<<blocks, 256, 0, s>>>(z, f, g, owner, N, k, d, gsum, count);
+    return cudaGetLastError();
+}
+cudaError_t outer_bary_apply(double* z, const double* gsum, const double* count, int k, int d, double gamma,
+                             double lambda, cudaStream_t s) {
+    bary_apply_kernel<<<k, 512, 0, s>>>(z, gsum, count, d, gamma, lambda);
+    return cudaGetLastError();
+}
+cudaError_t outer_cost_sum(const double* cost, const int32_t* owner, int N, int k, double* out, cudaStream_t s) {
+    cost_sum_kernel<<<(k + 127) / 128, 128, 0, s>>>(cost, owner, N, k, out);
     return cudaGetLastError();
 }
 cudaError_t outer_mean(const double* cost, int N, double* out, cudaStream_t s) {

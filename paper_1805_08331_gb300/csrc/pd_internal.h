@@ -138,6 +138,12 @@ cudaError_t outer_measure_mass(const double* z, int k, int d, double* out, cudaS
 cudaError_t outer_bary_step(double* z, const double* zmass, const double* f, const double* g, const int32_t* owner,
                             int N, int k, int d, double gamma, double lambda, cudaStream_t s);
 cudaError_t outer_mean(const double* cost, int N, double* out, cudaStream_t s);
+// sharded Alg. 2 step: per-shard sums (gsum [k][d*d], count [k]), then the update from the summed values
+cudaError_t outer_bary_grad(const double* z, const double* f, const double* g, const int32_t* owner, int N, int k,
+                            int d, double* gsum, double* count, cudaStream_t s);
+cudaError_t outer_bary_apply(double* z, const double* gsum, const double* count, int k, int d, double gamma,
+                             double lambda, cudaStream_t s);
+cudaError_t outer_cost_sum(const double* cost, const int32_t* owner, int N, int k, double* out, cudaStream_t s);
 cudaError_t outer_km_assign(const double* cost, int N, int k, int32_t* assign, double* objective, cudaStream_t s);
 cudaError_t outer_km_seed(const uint32_t* hist, const int32_t* idx, int k, int d, double* z, cudaStream_t s);
 cudaError_t outer_km_pairs(int N, int k, int32_t* pairs, cudaStream_t s);

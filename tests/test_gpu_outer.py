@@ -94,3 +94,74 @@ def test_outer_loops_reject_bad_arguments(ctx):
     ps = api.pd_sinkhorn_default_params(1e-2, 8, bary_sharpen=1)
     with pytest.raises(api.PdError):
         api.pd_kmeans(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), 1, ps, 1.0, 1, 1)
+
+
+def test_sharded_step_one_shard_is_pd_barycenter_bitwise(ctx):
+    """pd_barycenter_grad + pd_barycenter_apply with one shard: bitwise the
+    z of pd_barycenter (same solves, same sums in the same order), from a
+    given start and from the default start; energies to the rounding of the
+    mean."""
+    from paper_1805_08331_gb300 import sharded
+    d, gamma, lam, steps = 32, 5e-3, 5.0, 4
+    b, t, o = inputs.random_diagrams(6, nmin=10, nmax=60, seed=11)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hist, mass = hists_to_gpu(h), dev(masses(h).view(np.int32))
+    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=3000, tol=1e-6)
+    for z_init in (None, torch.from_numpy(np.triu(np.full((d, d), 0.05))).cuda()):
+        z_ref, e_ref = api.pd_barycenter(ctx, hist, mass, p, lam, steps, z_init=z_init)
+        z, e = sharded.barycenter_sharded(ctx, hist, mass, p, lam, steps, z_init=z_init)
+        torch.cuda.synchronize()
+        assert torch.equal(z, z_ref)
+        assert np.allclose(e.cpu().numpy(), e_ref.cpu().numpy(), rtol=1e-13, atol=0)
+
+
+def test_sharded_step_two_shards_match_one_gpu(ctx):
+    """The exchange of the sharded step emulated on one GPU: the diagrams in two
+    shards, each with its own pd_barycenter_grad and warm potentials, the two
+    sums added (the all-reduce), one pd_barycenter_apply.  Each pair's solve is
+    the same in either batch (results do not depend on the batch), so z only
+    differs from pd_barycenter by the rounding of adding two partial sums."""
+    d, gamma, lam, steps = 32, 5e-3, 5.0, 4
+    b, t, o = inputs.random_diagrams(7, nmin=10, nmax=60, seed=12)
+    h, _ = oracle.rasterize(b, t, o, d)
+    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=3000, tol=1e-6)
+    z0 = torch.from_numpy(np.triu(np.full((d, d), 0.05))).cuda()
+    z_ref, e_ref = api.pd_barycenter(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), p, lam, steps, z_init=z0)
+    shards = [h[:3], h[3:]]
+    hs = [(hists_to_gpu(x), dev(masses(x).view(np.int32))) for x in shards]
+    gw = [torch.empty((len(x), d * d + 1), dtype=torch.float64, device="cuda") for x in shards]
+    z = z0.clone()
+    e = []
+    for step in range(steps):
+        parts = [api.pd_barycenter_grad(ctx, hh, mm, p, z, 1, None, g, step > 0) for (hh, mm), g in zip(hs, gw)]
+        gsum = parts[0][0] + parts[1][0]
+        count = parts[0][1] + parts[1][1]
+        csum = parts[0][2] + parts[1][2]
+        assert count.item() == len(h)
+        api.pd_barycenter_apply(ctx, z, gsum, count, gamma, lam)
+        e.append((csum / count).item())
+    torch.cuda.synchronize()
+    assert torch.allclose(z, z_ref, rtol=1e-9, atol=1e-12 * z_ref.max().item())
+    assert np.allclose(e, e_ref.cpu().numpy(), rtol=1e-9, atol=0)
+
+
+def test_sharded_step_k_measures_with_owner(ctx):
+    """k = 2 measures, owner per diagram: the per-measure sums equal the
+    one-measure sums over each measure's own diagrams."""
+    d, gamma = 16, 1e-2
+    b, t, o = inputs.random_diagrams(5, nmin=8, nmax=30, seed=13)
+    h, _ = oracle.rasterize(b, t, o, d)
+    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=2000, tol=1e-6)
+    z = torch.from_numpy(np.stack([np.triu(np.full((d, d), 0.1)), np.triu(np.full((d, d), 0.2))])).cuda()
+    owner = torch.tensor([1, 0, 1, 1, 0], dtype=torch.int32, device="cuda")
+    gsum, count, csum = api.pd_barycenter_grad(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), p, z, 2, owner)
+    assert count.cpu().tolist() == [2.0, 3.0]
+    for c in range(2):
+        idx = [n for n in range(5) if owner[n].item() == c]
+        hc = h[idx]
+        g1, n1, s1 = api.pd_barycenter_grad(ctx, hists_to_gpu(hc), dev(masses(hc).view(np.int32)), p, z[c], 1)
+        assert n1.item() == len(idx)
+        assert torch.equal(gsum[c], g1[0]) and torch.equal(csum[c], s1[0])
+    with pytest.raises(api.PdError):
+        api.pd_barycenter_grad(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)),
+                               api.pd_sinkhorn_default_params(gamma, d, bary_sharpen=1), z, 2, owner)
