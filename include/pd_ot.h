@@ -232,6 +232,23 @@ pd_status pd_barycenter_apply(pd_ctx* ctx, double* z, int k, int d, const double
                               double gamma, double lambda, pd_stream stream);
 
 /*
+ * pd_kmeans_assign -- the assignment half of a k-means round (Sec. 5) against
+ * given real-valued centroids: cold-started PD_FP32 solves of the N x k pairs
+ * (a_n + R z_c, z_c + R a_n), assign[n] = argmin_c <P, C> (ties to the lowest
+ * c), objective = sum_n min_c <P, C> (diagram order).  With
+ * pd_barycenter_grad / pd_barycenter_apply (k measures, owner = assign) it
+ * makes the k-means round of pd_kmeans for diagrams sharded across processes.
+ *   hist, mass : uint32 [N][d][d], uint32 [N] (device); centroids: double [k][d*d] (device)
+ *   assign     : int32 [N] (device, output)
+ *   cost       : double [N][k] or NULL (device, output: every pair's cost)
+ *   objective  : double [1] or NULL (device, output)
+ * Synchronises `stream`.  Errors: PD_ERR_INVALID, PD_ERR_OOM, PD_ERR_CUDA.
+ */
+pd_status pd_kmeans_assign(pd_ctx* ctx, const uint32_t* hist, const uint32_t* mass, int N, int k,
+                           const pd_sinkhorn_params* params, const double* centroids, int32_t* assign,
+                           double* cost, double* objective, pd_stream stream);
+
+/*
  * pd_kmeans -- k-means on persistence diagrams (Sec. 5): centroids start as k
  * distinct input histograms drawn by splitmix64(seed) (draw r mod N, repeats
  * skipped).  Each round assigns every diagram n to argmin_c <P, C> of the pair

@@ -26,7 +26,7 @@ EXPORTED = ["pd_abi_version", "pd_ctx_create", "pd_ctx_destroy", "pd_last_error"
             "pd_sinkhorn_batch_noalloc", "pd_barycenter", "pd_kmeans", "pd_serve_default_config",
             "pd_serve_create", "pd_serve_load_centroids", "pd_serve_submit", "pd_serve_poll", "pd_serve_wait",
             "pd_serve_inject_failure", "pd_serve_destroy", "pd_sinkhorn_bounds", "pd_barycenter_grad",
-            "pd_barycenter_apply"]
+            "pd_barycenter_apply", "pd_kmeans_assign"]
 PD_Q_DISTANCE, PD_Q_NEAREST = 0, 1
 SERVE_D = (32, 64, 128, 256)
 PD_K_RASTER, PD_K_SETUP, PD_K_LOGSTEP, PD_K_ABSORB, PD_K_ITER, PD_K_FINALIZE, PD_K_COUNT = 0, 1, 2, 3, 4, 5, 16
@@ -112,6 +112,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                            _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
         lib.pd_barycenter_apply.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double,
                                             ctypes.c_double, _vp]
+        lib.pd_kmeans_assign.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SinkhornParams),
+                                         _vp, _vp, _vp, _vp, _vp]
         lib.pd_serve_default_config.argtypes = [ctypes.POINTER(ServeConfig)]
         lib.pd_serve_default_config.restype = None
         lib.pd_serve_create.argtypes = [_vp, ctypes.POINTER(ServeConfig), ctypes.POINTER(_vp)]
@@ -287,6 +289,20 @@ def pd_barycenter_apply(ctx: Context, z, gsum, count, gamma: float, lam: float, 
     ctx.check(ctx.lib.pd_barycenter_apply(ctx.handle, _ptr(z), k, d, _ptr(gsum), _ptr(count), float(gamma),
                                           float(lam), _stream(stream)))
     return z
+
+
+def pd_kmeans_assign(ctx: Context, hist, mass, params: SinkhornParams, centroids, want_cost=False, stream=None):
+    """Assignment of N histograms to the k centroids (float64 CUDA tensor
+    [k, d, d]).  Returns (assign [N] int32, objective [1] float64, cost [N, k]
+    float64 or None) as CUDA tensors."""
+    import torch
+    N, k = int(hist.shape[0]), int(centroids.shape[0])
+    assign = torch.empty(N, dtype=torch.int32, device=hist.device)
+    obj = torch.empty(1, dtype=torch.float64, device=hist.device)
+    cost = torch.empty((N, k), dtype=torch.float64, device=hist.device) if want_cost else None
+    ctx.check(ctx.lib.pd_kmeans_assign(ctx.handle, _ptr(hist), _ptr(mass), N, k, ctypes.byref(params),
+                                       _ptr(centroids), _ptr(assign), _ptr(cost), _ptr(obj), _stream(stream)))
+    return assign, obj, cost
 
 
 def pd_kmeans(ctx: Context, hist, mass, k: int, params: SinkhornParams, lam: float, rounds: int, bary_steps: int,

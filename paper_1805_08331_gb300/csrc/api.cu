@@ -690,6 +690,51 @@ extern "C" pd_status pd_barycenter_grad(pd_ctx* c, const uint32_t* hist, const u
     return PD_OK;
 }
 
+// k-means assignment (Sec. 5) of N diagrams to k real-valued centroids:
+// cold-started solves of (a_n + R z_c, z_c + R a_n) for every n, c, then
+// argmin_c (ties to the lowest c) and sum_n min_c cost.
+extern "C" pd_status pd_kmeans_assign(pd_ctx* c, const uint32_t* hist, const uint32_t* mass, int N, int k,
+                                      const pd_sinkhorn_params* prm, const double* centroids, int32_t* assign,
+                                      double* cost, double* objective, pd_stream stream) {
+    if (!c) return PD_ERR_INVALID;
+    c->err.clear();
+    pd_status st = check_params(c, prm, "pd_kmeans_assign");
+    if (st != PD_OK) return st;
+    if (N < 1 || k < 1 || !hist || !mass || !centroids || !assign)
+        return fail(c, PD_ERR_INVALID, "pd_kmeans_assign: need N >= 1, k >= 1, non-NULL hist, mass, centroids, assign");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const size_t NK = (size_t)N * k;
+    if (NK > (size_t)INT32_MAX) return fail(c, PD_ERR_INVALID, "pd_kmeans_assign: N * k too large");
+    Arena a{nullptr, 0};
+    auto layout = [&](Arena& ar, double** cst, int32_t** pairs, int32_t** iters, float** err, int32_t** status) {
+        *cst = ar.take<double>(cost ? 0 : NK); *pairs = ar.take<int32_t>(2 * NK); *iters = ar.take<int32_t>(NK);
+        *err = ar.take<float>(NK); *status = ar.take<int32_t>(NK);
+    };
+    double* cst; int32_t *pairs, *iters, *status; float* err;
+    layout(a, &cst, &pairs, &iters, &err, &status);
+    st = ensure_buffer(c, &c->ws2, &c->ws2_bytes, a.off, s);
+    if (st != PD_OK) return st;
+    a = Arena{(char*)c->ws2, 0};
+    layout(a, &cst, &pairs, &iters, &err, &status);
+    if (cost) cst = cost;
+    SkWS w;
+    int* counter;
+    st = sinkhorn_ws(c, (int)NK, prm, &w, &counter, s);
+    if (st != PD_OK) return st;
+    CUDA_TRY(c, outer_km_pairs(N, k, pairs, s));
+    w.histA = hist; w.massA = mass; w.wA = nullptr;
+    w.histB = nullptr; w.massB = nullptr; w.wB = centroids;
+    w.pairs = pairs;
+    SkRun r = make_run(prm);
+    r.pot_support_only = 0;
+    st = lse_solve(c, w, r, nullptr, cst, nullptr, nullptr, nullptr, nullptr, iters, err, status, counter, s);
+    if (st != PD_OK) return st;
+    CUDA_TRY(c, outer_km_assign(cst, N, k, assign, objective, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
 // Sharded Alg. 2 step, second half: z_c <- z_c exp(-lambda grad_c) from the
 // summed per-shard values.
 extern "C" pd_status pd_barycenter_apply(pd_ctx* c, double* z, int k, int d, const double* gsum, const double* count,

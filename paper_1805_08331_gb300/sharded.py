@@ -1,5 +1,5 @@
-"""Alg. 2 (smoothed barycenter) over diagrams sharded across processes, one GPU
-each.
+"""Alg. 2 (smoothed barycenter) and the k-means of Sec. 5 over diagrams sharded
+across processes, one GPU each.
 
 The gradient of the smoothed energy (gradient proposition of Sec. 4) is a sum
 over the diagrams, so a step splits at one exchange: every rank solves the
@@ -7,7 +7,9 @@ pairs (z + R a_n, a_n + R z) of its own diagrams and sums their gradient terms
 (``pd_barycenter_grad``), the per-rank sums are added by one all-reduce of
 d*d + 2 doubles, and every rank applies the same multiplicative update
 (``pd_barycenter_apply``), so z stays identical on all ranks.  With one rank
-the result is bitwise that of ``pd_barycenter``.  The arithmetic runs in the
+the result is bitwise that of ``pd_barycenter``.  k-means adds a local
+assignment per round (``pd_kmeans_assign``) and runs the same split step for
+all k centroids at once, owner = assignment.  The arithmetic runs in the
 library's kernels; this module only moves the sums between the ranks.
 """
 from __future__ import annotations
@@ -65,3 +67,41 @@ def barycenter_sharded(ctx, hist, mass, params, lam, outer_iters, z_init=None, g
         ops["apply"](ctx, z, gsum, count, params.gamma, lam)
         energy[t] = csum[0] / count[0]
     return z, energy
+
+
+def kmeans_sharded(ctx, hist, mass, params, centroids_init, lam, rounds, bary_steps, group=None, ops=None):
+    """k-means rounds (Sec. 5) over diagrams sharded across the ranks of
+    ``group``: each rank assigns its own diagrams (``pd_kmeans_assign``), the
+    objective is summed across ranks, and each of the ``bary_steps`` Alg. 2
+    steps of the centroid update adds the per-rank, per-centroid sums
+    (``pd_barycenter_grad`` with owner = assignment; k*d*d + 2k doubles) before
+    ``pd_barycenter_apply``.  centroids_init: float64 [k, d, d], the same on
+    every rank (pd_kmeans with rounds = 0 gives its seeding).  With one rank the
+    result is bitwise that of pd_kmeans from the same centroids.  Returns
+    (assign [N_r] of the last round, centroids [k, d, d], objective [rounds])."""
+    import torch
+    ops = ops or {"assign": api.pd_kmeans_assign, "grad": api.pd_barycenter_grad, "apply": api.pd_barycenter_apply}
+    dist, ws = _world(group)
+    d = params.d
+    z = centroids_init.to(torch.float64).clone().contiguous()
+    k = int(z.shape[0])
+    n_local = int(hist.shape[0])
+
+    def allreduce(t):
+        if ws > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        return t
+
+    g_warm = torch.empty((n_local, d * d + 1), dtype=torch.float64, device=z.device)
+    objective = torch.empty(rounds, dtype=torch.float64, device=z.device)
+    assign = None
+    for rd in range(rounds):
+        assign, obj, _ = ops["assign"](ctx, hist, mass, params, z)
+        objective[rd] = allreduce(obj.clone())[0]
+        for st in range(bary_steps):
+            gsum, count, csum = ops["grad"](ctx, hist, mass, params, z, k, assign, g_warm, st > 0)
+            if ws > 1:
+                buf = allreduce(torch.cat([gsum.reshape(-1), count, csum]))
+                gsum, count = buf[:k * d * d].reshape(k, d * d), buf[k * d * d:k * d * d + k]
+            ops["apply"](ctx, z, gsum, count, params.gamma, lam)
+    return assign, z, objective

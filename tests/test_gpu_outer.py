@@ -165,3 +165,59 @@ def test_sharded_step_k_measures_with_owner(ctx):
     with pytest.raises(api.PdError):
         api.pd_barycenter_grad(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)),
                                api.pd_sinkhorn_default_params(gamma, d, bary_sharpen=1), z, 2, owner)
+
+
+def test_kmeans_assign_matches_pd_kmeans_costs(ctx):
+    """pd_kmeans_assign against the seeded centroids: argmin of the costs it
+    returns (lowest index on ties), objective = sum of the minima, and the
+    costs equal those of pd_sinkhorn_batch-style solves of the same pairs
+    through pd_kmeans' first assignment (same objective)."""
+    d, gamma = 16, 5e-3
+    b, t, o, _ = inputs.mode_diagrams(12, 3, 40, 60, sigma=0.02, seed=5)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hist, mass = hists_to_gpu(h), dev(masses(h).view(np.int32))
+    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=300, tol=0.0)
+    _, c0, _ = api.pd_kmeans(ctx, hist, mass, 3, p, 5.0, 0, 2, seed=2)        # seeding only
+    a, obj, cost = api.pd_kmeans_assign(ctx, hist, mass, p, c0, want_cost=True)
+    _, _, obj_k = api.pd_kmeans(ctx, hist, mass, 3, p, 5.0, 1, 0, seed=2)     # one round, no update
+    torch.cuda.synchronize()
+    cost = cost.cpu().numpy()
+    assert np.array_equal(a.cpu().numpy(), np.argmin(cost, axis=1))
+    assert np.isclose(obj.item(), cost.min(axis=1).sum(), rtol=1e-14)
+    assert obj.item() == obj_k.item()
+
+
+@pytest.mark.parametrize("shards", [1, 2])
+def test_kmeans_sharded_matches_pd_kmeans(ctx, shards):
+    """kmeans_sharded from pd_kmeans' seeding: one shard gives bitwise the
+    assignments, centroids and objectives of pd_kmeans; two shards emulated on
+    one GPU (assign and grad per shard, sums added, one apply) the same
+    assignments and centroids to the rounding of the added partial sums."""
+    from paper_1805_08331_gb300 import sharded
+    d, gamma, k, lam, rounds, steps = 16, 5e-3, 3, 5.0, 3, 2
+    b, t, o, _ = inputs.mode_diagrams(12, 3, 40, 60, sigma=0.02, seed=5)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hist, mass = hists_to_gpu(h), dev(masses(h).view(np.int32))
+    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=2000, tol=1e-6)
+    _, c0, _ = api.pd_kmeans(ctx, hist, mass, k, p, lam, 0, steps, seed=3)
+    a_ref, c_ref, obj_ref = api.pd_kmeans(ctx, hist, mass, k, p, lam, rounds, steps, seed=3)
+    if shards == 1:
+        a, c, obj = sharded.kmeans_sharded(ctx, hist, mass, p, c0, lam, rounds, steps)
+        torch.cuda.synchronize()
+        assert torch.equal(a, a_ref) and torch.equal(c, c_ref) and torch.equal(obj, obj_ref)
+        return
+    parts = [(hists_to_gpu(x), dev(masses(x).view(np.int32))) for x in (h[:5], h[5:])]
+    gw = [torch.empty((hh.shape[0], d * d + 1), dtype=torch.float64, device="cuda") for hh, _ in parts]
+    z = c0.clone()
+    objs = []
+    for rd in range(rounds):
+        asg = [api.pd_kmeans_assign(ctx, hh, mm, p, z) for hh, mm in parts]
+        objs.append(sum(x[1].item() for x in asg))
+        for st in range(steps):
+            g = [api.pd_barycenter_grad(ctx, hh, mm, p, z, k, x[0], gg, st > 0)
+                 for (hh, mm), x, gg in zip(parts, asg, gw)]
+            api.pd_barycenter_apply(ctx, z, g[0][0] + g[1][0], g[0][1] + g[1][1], gamma, lam)
+    torch.cuda.synchronize()
+    assert torch.equal(torch.cat([asg[0][0], asg[1][0]]), a_ref)
+    assert torch.allclose(z, c_ref, rtol=1e-9, atol=1e-12 * c_ref.max().item())
+    assert np.allclose(objs, obj_ref.cpu().numpy(), rtol=1e-12, atol=0)
