@@ -63,7 +63,7 @@ struct L2Side {
     uint32_t row;     // short  [n]
     uint32_t col;     // short  [n]
     uint32_t chl;     // short  [n] support entries grouped by output chunk, row-major inside a chunk
-    uint32_t rows;    // short  [nr] non-empty rows
+    uint32_t rows;    // short  [nr] non-empty rows, longest first
     uint32_t cols;    // short  [nc] non-empty columns
     uint32_t colpos;  // short  [d] position of a column in cols, -1 if empty
     short chs[L2_MAXCH + 1];   // chunk starts in chl
@@ -180,6 +180,26 @@ static __device__ void l2_chunks(L2Side& s, int* warp_cnt, unsigned char* gb) {
         }
     }
     if (nch == 0 && threadIdx.x == 0) s.chs[0] = 0;
+    __syncthreads();
+}
+
+// Reorder the non-empty rows longest first (ties by row index).  In full
+// chunks the two half-warps of a warp run stage 1 on two consecutive rows, so
+// rows of equal length side by side keep the half-warps in step; stage 2 sums
+// over all rows whatever their order.  Needs blockDim.x >= nr.
+static __device__ __forceinline__ void l2_sort_rows(short* rows, int nr, const int* rp) {
+    const int e = threadIdx.x;
+    int k = 0, rank = 0;
+    if (e < nr) {
+        k = rows[e];
+        const int len = rp[k + 1] - rp[k];
+        for (int f = 0; f < nr; ++f) {
+            const int kf = rows[f], lf = rp[kf + 1] - rp[kf];
+            rank += (lf > len) || (lf == len && f < e);
+        }
+    }
+    __syncthreads();
+    if (e < nr) rows[rank] = (short)k;
     __syncthreads();
 }
 
@@ -302,7 +322,37 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
         const int c0 = ch * L2_CW;
         const int wc = min(L2_CW, out_nc - c0);
         // ---- stage 1 for the chunk's columns: element (r, cc), r over non-empty input rows
-        {
+        if (wc == L2_CW) {
+            // full chunk: lane handles columns cc and cc + 16 of one row, the two
+            // half-warps two consecutive rows, so each input cell's (h, column)
+            // is loaded once for two output columns
+            const int cc = lane & 15;
+            const float2* cta = ct + (out_cols[c0 + cc] + d - 1);
+            const float2* ctb = ct + (out_cols[c0 + cc + 16] + d - 1);
+            for (int r = 2 * wid + (lane >> 4); r < in_nr; r += 2 * (NT / 32)) {
+                const int k = in_rows[r];
+                const int q0 = in_rp[k], q1 = in_rp[k + 1];
+                float2 h = in_hin[q0];
+                int col = in_col[q0];
+                float2 ca = cta[-col], cb = ctb[-col];
+                float ma = h.x - ca.x, mb = h.x - cb.x;
+                float Sa = l2_ex2(h.y - ca.y), Sb = l2_ex2(h.y - cb.y);
+                for (int qq = q0 + 1; qq < q1; ++qq) {
+                    h = in_hin[qq];
+                    col = in_col[qq];
+                    ca = cta[-col];
+                    cb = ctb[-col];
+                    const float aa = h.x - ca.x, ab = h.x - cb.x;
+                    const float mna = fmaxf(ma, aa), mnb = fmaxf(mb, ab);
+                    Sa = fmaf(Sa, l2_ex2(ma - mna), l2_ex2((aa - mna) + (h.y - ca.y)));
+                    Sb = fmaf(Sb, l2_ex2(mb - mnb), l2_ex2((ab - mnb) + (h.y - cb.y)));
+                    ma = mna;
+                    mb = mnb;
+                }
+                L1[l2_lidx<NT>(r, cc)] = make_float2(ma, Sa);
+                L1[l2_lidx<NT>(r, cc + 16)] = make_float2(mb, Sb);
+            }
+        } else {
             int r = t / wc, cc = t - r * wc;
             const int dr = NT / wc, dc = NT - dr * wc;
             while (r < in_nr) {
@@ -499,6 +549,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
         const float* wt[2] = {q.am, q.bm};
         const int* rps[2] = {q.rpa, q.rpb};
         const int* cps[2] = {q.cpa, q.cpb};
+#pragma unroll
         for (int s = 0; s < 2; ++s) {
             L2Side& X = S[s];
             const int n = X.n;
@@ -522,6 +573,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
             for (int i = t; i <= d; i += NT) xrp[i] = rps[s][i];
             l2_compact(rps[s], d, sdp<short, GM>(gb, X.rows), &cnt[2], nullptr, wcnt);
             l2_compact(cps[s], d, sdp<short, GM>(gb, X.cols), &cnt[3], sdp<short, GM>(gb, X.colpos), wcnt);
+            l2_sort_rows(sdp<short, GM>(gb, X.rows), cnt[2], xrp);
             if (t == 0) {
                 X.nr = cnt[2]; X.nc = cnt[3]; X.nch = (cnt[3] + L2_CW - 1) / L2_CW;
                 const double wD = q.sc[s == 0 ? SC_AD : SC_BD];
