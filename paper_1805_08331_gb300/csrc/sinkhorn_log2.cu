@@ -613,8 +613,11 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     for (int it = 0; it < n_inner; ++it) {
         long long errq = 0;
         bool errbad = false;
-        l2_half<NT, GM>(S[1], S[0], K, false, errq, errbad, redD, &range_flag, gb);   // u-update: phi from psi
-        l2_half<NT, GM>(S[0], S[1], K, true, errq, errbad, redD, &range_flag, gb);    // v-update: psi from phi, err_t
+        // u-update (phi from psi), then v-update (psi from phi, err_t): one copy
+        // of the half-step code serves both (instruction cache)
+#pragma unroll 1
+        for (int hs = 0; hs < 2; ++hs)
+            l2_half<NT, GM>(S[1 - hs], S[hs], K, hs == 1, errq, errbad, redD, &range_flag, gb);
         errq = warp_sum(errq);
         if (lane == 0) redE[wid] = errq;
         // written next to redE and read after the same barrier (the next write
