@@ -214,7 +214,8 @@ pd_status pd_barycenter(pd_ctx* ctx, const uint32_t* hist, const uint32_t* mass,
  *   cost_sum[c]= the sum of their transport costs <P_n, C>.
  *   hist, mass : uint32 [N][d][d], uint32 [N] (device): this shard's diagrams
  *   k, z       : number of measures; double [k][d*d] (device, read only)
- *   owner      : int32 [N] (device) or NULL (every n belongs to measure 0)
+ *   owner      : int32 [N] (device) or NULL (every n belongs to measure 0);
+ *                a value outside [0, k) gives PD_ERR_INVALID (checked on the device first)
  *   g_warm     : double [N][d*d+1] (device) or NULL: the pairs' potentials g,
  *                written on return; read as the warm start when warm != 0
  *   gsum       : double [k][d*d]; count, cost_sum: double [k] (device, output)

@@ -657,6 +657,14 @@ extern "C" pd_status pd_barycenter_grad(pd_ctx* c, const uint32_t* hist, const u
                                        "cost_sum, and g_warm when warm");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(c, cudaSetDevice(c->device));
+    if (owner) {
+        // an owner outside [0, k) would index past z: refuse it before any solve
+        CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), s));
+        CUDA_TRY(c, outer_check_owner(owner, N, k, c->dflag, s));
+        CUDA_TRY(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (c->hflag[0]) return fail(c, PD_ERR_INVALID, "pd_barycenter_grad: owner values must lie in [0, k)");
+    }
     const int d = prm->d, n1 = d * d + 1;
     Arena a{nullptr, 0};
     auto layout = [&](Arena& ar, double** f, double** g, double** cost, int32_t** pairs, int32_t** iters, float** err,

@@ -178,6 +178,12 @@ __global__ void km_pairs_kernel(int N, int k, int32_t* __restrict__ pairs) {
     }
 }
 
+// flag = 1 if some owner[n] is outside [0, k)
+__global__ void check_owner_kernel(const int32_t* __restrict__ owner, int N, int k, int* __restrict__ flag) {
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
+        if (owner[n] < 0 || owner[n] >= k) atomicOr(flag, 1);
+}
+
 // pairs for the centroid batch: p = n -> (owner[n], n)   (owner NULL: (0, n))
 __global__ void owner_pairs_kernel(const int32_t* __restrict__ owner, int N, int32_t* __restrict__ pairs) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
@@ -234,6 +240,12 @@ cudaError_t outer_km_seed(const uint32_t* hist, const int32_t* idx, int k, int d
 }
 cudaError_t outer_km_pairs(int N, int k, int32_t* pairs, cudaStream_t s) {
     km_pairs_kernel<<<152, 256, 0, s>>>(N, k, pairs);
+    return cudaGetLastError();
+}
+cudaError_t outer_check_owner(const int32_t* owner, int N, int k, int* flag, cudaStream_t s) {
+    int blocks = (N + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    check_owner_kernel<<<blocks, 256, 0, s>>>(owner, N, k, flag);
     return cudaGetLastError();
 }
 cudaError_t outer_owner_pairs(const int32_t* owner, int N, int32_t* pairs, cudaStream_t s) {

@@ -148,6 +148,7 @@ cudaError_t outer_km_assign(const double* cost, int N, int k, int32_t* assign, d
 cudaError_t outer_km_seed(const uint32_t* hist, const int32_t* idx, int k, int d, double* z, cudaStream_t s);
 cudaError_t outer_km_pairs(int N, int k, int32_t* pairs, cudaStream_t s);
 cudaError_t outer_owner_pairs(const int32_t* owner, int N, int32_t* pairs, cudaStream_t s);
+cudaError_t outer_check_owner(const int32_t* owner, int N, int k, int* flag, cudaStream_t s);
 // entropic sharpening: H0 = largest input entropy (stored as the bits of a non-negative double)
 cudaError_t outer_input_entropy(const uint32_t* hist, int N, int d, unsigned long long* H0bits, cudaStream_t s);
 cudaError_t outer_sharpen(double* z, int k, int d, const unsigned long long* H0bits, cudaStream_t s);

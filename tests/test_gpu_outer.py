@@ -165,6 +165,12 @@ def test_sharded_step_k_measures_with_owner(ctx):
     with pytest.raises(api.PdError):
         api.pd_barycenter_grad(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)),
                                api.pd_sinkhorn_default_params(gamma, d, bary_sharpen=1), z, 2, owner)
+    for bad in (2, -1):                                    # owner outside [0, k): refused, nothing solved
+        ob = owner.clone()
+        ob[3] = bad
+        with pytest.raises(api.PdError) as e:
+            api.pd_barycenter_grad(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), p, z, 2, ob)
+        assert e.value.status == api.PD_ERR_INVALID
 
 
 def test_kmeans_assign_matches_pd_kmeans_costs(ctx):
