@@ -128,7 +128,9 @@ void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, int d);
  * Potentials use P_xy = a_x b_y exp((f_x + g_y - C_xy)/gamma).
  *   histA, massA : uint32 [NA][d][d], uint32 [NA]   (device)
  *   histB, massB : uint32 [NB][d][d], uint32 [NB]   (device)
- *   pairs        : int32 [P][2] (ia, ib) indices, or NULL meaning pair p = (p, p) (device)
+ *   pairs        : int32 [P][2] (ia, ib) indices, or NULL meaning pair p = (p, p) (device);
+ *                  the arrays' lengths are not passed, so the caller keeps ia and ib
+ *                  within histA / histB (not checked)
  *   P            : number of pairs (>= 0)
  *   params       : host pointer
  *   g_init       : double [P][d*d+1] initial g (warm start), or NULL for g = 0 (device)
