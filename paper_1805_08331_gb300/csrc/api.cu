@@ -309,6 +309,11 @@ static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hb
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // on-chip CTAs per SM that the largest pair's shared memory allows (dynamic
+    // part + the kernel's static part + the runtime's 1 KB per CTA)
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int fit_per_sm = smem > 0 ? (int)((size_t)smem_sm / (smem + 2048)) : 3;
     int fixed_threads = 0;
     if (const char* ev = std::getenv("PD_LSE2_THREADS")) {
         const int v = std::atoi(ev);
@@ -327,7 +332,13 @@ static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hb
         if ((e = cudaMemsetAsync(counter, 0, 8 * sizeof(int), s)) != cudaSuccess) return e;
         {
             ProfScope ps(c, PD_K_ITER, s);
-            const int threads = fixed_threads ? fixed_threads : (active > 2 * nsm ? 256 : (active > nsm ? 512 : 1024));
+            // 256 threads while several pairs share an SM; wider CTAs once fewer
+            // pairs than 2 (1) per SM remain, or when the largest pair's shared
+            // memory lets only 2 (1) CTAs onto an SM (e.g. a dense barycenter
+            // side), so that the SM still runs 16-32 warps
+            const int by_active = active > 2 * nsm ? 256 : (active > nsm ? 512 : 1024);
+            const int by_smem = fit_per_sm <= 1 ? 1024 : (fit_per_sm == 2 ? 512 : 256);
+            const int threads = fixed_threads ? fixed_threads : (by_active > by_smem ? by_active : by_smem);
             // Widening: a pair alone on an SM iterates ~2x faster in a
             // 512/1024-thread CTA than in a 256-thread CTA sharing the SM, so
             // once no more than 2 (1) pairs per SM are left the launch hands
