@@ -369,7 +369,14 @@ cudaError_t serve_round(pd_server* sv, int pi, std::vector<Req*>& pending) {
     const int inner = sv->cfg.inner_iters > 0 ? sv->cfg.inner_iters : 32;
     const size_t smem = (size_t)((int*)P.h_cnt.p)[2];
     const int na = (int)P.active.size();
-    const int threads = na > 2 * nsm ? 256 : (na > nsm ? 512 : 1024);
+    // wider CTAs when few pairs are active, or when the largest pair's shared
+    // memory lets only 2 (1) CTAs onto an SM (dynamic + static + 1 KB per CTA)
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, sv->device);
+    const int fit_per_sm = smem > 0 ? (int)((size_t)smem_sm / (smem + 2048)) : 3;
+    const int by_active = na > 2 * nsm ? 256 : (na > nsm ? 512 : 1024);
+    const int by_smem = fit_per_sm <= 1 ? 1024 : (fit_per_sm == 2 ? 512 : 256);
+    const int threads = by_active > by_smem ? by_active : by_smem;
     SV_TRY(cudaMemsetAsync(P.counter, 0, sizeof(int) * 4, P.stream));
     SV_TRY(P.gbits >= 0 ? sk_launch_lse2(P.w, sv->run, inner, P.counter, smem, P.gbits, threads, P.stream)
                         : sk_launch_lse_smem(P.w, sv->run, inner, P.counter, P.counter + 1, P.stream));
