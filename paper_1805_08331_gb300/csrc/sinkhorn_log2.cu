@@ -59,7 +59,8 @@ struct L2Side {
     uint32_t pot;     // float2 [n] potential/gamma in log2 units (hi, lo)
     uint32_t hin;     // float2 [n] lw + pot, the side's h when it is the input
     uint32_t w;       // float  [n] weight (marginal error)
-    uint32_t rp;      // int    [d+1] row pointers into the support (row-major)
+    uint32_t rp;      // int    [d+1] row pointers into the support while loading; then, per
+                      //        non-empty row r: first cell | one-past-last cell << 16
     uint32_t row;     // short  [n]
     uint32_t col;     // short  [n]
     uint32_t chl;     // short  [n] support entries grouped by output chunk, row-major inside a chunk
@@ -266,7 +267,7 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
     const short* in_row = sdp<short, GM>(gb, in.row);
     const short* in_col = sdp<short, GM>(gb, in.col);
     const short* in_rows = sdp<short, GM>(gb, in.rows);
-    const int* in_rp = sdp<int, GM>(gb, in.rp);
+    const int* in_rq = sdp<int, GM>(gb, in.rp);
     const float2* ct = smp<float2>(K.ct);
     const float2* cdt = smp<float2>(K.cdt);
     float2* L1 = smp<float2>(K.L1);
@@ -330,8 +331,8 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
             const float2* cta = ct + (out_cols[c0 + cc] + d - 1);
             const float2* ctb = ct + (out_cols[c0 + cc + 16] + d - 1);
             for (int r = 2 * wid + (lane >> 4); r < in_nr; r += 2 * (NT / 32)) {
-                const int k = in_rows[r];
-                const int q0 = in_rp[k], q1 = in_rp[k + 1];
+                const int rq = in_rq[r];
+                const int q0 = rq & 0xffff, q1 = rq >> 16;
                 float2 h = in_hin[q0];
                 int col = in_col[q0];
                 float2 ca = cta[-col], cb = ctb[-col];
@@ -356,9 +357,9 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
             int r = t / wc, cc = t - r * wc;
             const int dr = NT / wc, dc = NT - dr * wc;
             while (r < in_nr) {
-                const int k = in_rows[r];
                 const int j = out_cols[c0 + cc];
-                const int q0 = in_rp[k], q1 = in_rp[k + 1];
+                const int rq = in_rq[r];
+                const int q0 = rq & 0xffff, q1 = rq >> 16;
                 const float2* ctj = ct + (j + d - 1);
                 // online log-sum-exp over the row's cells: (m, S) with value m + log2 S
                 float2 h = in_hin[q0];
@@ -502,6 +503,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
             fits = l2_side_bytes(nA, nB, d) <= gcap && l2_table_bytes(nrA > nrB ? nrA : nrB, d) <= (size_t)smem_cap;
         else
             fits = l2_need(nA, nB, nrA, nrB, d) <= (size_t)smem_cap;
+        fits = fits && nA < 32768 && nB < 32768;   // cell indices are 16-bit (chl, packed row ranges)
     }
     __syncthreads();
     if (!fits) {
@@ -574,6 +576,16 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
             l2_compact(rps[s], d, sdp<short, GM>(gb, X.rows), &cnt[2], nullptr, wcnt);
             l2_compact(cps[s], d, sdp<short, GM>(gb, X.cols), &cnt[3], sdp<short, GM>(gb, X.colpos), wcnt);
             l2_sort_rows(sdp<short, GM>(gb, X.rows), cnt[2], xrp);
+            {
+                // row pointers -> one word per non-empty row (stage 1 loads one value)
+                const short* xrows = sdp<short, GM>(gb, X.rows);
+                const int nr = cnt[2];
+                int v = 0;
+                if (t < nr) { const int k = xrows[t]; v = xrp[k] | (xrp[k + 1] << 16); }
+                __syncthreads();
+                if (t < nr) xrp[t] = v;
+                __syncthreads();
+            }
             if (t == 0) {
                 X.nr = cnt[2]; X.nc = cnt[3]; X.nch = (cnt[3] + L2_CW - 1) / L2_CW;
                 const double wD = q.sc[s == 0 ? SC_AD : SC_BD];
