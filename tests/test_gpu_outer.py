@@ -94,6 +94,19 @@ def test_outer_loops_reject_bad_arguments(ctx):
     ps = api.pd_sinkhorn_default_params(1e-2, 8, bary_sharpen=1)
     with pytest.raises(api.PdError):
         api.pd_kmeans(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), 1, ps, 1.0, 1, 1)
+    # the split step and the assignment: bad sizes and parameters are refused
+    z = torch.zeros((1, 8, 8), dtype=torch.float64, device="cuda")
+    gs = torch.zeros((1, 64), dtype=torch.float64, device="cuda")
+    cnt = torch.ones(1, dtype=torch.float64, device="cuda")
+    for gamma, lam in ((0.0, 1.0), (1e-2, 0.0), (1e-2, -1.0)):
+        with pytest.raises(api.PdError) as e:
+            api.pd_barycenter_apply(ctx, z, gs, cnt, gamma, lam)
+        assert e.value.status == api.PD_ERR_INVALID
+    with pytest.raises(api.PdError):
+        api.pd_barycenter_grad(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), p, z, 0)     # k = 0
+    a, obj, _ = api.pd_kmeans_assign(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), p, z[:1] + 1.0)
+    torch.cuda.synchronize()
+    assert a.cpu().tolist() == [0, 0] and np.isfinite(obj.item())
 
 
 def test_sharded_step_one_shard_is_pd_barycenter_bitwise(ctx):
