@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--serve-gamma", type=float, default=5e-3)
     ap.add_argument("--serve-tol", type=float, default=1e-4)
     ap.add_argument("--serve-nmax", type=int, default=5000, help="largest diagram of the stream (points)")
+    ap.add_argument("--serve-inner", type=int, default=64, help="iterations per serving scheduling round")
     return ap.parse_args()
 
 
@@ -445,7 +446,7 @@ def serve_leg(args, ctx):
         b, t, o = q
         return b[o[i]:o[i + 1]], t[o[i]:o[i + 1]]
 
-    cfg = api.serve_default_config(gamma=args.serve_gamma, tol=args.serve_tol, max_iter=5000, inner_iters=32,
+    cfg = api.serve_default_config(gamma=args.serve_gamma, tol=args.serve_tol, max_iter=5000, inner_iters=args.serve_inner,
                                    max_hbm_bytes=48 << 30, warm_start=1)
     sv = api.Server(ctx, cfg)
     for d in grids:

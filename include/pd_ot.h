@@ -297,7 +297,7 @@ typedef struct {
     double gamma;          /* entropic regularisation of every solve (> 0) */
     double tol;            /* relative marginal tolerance of every solve (>= 0) */
     int max_iter;          /* iterations per solve at most (>= 1) */
-    int inner_iters;       /* iterations per scheduling round (<= 0: 32) */
+    int inner_iters;       /* iterations per scheduling round (<= 0: 64) */
     int slots[4];          /* pair slots for d = 32, 64, 128, 256; 0: from max_hbm_bytes;
                               < 0: no pool for that d (its queries are refused) */
     size_t max_hbm_bytes;  /* device memory shared equally by the pools whose slots[] is 0
@@ -327,7 +327,7 @@ typedef struct {
     double latency_ms;   /* submit to completion, host steady clock */
 } pd_result;
 
-/* Default configuration: gamma 5e-3, tol 1e-4, max_iter 5000, inner_iters 32,
+/* Default configuration: gamma 5e-3, tol 1e-4, max_iter 5000, inner_iters 64,
  * slots from half the free memory, queue_capacity 65536, warm_start 1. */
 void pd_serve_default_config(pd_serve_config* cfg);
 /* Create a server on ctx's device (ctx must outlive the server; the server

@@ -366,7 +366,7 @@ cudaError_t serve_round(pd_server* sv, int pi, std::vector<Req*>& pending) {
     // ---- 3. one round of iterations, then the slots' status
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, sv->device);
-    const int inner = sv->cfg.inner_iters > 0 ? sv->cfg.inner_iters : 32;
+    const int inner = sv->cfg.inner_iters > 0 ? sv->cfg.inner_iters : 64;
     const size_t smem = (size_t)((int*)P.h_cnt.p)[2];
     const int na = (int)P.active.size();
     // wider CTAs when few pairs are active, or when the largest pair's shared
@@ -535,7 +535,7 @@ extern "C" void pd_serve_default_config(pd_serve_config* cfg) {
     cfg->gamma = 5e-3;
     cfg->tol = 1e-4;
     cfg->max_iter = 5000;
-    cfg->inner_iters = 32;
+    cfg->inner_iters = 64;
     cfg->max_hbm_bytes = 0;
     cfg->queue_capacity = 65536;
     cfg->warm_start = 1;
@@ -552,7 +552,7 @@ extern "C" pd_status pd_serve_create(pd_ctx* ctx, const pd_serve_config* cfg, pd
     sv->device = dev;
     sv->cfg = *cfg;
     if (sv->cfg.queue_capacity <= 0) sv->cfg.queue_capacity = 65536;
-    if (sv->cfg.inner_iters <= 0) sv->cfg.inner_iters = 32;
+    if (sv->cfg.inner_iters <= 0) sv->cfg.inner_iters = 64;
     sv->run.max_iter = cfg->max_iter;
     sv->run.tol = cfg->tol;
     sv->run.tau = 20.0;
