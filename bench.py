@@ -143,12 +143,17 @@ def peaks():
 
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
-NUM_SMS = 152
+
+
+def num_sms():
+    """SM count of the current device (152 on a GB300)."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
 def fp32_peak_tflops(sm_mhz):
-    """CUDA-core FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x clock."""
-    return NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    """CUDA-core FP32 FMA peak: SMs x 128 lanes x 2 flop x clock."""
+    return num_sms() * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 # DRAM bytes (read + write) of the base-2 iteration kernel per pair and
@@ -160,8 +165,8 @@ LSE2_DRAM_BYTES_PER_PAIR_LAUNCH = (54.430976e6 + 0.329472e6) / 512
 
 
 def mufu_peak_gexp(sm_mhz):
-    """Special-function-unit ex2 peak: 152 SMs x 16 ex2/clk x clock, in 1e9/s."""
-    return NUM_SMS * MUFU_PER_SM * sm_mhz * 1e6 / 1e9
+    """Special-function-unit ex2 peak: SMs x 16 ex2/clk x clock, in 1e9/s."""
+    return num_sms() * MUFU_PER_SM * sm_mhz * 1e6 / 1e9
 
 
 def lse_terms_per_iteration(hist, pairs, d):
@@ -229,6 +234,32 @@ def cpu_baseline(args, b, t, o, n_pairs):
     return {"value": cells / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"first {n_pairs} pairs of the workload solved to tol by the FP64 oracle "
                       f"(OpenMP over pairs), {dt:.1f} s"}, r
+
+
+def parity_sample(args, b, t, o, outs, status):
+    """Costs of a sample of the timed step's pairs against the FP64 oracle run
+    with the same max_iter and tol: the first few pairs, the first two pairs
+    that stopped at max_iter (if any) and the largest pair (most points)."""
+    import oracle
+    P = args.pairs
+    npts = np.diff(o)
+    size = npts[0::2] + npts[1::2]
+    sel = list(range(min(args.parity_sample, P)))
+    sel += [int(p) for p in np.nonzero(status == 6)[0][:2] if int(p) not in sel]
+    big = int(np.argmax(size))
+    if big not in sel:
+        sel.append(big)
+    hist, _ = oracle.rasterize(b, t, o, args.d)
+    hA = np.stack([hist[2 * p] for p in sel])
+    hB = np.stack([hist[2 * p + 1] for p in sel])
+    t0 = time.perf_counter()
+    ref = oracle.sinkhorn_pd_batch(args.d, args.gamma, hA, hB, args.max_iter, args.tol)
+    dt = time.perf_counter() - t0
+    c_gpu = outs["cost"].cpu().numpy()[sel]
+    rel = np.abs(c_gpu - ref["cost"]) / ref["cost"]
+    return {"pairs_checked": len(sel), "pairs": sel, "status": [int(status[p]) for p in sel],
+            "points": [int(size[p]) for p in sel], "rel_cost_err_vs_fp64": [float(x) for x in rel],
+            "max_rel_cost_err_vs_fp64": float(rel.max()), "oracle_s": dt}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -303,6 +334,7 @@ def run_ours(args):
     ctx.profile_enable(True)
     ev = []
     cells = 0.0
+    cells_all = 0.0
     iters_in_iter_kernel = 0
     pair_launches = 0.0
     lse_terms = 0.0
@@ -317,7 +349,11 @@ def run_ours(args):
         e1.record(stream)
         ev.append((e0, e1))
         it = outs["iters"].cpu().numpy()
-        cells += float(it.sum()) * 2 * (d * d + 1)
+        ok = outs["status"].cpu().numpy() == api.PD_OK
+        # only results within the stated error count: pairs that stopped at
+        # max_iter above tol are reported beside the value, not in it
+        cells += float(it[ok].sum()) * 2 * (d * d + 1)
+        cells_all += float(it.sum()) * 2 * (d * d + 1)
         iters_in_iter_kernel += int(np.maximum(it - 1, 0).sum())
         lse_terms += float((it * terms).sum())
     torch.cuda.synchronize()
@@ -331,6 +367,7 @@ def run_ours(args):
     tot_ms = max_over_ranks(my_ms, ws)
     all_cells = sum_over_ranks(cells, ws)
     value = all_cells / (tot_ms / 1e3)
+    value_all_pairs = sum_over_ranks(cells_all, ws) / (tot_ms / 1e3)
     status = outs["status"].cpu().numpy()
     errs = outs["err"].cpu().numpy()
 
@@ -350,7 +387,8 @@ def run_ours(args):
         cost_host.copy_(out["cost"], non_blocking=True)
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
-        e2e_cells += float(out["iters"].sum().item()) * 2 * (d * d + 1)
+        ok = out["status"] == api.PD_OK
+        e2e_cells += float(out["iters"][ok].sum().item()) * 2 * (d * d + 1)
     e2e_s = max_over_ranks(e2e_s, ws)
     e2e_val = sum_over_ranks(e2e_cells, ws) / e2e_s
 
@@ -367,24 +405,33 @@ def run_ours(args):
         peak = fp32_peak_tflops(pk.get("sm_max_mhz", 2070.0))
         bound, unit, kname = "alu", "TFLOP/s", "sk_iter_fp32_kernel (CUDA-core FP32 separable GEMMs)"
         achieved = flops / (iter_ms / 1e3) / 1e12 if iter_ms > 0 else 0.0
-        src = f"{pk_kind} sm_max_mhz x 152 SMs x 128 FP32 lanes x 2"
+        src = f"{pk_kind} sm_max_mhz x {num_sms()} SMs x 128 FP32 lanes x 2"
     else:
         peak = mufu_peak_gexp(pk.get("sm_max_mhz", 2070.0))
         bound, unit, kname = "alu", "Gexp/s", "sk_lse2_kernel (on-chip base-2 log-domain separable Sinkhorn)"
         achieved = lse_terms / (iter_ms / 1e3) / 1e9 if iter_ms > 0 else 0.0
-        src = f"{pk_kind} sm_max_mhz x 152 SMs x 16 MUFU ex2/clk (one exponential per log-sum-exp term)"
+        src = f"{pk_kind} sm_max_mhz x {num_sms()} SMs x 16 MUFU ex2/clk (one exponential per log-sum-exp term)"
     traffic = None
     if precision == api.PD_FP32 and iter_launches:
         # pair loads: the first launch of a step loads every pair; the
         # drain-time hand-overs reload at most 2 x 152 pairs (512-thread CTAs)
         # and then at most 152 (1024-thread CTAs)
         per_step = iter_launches / max(args.steps, 1)
-        pair_launches = args.steps * (P + (2 * NUM_SMS if per_step >= 2 else 0) + (NUM_SMS if per_step >= 3 else 0))
+        nsm = num_sms()
+        pair_launches = args.steps * (P + (2 * nsm if per_step >= 2 else 0) + (nsm if per_step >= 3 else 0))
         traffic = LSE2_DRAM_BYTES_PER_PAIR_LAUNCH * pair_launches / iter_launches
+    # the metric's own tensor-unit roofline: one cell update of the dense
+    # separable form = two d x d x d GEMMs per half-step over 2 (d^2 + 1) cells,
+    # 4d flop per cell, against the sustained BF16 tensor peak
+    tpk = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    tensor_unit = {"flop_per_cell": 4 * d, "peak_tflops": tpk,
+                   "peak_source": f"{pk_kind} bf16_tflops_sustained",
+                   "achieved_tflops": value / ws * 4 * d / 1e12,
+                   "frac": value / ws * 4 * d / (tpk * 1e12)}
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak if peak else None, "traffic": traffic, "kernel": kname, "peak_source": src,
             "launches": iter_launches, "kernel_ms": iter_ms,
-            "share_of_step": iter_ms / my_ms if my_ms else None}
+            "share_of_step": iter_ms / my_ms if my_ms else None, "tensor_unit": tensor_unit}
     launches = int(sum(n for _, n in prof.values()))
 
     # ---- parity sample and CPU baseline (rank 0 only)
@@ -392,11 +439,8 @@ def run_ours(args):
     parity = None
     if rank == 0 and not args.no_cpu_baseline:
         n = max(1, min(args.cpu_sample, P))
-        cpu, ref = cpu_baseline(args, b, t, o, n)
-        k = min(args.parity_sample, n)
-        c_gpu = outs["cost"].cpu().numpy()[:k]
-        rel = np.abs(c_gpu - ref["cost"][:k]) / ref["cost"][:k]
-        parity = {"pairs_checked": int(k), "max_rel_cost_err_vs_fp64": float(rel.max())}
+        cpu, _ = cpu_baseline(args, b, t, o, n)
+        parity = parity_sample(args, b, t, o, outs, status)
     serving = None
     if rank == 0 and not args.no_serve:
         serving = serve_leg(args, ctx)
@@ -409,7 +453,12 @@ def run_ours(args):
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clk, "parity": parity,
                 "status_counts": {str(int(s)): int((status == s).sum()) for s in np.unique(status)},
-                "max_err": float(errs.max()), "serving": serving}
+                "value_counts": "pairs with status PD_OK (relative marginal error <= tol) only",
+                "excluded": {"pairs": int((status != api.PD_OK).sum()),
+                             "iterations_per_step": int(outs["iters"].cpu().numpy()[status != api.PD_OK].sum()),
+                             "value_with_them": value_all_pairs},
+                "max_err": float(errs.max()), "max_err_counted": float(errs[status == api.PD_OK].max()) if
+                (status == api.PD_OK).any() else None, "serving": serving}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

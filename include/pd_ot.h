@@ -387,30 +387,34 @@ pd_status pd_profile_read(pd_ctx* ctx, double* ms_host, int64_t* launches_host);
 
 /*
  * pd_sinkhorn_batch_noalloc -- the PD_FP32 solve of pd_sinkhorn_batch without
- * any memory allocation.  (A library feature; the paper has no counterpart.)
+ * any device memory allocation.  (A library feature; the paper has no
+ * counterpart.)
  *
- * For callers that must not allocate device memory: code that runs while a
- * stream is being captured into a CUDA graph (cudaMalloc is not allowed
- * there), applications that hand all device memory to their own pool
- * allocator and forbid libraries from calling cudaMalloc / cudaFree (which also
- * synchronise the device), and latency-critical serving threads that cannot
- * afford an allocation's implicit synchronisation.  It takes no pd_ctx (a
- * context allocates) and calls no cudaMalloc, cudaFree or other allocating
- * routine.
+ * For callers that must not allocate device memory: applications that hand
+ * all device memory to their own pool allocator and forbid libraries from
+ * calling cudaMalloc / cudaFree (which also synchronise the whole device and
+ * can fail once the pool holds the memory), and latency-critical serving
+ * threads that cannot afford an allocation's implicit device-wide
+ * synchronisation.  It takes no pd_ctx (a context allocates) and calls no
+ * cudaMalloc, cudaFree or other device-allocating routine.
  *
  * Its workspace is a fixed 16 MiB array in device memory that every GPU that
  * loads this library holds until the process exits.  That bounds the batch: the
  * pairs must fit in 16 MiB of workspace, about 9 pairs at d = 100..128 and 35
  * pairs at d <= 64; a larger P returns PD_ERR_INVALID.  params->precision must
- * be PD_FP32.  Arguments, outputs and results are those of pd_sinkhorn_batch,
- * computed on the current CUDA device.
+ * be PD_FP32, params->p must be 2 and params->eps_stages must be 0 (the
+ * gamma-continuation is not run here; other values return PD_ERR_INVALID).
+ * Arguments, outputs and results are those of pd_sinkhorn_batch, computed on
+ * the current CUDA device.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the one array and it keeps the last call's contents (each
  * call initialises everything it reads), so calls whose GPU work overlaps --
  * on two streams, or from two host threads -- race and corrupt each other's
- * results; serialise them.  Synchronises `stream`.
+ * results; serialise them.  Like pd_sinkhorn_batch, the call reads per-pair
+ * counters back to the host between its launches and synchronises `stream`
+ * before it returns.
  * Errors: PD_ERR_INVALID (bad params, NULL input/cost, P too large for the
  * array), PD_ERR_CUDA.
  */

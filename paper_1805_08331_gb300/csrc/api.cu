@@ -7,6 +7,7 @@
 #include <vector>
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 
 #include "pd_internal.h"
 #include "../../include/pd_ot.h"
@@ -860,11 +861,13 @@ extern "C" pd_status pd_kmeans(pd_ctx* c, const uint32_t* hist, const uint32_t* 
 // cudaMalloc: every GPU that loads this library reserves it for the lifetime
 // of the process.  Host code cannot use the array's name as a device address
 // (in host code it names a host-side stand-in), so the device address is
-// obtained once per device with cudaGetSymbolAddress and cached.
+// obtained once per device with cudaGetSymbolAddress and cached; the cache
+// entries are atomics, so two host threads making their first call on one
+// device at the same time both store the same address without a data race.
 #define PD_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define PD_NOALLOC_MAX_DEVICES 64
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PD_NOALLOC_SCRATCH_BYTES];
-static void* g_noalloc_addr[PD_NOALLOC_MAX_DEVICES];
+static std::atomic<void*> g_noalloc_addr[PD_NOALLOC_MAX_DEVICES];
 
 extern "C" pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint32_t* massA,
                                                const uint32_t* histB, const uint32_t* massB,
@@ -874,8 +877,10 @@ extern "C" pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint
                                                float* err, int32_t* status, pd_stream stream) {
     if (!prm) return PD_ERR_INVALID;
     const int d = prm->d;
+    // gamma-continuation (eps_stages) is a pd_sinkhorn_batch feature this entry
+    // point does not run: refused rather than silently ignored
     if (d < 2 || d > 256 || !(prm->gamma > 0) || !std::isfinite(prm->gamma) || prm->max_iter < 1 ||
-        !(prm->tol >= 0) || prm->precision != PD_FP32 || prm->p != 2.0 || P < 0)
+        !(prm->tol >= 0) || prm->precision != PD_FP32 || prm->p != 2.0 || prm->eps_stages != 0 || P < 0)
         return PD_ERR_INVALID;
     if (P == 0) return PD_OK;
     if (!cost || !histA || !histB || !massA || !massB) return PD_ERR_INVALID;
@@ -883,37 +888,21 @@ extern "C" pd_status pd_sinkhorn_batch_noalloc(const uint32_t* histA, const uint
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= PD_NOALLOC_MAX_DEVICES) return PD_ERR_CUDA;
     // one-time set-up on this device: device address of the static scratch array
-    if (!g_noalloc_addr[dev]) {
-        void* a = nullptr;
-        if (cudaGetSymbolAddress(&a, g_noalloc_scratch) != cudaSuccess || !a) return PD_ERR_CUDA;
-        g_noalloc_addr[dev] = a;
+    void* base = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!base) {
+        if (cudaGetSymbolAddress(&base, g_noalloc_scratch) != cudaSuccess || !base) return PD_ERR_CUDA;
+        g_noalloc_addr[dev].store(base, std::memory_order_release);
     }
     const int dp = ((d + 63) / 64) * 64;
     int* counter = nullptr;
     if (pd_carve_ws(nullptr, P, d, dp, prm->gamma, nullptr, &counter) > PD_NOALLOC_SCRATCH_BYTES)
         return PD_ERR_INVALID;   // this many pairs at this d do not fit in the static scratch
     SkWS w;
-    pd_carve_ws((char*)g_noalloc_addr[dev], P, d, dp, prm->gamma, &w, &counter);
+    pd_carve_ws((char*)base, P, d, dp, prm->gamma, &w, &counter);
     w.histA = histA; w.histB = histB; w.massA = massA; w.massB = massB; w.pairs = pairs;
-    float tab[5 * 256];
-    for (int m = 0; m < dp; ++m) {
-        double z = (double)m / d;
-        double v = z * z / prm->gamma, v2 = 0.5 * z * z / prm->gamma;
-        float hi = (float)v, hi2 = (float)v2;
-        tab[m] = hi;
-        tab[dp + m] = (float)(v - (double)hi);
-        tab[2 * dp + m] = hi2;
-        tab[3 * dp + m] = (float)(v2 - (double)hi2);
-        tab[4 * dp + m] = m == 0 ? -INFINITY : (float)(2.0 * std::log(z));
-    }
-    if (cudaMemcpyAsync(w.ctab, tab, sizeof(float) * 5 * dp, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return PD_ERR_CUDA;
-    SkRun r{};
-    r.max_iter = prm->max_iter;
-    r.tol = prm->tol;
-    r.tau = 20.0;
-    r.absorb_every = 64;
-    r.rel_thresh = -21.0;
+    w.p = prm->p;
+    if (pd_upload_cost_tables(w, prm->gamma, s) != cudaSuccess) return PD_ERR_CUDA;
+    const SkRun r = make_run(prm);
     if (sk_launch_setup(w, g_init, s) != cudaSuccess) return PD_ERR_CUDA;
     int hcount[4] = {0, 0, 0, 0};
     if (lse_rounds(nullptr, w, r, counter, hcount, s) != cudaSuccess) return PD_ERR_CUDA;

@@ -1,6 +1,7 @@
 """The allocation-free solve, pd_sinkhorn_batch_noalloc, for callers that may
-not allocate device memory (stream capture, pool allocators, latency-critical
-threads).  Called through the C ABI with caller-owned buffers, it must give the
+not allocate device memory (applications whose pool allocator owns the device
+memory, latency-critical threads that cannot take an allocation's device-wide
+synchronisation).  Called through the C ABI with caller-owned buffers, it must give the
 same results as pd_sinkhorn_batch on two calls in a row (the second call reuses
 the static workspace the first one left behind), and refuse batches that do not
 fit its fixed workspace.  Collected last so that a failure here does not stop a
@@ -37,9 +38,10 @@ def test_noalloc_matches_pd_sinkhorn_batch_on_two_calls():
     lib = api.load(build_if_missing=True)
     ctx = api.Context(0)
     try:
-        for seed, d, P, gamma in ((3, 64, 6, 5e-3), (4, 128, 4, 1e-3)):
+        for seed, d, P, gamma, every in ((3, 64, 6, 5e-3, 0), (4, 128, 4, 1e-3, 16)):
             hist, mass, pairs = _problem(ctx, seed, d, P)
             prm = api.pd_sinkhorn_default_params(gamma, d, max_iter=3000, tol=1e-6)
+            prm.absorb_every = every   # a non-default parameter reaches both entry points alike
             ref = api.pd_sinkhorn_batch(ctx, hist, mass, hist, mass, prm, pairs=pairs, want_marginals=True,
                                         want_potentials=True)
             out = _outputs(P, d * d + 1)
@@ -71,6 +73,12 @@ def test_noalloc_rejects_batches_beyond_its_workspace():
         prm = api.pd_sinkhorn_default_params(1e-3, 128, max_iter=10, tol=0.0)
         with pytest.raises(api.PdError) as e:
             api.pd_sinkhorn_batch_noalloc(hist, mass, hist, mass, prm, pairs=pairs, out=_outputs(64, 128 * 128 + 1))
+        assert e.value.status == api.PD_ERR_INVALID
+        # the gamma-continuation is not run by this entry point: refused, not ignored
+        prm.eps_stages = 2
+        with pytest.raises(api.PdError) as e:
+            api.pd_sinkhorn_batch_noalloc(hist[:2], mass[:2], hist[:2], mass[:2], prm, pairs=pairs[:1],
+                                          out=_outputs(1, 128 * 128 + 1))
         assert e.value.status == api.PD_ERR_INVALID
     finally:
         ctx.close()
