@@ -178,6 +178,34 @@ pd_status pd_sinkhorn_bounds(pd_ctx* ctx, const uint32_t* histA, const uint32_t*
                              float* err, int32_t* status, pd_stream stream);
 
 /*
+ * pd_workspace_query -- device workspace bytes a context holds for one call of
+ * operation `op` with these parameters (n = P pairs for PD_OP_SINKHORN and
+ * PD_OP_BOUNDS, N diagrams for the others; k = measures or centroids, read by
+ * the k-means operations only).  The figure is the largest the call needs
+ * (with the optional caller arrays of pd_barycenter_grad / pd_kmeans_assign
+ * NULL).  A context allocates this itself (grow-only, kept until
+ * pd_ctx_destroy), or the caller supplies it with pd_ctx_set_workspace.
+ * Library feature for memory planning; no counterpart in the paper.
+ * Errors: PD_ERR_INVALID (unknown op, NULL bytes/params, bad d, n or k).
+ */
+enum { PD_OP_SINKHORN = 0, PD_OP_BOUNDS = 1, PD_OP_BARYCENTER = 2, PD_OP_BARY_GRAD = 3,
+       PD_OP_KMEANS_ASSIGN = 4, PD_OP_KMEANS = 5 };
+pd_status pd_workspace_query(int op, const pd_sinkhorn_params* params, int n, int k, size_t* bytes);
+
+/*
+ * pd_ctx_set_workspace -- make `ws` (device memory of `bytes` bytes, 256-byte
+ * aligned, owned by the caller) the context's workspace: from then on the
+ * context allocates no workspace of its own (it frees what it held), and a
+ * call whose need (pd_workspace_query) exceeds `bytes` returns PD_ERR_OOM
+ * without running.  ws = NULL returns to library-allocated workspace.  The
+ * buffer must stay valid until the next pd_ctx_set_workspace or
+ * pd_ctx_destroy; calls on this context overwrite it.  Synchronises the
+ * device.  (The serving pools of pd_serve_create are sized by their own
+ * configuration.)  Errors: PD_ERR_INVALID (misaligned ws), PD_ERR_CUDA.
+ */
+pd_status pd_ctx_set_workspace(pd_ctx* ctx, void* ws, size_t bytes);
+
+/*
  * pd_barycenter -- Alg. 2 (smoothed barycenter).  z starts as z_init, or, when
  * z_init is NULL, as the uniform measure above the diagonal (every cell j >= i
  * gets mean_i |D_i| / (d(d+1)/2)).  Each of the outer_iters steps solves the N
@@ -190,13 +218,21 @@ pd_status pd_sinkhorn_bounds(pd_ctx* ctx, const uint32_t* histA, const uint32_t*
  *   params      : inner Sinkhorn parameters (precision must be PD_FP32)
  *   lambda      : step size (> 0); outer_iters >= 0
  *   z_init      : double [d*d] or NULL (device); z_out: double [d*d] (device)
+ *   rel_energy_tol : the stop of the barycenter experiment (Sec. 5): after step
+ *                 t >= 1, stop when |E_t / E_{t-1} - 1| < rel_energy_tol, E_t the
+ *                 energy of z_t below (the update of step t is applied first);
+ *                 0 runs all outer_iters steps
  *   energy      : double [outer_iters] or NULL: mean transport cost of step t's
- *                 plans, (1/N) sum_i <P_i, C> (the energy of z_t) (device)
- * Synchronises `stream`.  Errors: PD_ERR_INVALID, PD_ERR_OOM, PD_ERR_CUDA.
+ *                 plans, (1/N) sum_i <P_i, C> (the energy of z_t) (device);
+ *                 entries past the steps run are not written
+ *   steps_host  : int (host) or NULL: number of steps run
+ * Synchronises `stream` (once per step when rel_energy_tol > 0, to read E_t).
+ * Errors: PD_ERR_INVALID, PD_ERR_OOM, PD_ERR_CUDA.
  */
 pd_status pd_barycenter(pd_ctx* ctx, const uint32_t* hist, const uint32_t* mass, int N,
                         const pd_sinkhorn_params* params, double lambda, int outer_iters,
-                        const double* z_init, double* z_out, double* energy, pd_stream stream);
+                        double rel_energy_tol, const double* z_init, double* z_out, double* energy,
+                        int* steps_host, pd_stream stream);
 
 /*
  * pd_barycenter_grad / pd_barycenter_apply -- one Alg. 2 step split at its only

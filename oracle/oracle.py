@@ -63,6 +63,10 @@ def _load():
             lib.or_barycenter_s.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                             _dp, _dp, _dp, ctypes.c_int]
+            lib.or_barycenter_e.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            _dp, _dp, _dp, ctypes.c_int, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_int)]
             lib.or_sharpen.argtypes = [ctypes.c_int, _dp, ctypes.c_double]
             lib.or_sharpen.restype = ctypes.c_double
             lib.or_kmeans.argtypes = [ctypes.c_int, ctypes.c_double, _u32p, ctypes.c_int, ctypes.c_int,
@@ -196,20 +200,23 @@ def sharpen(d, z, H0):
     return z.reshape(d, d), beta
 
 
-def barycenter(d, gamma, hists, lam, outer_iters, max_iter, tol, z_init=None, sharpen=False):
-    """Alg. 2 (optionally with entropic sharpening after every step).
-    hists: uint32 [N,d,d].  Returns (z [d,d], energy [outer_iters])."""
+def barycenter(d, gamma, hists, lam, outer_iters, max_iter, tol, z_init=None, sharpen=False,
+               rel_energy_tol=0.0):
+    """Alg. 2 (optionally with entropic sharpening after every step, and with
+    the stop |E_t/E_{t-1} - 1| < rel_energy_tol after step t >= 1).
+    hists: uint32 [N,d,d].  Returns (z [d,d], energy [steps run])."""
     hists = np.ascontiguousarray(hists, dtype=np.uint32)
     N = hists.shape[0]
     zi = None if z_init is None else np.ascontiguousarray(z_init, dtype=np.float64).ravel()
     z = np.empty(d * d)
-    e = np.empty(outer_iters)
-    rc = _load().or_barycenter_s(d, gamma, _ptr(hists, _u32p), N, float(lam), int(outer_iters),
+    e = np.empty(max(outer_iters, 1))
+    steps = ctypes.c_int(0)
+    rc = _load().or_barycenter_e(d, gamma, _ptr(hists, _u32p), N, float(lam), int(outer_iters),
                                  int(max_iter), float(tol), _ptr(zi, _dp), _ptr(z, _dp), _ptr(e, _dp),
-                                 1 if sharpen else 0)
+                                 1 if sharpen else 0, float(rel_energy_tol), ctypes.byref(steps))
     if rc != 0:
         raise ValueError("or_barycenter failed")
-    return z.reshape(d, d), e
+    return z.reshape(d, d), e[:steps.value]
 
 
 def kmeans(d, gamma, hists, k, lam, rounds, bary_steps, max_iter, tol, seed):

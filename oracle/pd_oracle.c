@@ -29,7 +29,8 @@
  *                        as a = (hist_A, |B|), b = (hist_B, |A|) (Prop. 1).
  *   or_barycenter     -- Alg. 2 (smoothed barycenter) with the gradient of
  *                        Prop. (gradient of E^gamma) and the multiplicative
- *                        update.
+ *                        update; or_barycenter_e adds the barycenter
+ *                        experiment's stop |E_{t+1}/E_t - 1| < tol (Sec. 5).
  *   or_kmeans         -- Sec. 5 k-means: assignment by Alg. 1 cost, centroid
  *                        update by Alg. 2.
  *   or_sharpen        -- entropic sharpening of a measure (Solomon et al., the
@@ -360,9 +361,14 @@ double or_sharpen(int d, double* z, double H0) {
     return beta;
 }
 
-int or_barycenter_s(int d, double gamma, const uint32_t* hists, int N, double lambda,
+/* Alg. 2 with the stopping rule of the barycenter experiment (Sec. 5, Fig. 5):
+ * after step t (its Sinkhorn solves give the energy E_t of z_t, then z is
+ * updated), stop when t >= 1 and |E_t / E_{t-1} - 1| < rel_energy_tol
+ * (rel_energy_tol <= 0: run all outer_iters steps).  *steps_out (if not NULL)
+ * receives the number of steps run; energy[0 .. steps-1] is written. */
+int or_barycenter_e(int d, double gamma, const uint32_t* hists, int N, double lambda,
                     int outer_iters, int max_iter, double tol, const double* z_init,
-                    double* z_out, double* energy, int sharpen) {
+                    double* z_out, double* energy, int sharpen, double rel_energy_tol, int* steps_out) {
     const int D = d * d, n = D + 1;
     if (N <= 0 || d < 2) return -1;
     double* z = (double*)malloc(sizeof(double) * D);
@@ -391,6 +397,8 @@ int or_barycenter_s(int d, double gamma, const uint32_t* hists, int N, double la
         }
         free(w);
     }
+    double e_prev = NAN;
+    int steps = 0;
     for (int t = 0; t < outer_iters; ++t) {
         double zm = 0;
         for (int x = 0; x < D; ++x) zm += z[x];
@@ -408,11 +416,10 @@ int or_barycenter_s(int d, double gamma, const uint32_t* hists, int N, double la
             bad |= (rc != 0);
             free(a); free(b); free(gw);
         }
-        if (energy) {
-            or_ksum e = {0, 0};
-            for (int i = 0; i < N; ++i) ks_add(&e, costs[i]);
-            energy[t] = ks_val(&e) / N;
-        }
+        or_ksum ek = {0, 0};
+        for (int i = 0; i < N; ++i) ks_add(&ek, costs[i]);
+        const double e_t = ks_val(&ek) / N;
+        if (energy) energy[t] = e_t;
         double lzm = log(zm);
         for (int x = 0; x < D; ++x) {
             if (!(z[x] > 0)) continue;
@@ -423,10 +430,21 @@ int or_barycenter_s(int d, double gamma, const uint32_t* hists, int N, double la
             z[x] *= exp(-lambda * grad);
         }
         if (sharpen) or_sharpen(d, z, H0);
+        steps = t + 1;
+        if (rel_energy_tol > 0 && t >= 1 && fabs(e_t / e_prev - 1.0) < rel_energy_tol) break;
+        e_prev = e_t;
     }
     memcpy(z_out, z, sizeof(double) * D);
+    if (steps_out) *steps_out = steps;
     free(z); free(gs); free(fs); free(costs);
     return bad ? -1 : 0;
+}
+
+int or_barycenter_s(int d, double gamma, const uint32_t* hists, int N, double lambda,
+                    int outer_iters, int max_iter, double tol, const double* z_init,
+                    double* z_out, double* energy, int sharpen) {
+    return or_barycenter_e(d, gamma, hists, N, lambda, outer_iters, max_iter, tol, z_init, z_out, energy,
+                           sharpen, 0.0, NULL);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -26,7 +26,8 @@ EXPORTED = ["pd_abi_version", "pd_ctx_create", "pd_ctx_destroy", "pd_last_error"
             "pd_sinkhorn_batch_noalloc", "pd_barycenter", "pd_kmeans", "pd_serve_default_config",
             "pd_serve_create", "pd_serve_load_centroids", "pd_serve_submit", "pd_serve_poll", "pd_serve_wait",
             "pd_serve_inject_failure", "pd_serve_destroy", "pd_sinkhorn_bounds", "pd_barycenter_grad",
-            "pd_barycenter_apply", "pd_kmeans_assign"]
+            "pd_barycenter_apply", "pd_kmeans_assign", "pd_workspace_query", "pd_ctx_set_workspace"]
+PD_OP_SINKHORN, PD_OP_BOUNDS, PD_OP_BARYCENTER, PD_OP_BARY_GRAD, PD_OP_KMEANS_ASSIGN, PD_OP_KMEANS = 0, 1, 2, 3, 4, 5
 PD_Q_DISTANCE, PD_Q_NEAREST = 0, 1
 SERVE_D = (32, 64, 128, 256)
 PD_K_RASTER, PD_K_SETUP, PD_K_LOGSTEP, PD_K_ABSORB, PD_K_ITER, PD_K_FINALIZE, PD_K_COUNT = 0, 1, 2, 3, 4, 5, 16
@@ -105,7 +106,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.pd_sinkhorn_bounds.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
                                            ctypes.POINTER(SinkhornParams), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         lib.pd_barycenter.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(SinkhornParams), ctypes.c_double,
-                                      ctypes.c_int, _vp, _vp, _vp, _vp]
+                                      ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int), _vp]
+        lib.pd_workspace_query.argtypes = [ctypes.c_int, ctypes.POINTER(SinkhornParams), ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_size_t)]
+        lib.pd_ctx_set_workspace.argtypes = [_vp, _vp, ctypes.c_size_t]
         lib.pd_kmeans.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SinkhornParams),
                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _vp, _vp, _vp, _vp]
         lib.pd_barycenter_grad.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SinkhornParams),
@@ -252,16 +256,35 @@ def pd_sinkhorn_bounds(ctx: Context, histA, massA, histB, massB, params: Sinkhor
 
 
 def pd_barycenter(ctx: Context, hist, mass, params: SinkhornParams, lam: float, outer_iters: int, z_init=None,
-                  stream=None):
-    """Alg. 2 on N histograms (int32 CUDA tensors holding uint32 counts).
-    Returns (z [d,d] float64 CUDA tensor, energy [outer_iters] float64)."""
+                  stream=None, rel_energy_tol: float = 0.0):
+    """Alg. 2 on N histograms (int32 CUDA tensors holding uint32 counts), at
+    most outer_iters steps; with rel_energy_tol > 0 it stops after the first
+    step t >= 1 with |E_t/E_{t-1} - 1| < rel_energy_tol.
+    Returns (z [d,d] float64 CUDA tensor, energy [steps run] float64)."""
     import torch
     d = params.d
     z = torch.empty((d, d), dtype=torch.float64, device=hist.device)
     e = torch.empty(max(outer_iters, 1), dtype=torch.float64, device=hist.device)
+    steps = ctypes.c_int(0)
     ctx.check(ctx.lib.pd_barycenter(ctx.handle, _ptr(hist), _ptr(mass), int(hist.shape[0]), ctypes.byref(params),
-                                    float(lam), int(outer_iters), _ptr(z_init), _ptr(z), _ptr(e), _stream(stream)))
-    return z, e[:outer_iters]
+                                    float(lam), int(outer_iters), float(rel_energy_tol), _ptr(z_init), _ptr(z),
+                                    _ptr(e), ctypes.byref(steps), _stream(stream)))
+    return z, e[:steps.value]
+
+
+def pd_workspace_query(op: int, params: SinkhornParams, n: int, k: int = 0) -> int:
+    """Device workspace bytes a context holds for one call of `op` (PD_OP_*)."""
+    out = ctypes.c_size_t(0)
+    st = load().pd_workspace_query(int(op), ctypes.byref(params), int(n), int(k), ctypes.byref(out))
+    if st != PD_OK:
+        raise PdError(st, "pd_workspace_query failed")
+    return int(out.value)
+
+
+def pd_ctx_set_workspace(ctx: Context, ws=None, nbytes: int = 0):
+    """Give the context a caller-owned device buffer (a CUDA tensor, 256-byte
+    aligned) as its workspace; None returns to library-allocated workspace."""
+    ctx.check(ctx.lib.pd_ctx_set_workspace(ctx.handle, _ptr(ws), int(nbytes) if ws is not None else 0))
 
 
 def pd_barycenter_grad(ctx: Context, hist, mass, params: SinkhornParams, z, k: int = 1, owner=None, g_warm=None,

@@ -22,6 +22,12 @@ struct pd_ctx {
     size_t ws2_bytes = 0;
     int* dflag = nullptr;      // small device scratch (error flags, counters)
     int* hflag = nullptr;      // pinned host mirror
+    double* hval = nullptr;    // pinned host doubles (per-step energies)
+    // caller-supplied workspace (pd_ctx_set_workspace): when set, ws is carved
+    // from its start and ws2 from its end, and nothing is allocated
+    char* ext = nullptr;
+    size_t ext_bytes = 0;
+    size_t ws2_live = 0;       // bytes of ext used by ws2 in the current call
     // launch profiler
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;   // free events
@@ -62,7 +68,14 @@ static pd_status fail(pd_ctx* c, pd_status s, const char* fmt, ...) {
             return fail(ctx, PD_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(_e));    \
     } while (0)
 
-extern "C" int pd_abi_version(void) { return 1; }
+// Start of every entry point that takes a context: clear the message and the
+// per-call use of a caller-supplied workspace.
+static void call_begin(pd_ctx* c) {
+    call_begin(c);
+    c->ws2_live = 0;
+}
+
+extern "C" int pd_abi_version(void) { return 2; }
 
 extern "C" pd_status pd_ctx_create(int device, pd_ctx** out) {
     if (!out) return PD_ERR_INVALID;
@@ -74,6 +87,9 @@ extern "C" pd_status pd_ctx_create(int device, pd_ctx** out) {
     c->device = device;
     if (cudaMalloc(&c->dflag, 64 * sizeof(int)) != cudaSuccess) { delete c; return PD_ERR_OOM; }
     if (cudaMallocHost(&c->hflag, 64 * sizeof(int)) != cudaSuccess) { cudaFree(c->dflag); delete c; return PD_ERR_OOM; }
+    if (cudaMallocHost(&c->hval, 8 * sizeof(double)) != cudaSuccess) {
+        cudaFree(c->dflag); cudaFreeHost(c->hflag); delete c; return PD_ERR_OOM;
+    }
     *out = c;
     return PD_OK;
 }
@@ -84,10 +100,13 @@ extern "C" void pd_ctx_destroy(pd_ctx* c) {
     cudaDeviceSynchronize();
     for (auto& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
-    if (c->ws) cudaFree(c->ws);
-    if (c->ws2) cudaFree(c->ws2);
+    if (!c->ext) {
+        if (c->ws) cudaFree(c->ws);
+        if (c->ws2) cudaFree(c->ws2);
+    }
     if (c->dflag) cudaFree(c->dflag);
     if (c->hflag) cudaFreeHost(c->hflag);
+    if (c->hval) cudaFreeHost(c->hval);
     delete c;
 }
 
@@ -95,7 +114,7 @@ extern "C" const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str(
 
 extern "C" pd_status pd_profile_enable(pd_ctx* c, int enable) {
     if (!c) return PD_ERR_INVALID;
-    c->err.clear();
+    call_begin(c);
     if (enable) {
         if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PD_ERR_CUDA, "cudaSetDevice failed");
         for (auto& r : c->recs) { c->ev_pool.push_back(r.a); c->ev_pool.push_back(r.b); }
@@ -107,7 +126,7 @@ extern "C" pd_status pd_profile_enable(pd_ctx* c, int enable) {
 
 extern "C" pd_status pd_profile_read(pd_ctx* c, double* ms, int64_t* launches) {
     if (!c) return PD_ERR_INVALID;
-    c->err.clear();
+    call_begin(c);
     if (ms) for (int k = 0; k < PD_K_COUNT; ++k) ms[k] = 0.0;
     if (launches) for (int k = 0; k < PD_K_COUNT; ++k) launches[k] = 0;
     for (auto& r : c->recs) {
@@ -125,7 +144,7 @@ extern "C" pd_status pd_profile_read(pd_ctx* c, double* ms, int64_t* launches) {
 extern "C" pd_status pd_rasterize(pd_ctx* c, const double* birth, const double* death, const int64_t* offsets,
                                   int B, int d, uint32_t* hist, uint32_t* mass, pd_stream stream) {
     if (!c) return PD_ERR_INVALID;
-    c->err.clear();
+    call_begin(c);
     if (B < 0 || d < 2 || d > 256) return fail(c, PD_ERR_INVALID, "pd_rasterize: need B >= 0 and 2 <= d <= 256");
     if (B == 0) return PD_OK;
     if (!offsets || !hist || !mass) return fail(c, PD_ERR_INVALID, "pd_rasterize: NULL pointer");
@@ -233,8 +252,25 @@ static SkRun make_run(const pd_sinkhorn_params* prm) {
     return r;
 }
 
-// Grow-only device buffer owned by the context.
+// Grow-only device buffer owned by the context, or, with a caller-supplied
+// workspace, a range of it: the Sinkhorn workspace (ws) at its start, the
+// outer-loop buffers (ws2, always taken first within a call) at its end.
 static pd_status ensure_buffer(pd_ctx* c, void** buf, size_t* have, size_t need, cudaStream_t s) {
+    if (c->ext) {
+        const bool is_ws2 = (buf == &c->ws2);
+        const size_t n = align256(need);
+        if (is_ws2 ? n > c->ext_bytes : n + c->ws2_live > c->ext_bytes)
+            return fail(c, PD_ERR_OOM, "caller-supplied workspace of %zu bytes is too small (%zu more needed)",
+                        c->ext_bytes, n + (is_ws2 ? 0 : c->ws2_live) - c->ext_bytes);
+        if (is_ws2) {
+            *buf = c->ext + (c->ext_bytes - n);
+            c->ws2_live = n;
+        } else {
+            *buf = c->ext;
+        }
+        *have = n;
+        return PD_OK;
+    }
     if (need <= *have) return PD_OK;
     CUDA_TRY(c, cudaStreamSynchronize(s));
     if (*buf) cudaFree(*buf);
@@ -420,7 +456,7 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
                                        float* row_marg, float* col_marg, double* f, double* g, int32_t* iters,
                                        float* err, int32_t* status, pd_stream stream) {
     if (!c) return PD_ERR_INVALID;
-    c->err.clear();
+    call_begin(c);
     if (!prm) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: NULL params");
     const int d = prm->d;
     if (d < 2 || d > 256) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: d must be in [2,256]");
@@ -443,16 +479,9 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     SkWS w;
     int* counter;
     size_t need = pd_carve_ws(nullptr, P, d, dp, prm->gamma, nullptr, &counter);
-    if (need > c->ws_bytes) {
-        CUDA_TRY(c, cudaStreamSynchronize(s));
-        if (c->ws) cudaFree(c->ws);
-        c->ws = nullptr;
-        c->ws_bytes = 0;
-        if (cudaMalloc(&c->ws, need) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(c, PD_ERR_OOM, "pd_sinkhorn_batch: cannot allocate %zu bytes of workspace", need);
-        }
-        c->ws_bytes = need;
+    {
+        pd_status st0 = ensure_buffer(c, &c->ws, &c->ws_bytes, need, s);
+        if (st0 != PD_OK) return st0;
     }
     pd_carve_ws((char*)c->ws, P, d, dp, prm->gamma, &w, &counter);
     w.histA = histA; w.histB = histB; w.massA = massA; w.massB = massB; w.pairs = pairs;
@@ -547,7 +576,7 @@ extern "C" pd_status pd_sinkhorn_bounds(pd_ctx* c, const uint32_t* histA, const 
                                         double* lower, double* upper, int32_t* iters, float* err, int32_t* status,
                                         pd_stream stream) {
     if (!c) return PD_ERR_INVALID;
-    c->err.clear();
+    call_begin(c);
     if (!prm) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: NULL params");
     const int d = prm->d;
     if (d < 2 || d > 256) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_bounds: d must be in [2,256]");
@@ -589,65 +618,116 @@ struct Arena {
     template <class T> T* take(size_t n) { T* r = (T*)(base ? base + off : nullptr); off += (n * sizeof(T) + 255) & ~size_t(255); return r; }
 };
 
+// Outer-loop buffers of pd_barycenter in ws2 (base == nullptr: sizes only).
+struct BaryBufs {
+    double *z, *zmass, *f, *g, *cost, *ebuf;
+    int32_t *pairs, *iters, *status;
+    float* err;
+    unsigned long long* H0bits;
+};
+static size_t bary_layout(char* base, int N, int d, BaryBufs* o) {
+    const int D = d * d, n1 = D + 1;
+    Arena a{base, 0};
+    BaryBufs t;
+    t.z = a.take<double>(D); t.zmass = a.take<double>(1); t.f = a.take<double>((size_t)N * n1);
+    t.g = a.take<double>((size_t)N * n1); t.cost = a.take<double>(N); t.pairs = a.take<int32_t>(2 * (size_t)N);
+    t.iters = a.take<int32_t>(N); t.err = a.take<float>(N); t.status = a.take<int32_t>(N);
+    t.H0bits = a.take<unsigned long long>(1); t.ebuf = a.take<double>(1);
+    if (o) *o = t;
+    return a.off;
+}
+
 extern "C" pd_status pd_barycenter(pd_ctx* c, const uint32_t* hist, const uint32_t* mass, int N,
                                    const pd_sinkhorn_params* prm, double lambda, int outer_iters,
-                                   const double* z_init, double* z_out, double* energy, pd_stream stream) {
+                                   double rel_energy_tol, const double* z_init, double* z_out, double* energy,
+                                   int* steps_host, pd_stream stream) {
     if (!c) return PD_ERR_INVALID;
-    c->err.clear();
+    call_begin(c);
+    if (steps_host) *steps_host = 0;
     pd_status st = check_params(c, prm, "pd_barycenter");
     if (st != PD_OK) return st;
     if (N < 1 || !hist || !mass || !z_out) return fail(c, PD_ERR_INVALID, "pd_barycenter: need N >= 1, hist, mass, z_out");
     if (!(lambda > 0) || outer_iters < 0) return fail(c, PD_ERR_INVALID, "pd_barycenter: need lambda > 0, outer_iters >= 0");
+    if (!(rel_energy_tol >= 0) || !std::isfinite(rel_energy_tol))
+        return fail(c, PD_ERR_INVALID, "pd_barycenter: rel_energy_tol must be finite and >= 0");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(c, cudaSetDevice(c->device));
-    const int d = prm->d, D = d * d, n1 = D + 1;
-    Arena a{nullptr, 0};
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) {
-            st = ensure_buffer(c, &c->ws2, &c->ws2_bytes, a.off, s);
-            if (st != PD_OK) return st;
-            a = Arena{(char*)c->ws2, 0};
-        }
-        a.take<double>(D); a.take<double>(1); a.take<double>((size_t)N * n1); a.take<double>((size_t)N * n1);
-        a.take<double>(N); a.take<int32_t>(2 * (size_t)N); a.take<int32_t>(N); a.take<float>(N); a.take<int32_t>(N);
-        a.take<unsigned long long>(1);
-        if (pass == 0) continue;
-    }
-    a.off = 0;
-    double* z = a.take<double>(D);
-    double* zmass = a.take<double>(1);
-    double* f = a.take<double>((size_t)N * n1);
-    double* g = a.take<double>((size_t)N * n1);
-    double* cost = a.take<double>(N);
-    int32_t* pairs = a.take<int32_t>(2 * (size_t)N);
-    int32_t* iters = a.take<int32_t>(N);
-    float* err = a.take<float>(N);
-    int32_t* status = a.take<int32_t>(N);
-    unsigned long long* H0bits = a.take<unsigned long long>(1);
+    const int d = prm->d, D = d * d;
+    st = ensure_buffer(c, &c->ws2, &c->ws2_bytes, bary_layout(nullptr, N, d, nullptr), s);
+    if (st != PD_OK) return st;
+    BaryBufs B;
+    bary_layout((char*)c->ws2, N, d, &B);
+    double* z = B.z;
     SkWS w;
     int* counter;
     st = sinkhorn_ws(c, N, prm, &w, &counter, s);
     if (st != PD_OK) return st;
-    if (prm->bary_sharpen) CUDA_TRY(c, outer_input_entropy(hist, N, d, H0bits, s));
+    if (prm->bary_sharpen) CUDA_TRY(c, outer_input_entropy(hist, N, d, B.H0bits, s));
     if (z_init) CUDA_TRY(c, cudaMemcpyAsync(z, z_init, sizeof(double) * D, cudaMemcpyDeviceToDevice, s));
     else CUDA_TRY(c, outer_bary_init_uniform(z, mass, N, d, s));
-    CUDA_TRY(c, outer_owner_pairs(nullptr, N, pairs, s));
+    CUDA_TRY(c, outer_owner_pairs(nullptr, N, B.pairs, s));
     SkRun r = make_run(prm);
     r.pot_support_only = 1;
+    const bool stop_rule = rel_energy_tol > 0;
+    double e_prev = 0.0;
+    int steps = 0;
     for (int t = 0; t < outer_iters; ++t) {
-        CUDA_TRY(c, outer_measure_mass(z, 1, d, zmass, s));
+        CUDA_TRY(c, outer_measure_mass(z, 1, d, B.zmass, s));
         w.histA = nullptr; w.massA = nullptr; w.wA = z;            // a side: z + R a_i
         w.histB = hist; w.massB = mass; w.wB = nullptr;            // b side: a_i + R z
-        w.pairs = pairs;
-        st = lse_solve(c, w, r, t > 0 ? g : nullptr, cost, nullptr, nullptr, f, g, iters, err, status, counter, s);
+        w.pairs = B.pairs;
+        st = lse_solve(c, w, r, t > 0 ? B.g : nullptr, B.cost, nullptr, nullptr, B.f, B.g, B.iters, B.err, B.status,
+                       counter, s);
         if (st != PD_OK) return st;
-        if (energy) CUDA_TRY(c, outer_mean(cost, N, energy + t, s));
-        CUDA_TRY(c, outer_bary_step(z, zmass, f, g, nullptr, N, 1, d, prm->gamma, lambda, s));
-        if (prm->bary_sharpen) CUDA_TRY(c, outer_sharpen(z, 1, d, H0bits, s));
+        double* et = energy ? energy + t : B.ebuf;
+        if (energy || stop_rule) CUDA_TRY(c, outer_mean(B.cost, N, et, s));
+        CUDA_TRY(c, outer_bary_step(z, B.zmass, B.f, B.g, nullptr, N, 1, d, prm->gamma, lambda, s));
+        if (prm->bary_sharpen) CUDA_TRY(c, outer_sharpen(z, 1, d, B.H0bits, s));
+        steps = t + 1;
+        if (stop_rule) {
+            // the barycenter experiment's stop (Sec. 5): |E_t / E_{t-1} - 1| < rel_energy_tol
+            CUDA_TRY(c, cudaMemcpyAsync(c->hval, et, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            const double e_t = c->hval[0];
+            if (t >= 1 && std::fabs(e_t / e_prev - 1.0) < rel_energy_tol) break;
+            e_prev = e_t;
+        }
     }
     CUDA_TRY(c, cudaMemcpyAsync(z_out, z, sizeof(double) * D, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (steps_host) *steps_host = steps;
     return PD_OK;
+}
+
+// Buffers of pd_barycenter_grad in ws2 (own_g: g is not the caller's g_warm).
+static size_t grad_layout(char* base, int N, int d, bool own_g, double** f, double** g, double** cost,
+                          int32_t** pairs, int32_t** iters, float** err, int32_t** status) {
+    const size_t n1 = (size_t)d * d + 1;
+    Arena ar{base, 0};
+    *f = ar.take<double>((size_t)N * n1); *g = ar.take<double>(own_g ? (size_t)N * n1 : 0);
+    *cost = ar.take<double>(N); *pairs = ar.take<int32_t>(2 * (size_t)N); *iters = ar.take<int32_t>(N);
+    *err = ar.take<float>(N); *status = ar.take<int32_t>(N);
+    return ar.off;
+}
+
+// Buffers of pd_kmeans_assign in ws2 (own_cost: the caller passed no cost array).
+static size_t assign_layout(char* base, size_t NK, bool own_cost, double** cst, int32_t** pairs, int32_t** iters,
+                            float** err, int32_t** status) {
+    Arena ar{base, 0};
+    *cst = ar.take<double>(own_cost ? NK : 0); *pairs = ar.take<int32_t>(2 * NK); *iters = ar.take<int32_t>(NK);
+    *err = ar.take<float>(NK); *status = ar.take<int32_t>(NK);
+    return ar.off;
+}
+
+// Buffers of pd_kmeans in ws2.
+static size_t kmeans_layout(char* base, int N, int k, int d, double** zmass, double** f, double** g, double** cost,
+                            int32_t** pairs, int32_t** iters, float** err, int32_t** status, int32_t** idx) {
+    const size_t n1 = (size_t)d * d + 1, NK = (size_t)N * k;
+    Arena ar{base, 0};
+    *zmass = ar.take<double>(k); *f = ar.take<double>((size_t)N * n1); *g = ar.take<double>((size_t)N * n1);
+    *cost = ar.take<double>(NK); *pairs = ar.take<int32_t>(2 * NK); *iters = ar.take<int32_t>(NK);
+    *err = ar.take<float>(NK); *status = ar.take<int32_t>(NK); *idx = ar.take<int32_t>(k);
+    return ar.off;
 }
 
 // Sharded Alg. 2 step, first half: solve this shard's pairs
@@ -659,7 +739,7 @@ extern "C" pd_status pd_barycenter_grad(pd_ctx* c, const uint32_t* hist, const u
                                         double* g_warm, int warm, double* gsum, double* count, double* cost_sum,
                                         pd_stream stream) {
     if (!c) return PD_ERR_INVALID;
-    c->err.clear();
+    call_begin(c);
     pd_status st = check_params(c, prm, "pd_barycenter_grad");
     if (st == PD_OK && prm->bary_sharpen)
         return fail(c, PD_ERR_INVALID, "pd_barycenter_grad: bary_sharpen is not supported (sharpening is not part of the sharded step)");
@@ -677,20 +757,12 @@ extern "C" pd_status pd_barycenter_grad(pd_ctx* c, const uint32_t* hist, const u
         CUDA_TRY(c, cudaStreamSynchronize(s));
         if (c->hflag[0]) return fail(c, PD_ERR_INVALID, "pd_barycenter_grad: owner values must lie in [0, k)");
     }
-    const int d = prm->d, n1 = d * d + 1;
-    Arena a{nullptr, 0};
-    auto layout = [&](Arena& ar, double** f, double** g, double** cost, int32_t** pairs, int32_t** iters, float** err,
-                      int32_t** status) {
-        *f = ar.take<double>((size_t)N * n1); *g = ar.take<double>(g_warm ? 0 : (size_t)N * n1);
-        *cost = ar.take<double>(N); *pairs = ar.take<int32_t>(2 * (size_t)N); *iters = ar.take<int32_t>(N);
-        *err = ar.take<float>(N); *status = ar.take<int32_t>(N);
-    };
+    const int d = prm->d;
     double *f, *g, *cost; int32_t *pairs, *iters, *status; float* err;
-    layout(a, &f, &g, &cost, &pairs, &iters, &err, &status);
-    st = ensure_buffer(c, &c->ws2, &c->ws2_bytes, a.off, s);
+    st = ensure_buffer(c, &c->ws2, &c->ws2_bytes,
+                       grad_layout(nullptr, N, d, g_warm == nullptr, &f, &g, &cost, &pairs, &iters, &err, &status), s);
     if (st != PD_OK) return st;
-    a = Arena{(char*)c->ws2, 0};
-    layout(a, &f, &g, &cost, &pairs, &iters, &err, &status);
+    grad_layout((char*)c->ws2, N, d, g_warm == nullptr, &f, &g, &cost, &pairs, &iters, &err, &status);
     if (g_warm) g = g_warm;
     SkWS w;
     int* counter;
@@ -717,7 +789,7 @@ extern "C" pd_status pd_kmeans_assign(pd_ctx* c, const uint32_t* hist, const uin
                                       const pd_sinkhorn_params* prm, const double* centroids, int32_t* assign,
                                       double* cost, double* objective, pd_stream stream) {
     if (!c) return PD_ERR_INVALID;
-    c->err.clear();
+    call_begin(c);
     pd_status st = check_params(c, prm, "pd_kmeans_assign");
     if (st != PD_OK) return st;
     if (N < 1 || k < 1 || !hist || !mass || !centroids || !assign)
@@ -726,17 +798,11 @@ extern "C" pd_status pd_kmeans_assign(pd_ctx* c, const uint32_t* hist, const uin
     CUDA_TRY(c, cudaSetDevice(c->device));
     const size_t NK = (size_t)N * k;
     if (NK > (size_t)INT32_MAX) return fail(c, PD_ERR_INVALID, "pd_kmeans_assign: N * k too large");
-    Arena a{nullptr, 0};
-    auto layout = [&](Arena& ar, double** cst, int32_t** pairs, int32_t** iters, float** err, int32_t** status) {
-        *cst = ar.take<double>(cost ? 0 : NK); *pairs = ar.take<int32_t>(2 * NK); *iters = ar.take<int32_t>(NK);
-        *err = ar.take<float>(NK); *status = ar.take<int32_t>(NK);
-    };
     double* cst; int32_t *pairs, *iters, *status; float* err;
-    layout(a, &cst, &pairs, &iters, &err, &status);
-    st = ensure_buffer(c, &c->ws2, &c->ws2_bytes, a.off, s);
+    st = ensure_buffer(c, &c->ws2, &c->ws2_bytes, assign_layout(nullptr, NK, cost == nullptr, &cst, &pairs, &iters, &err,
+                                                                &status), s);
     if (st != PD_OK) return st;
-    a = Arena{(char*)c->ws2, 0};
-    layout(a, &cst, &pairs, &iters, &err, &status);
+    assign_layout((char*)c->ws2, NK, cost == nullptr, &cst, &pairs, &iters, &err, &status);
     if (cost) cst = cost;
     SkWS w;
     int* counter;
@@ -760,7 +826,7 @@ extern "C" pd_status pd_kmeans_assign(pd_ctx* c, const uint32_t* hist, const uin
 extern "C" pd_status pd_barycenter_apply(pd_ctx* c, double* z, int k, int d, const double* gsum, const double* count,
                                          double gamma, double lambda, pd_stream stream) {
     if (!c) return PD_ERR_INVALID;
-    c->err.clear();
+    call_begin(c);
     if (!z || !gsum || !count || k < 1 || d < 2 || d > 256 || !(gamma > 0) || !(lambda > 0))
         return fail(c, PD_ERR_INVALID, "pd_barycenter_apply: need z, gsum, count, k >= 1, 2 <= d <= 256, "
                                        "gamma > 0, lambda > 0");
@@ -784,7 +850,7 @@ extern "C" pd_status pd_kmeans(pd_ctx* c, const uint32_t* hist, const uint32_t* 
                                uint64_t seed, int32_t* assign, double* centroids, double* objective,
                                pd_stream stream) {
     if (!c) return PD_ERR_INVALID;
-    c->err.clear();
+    call_begin(c);
     pd_status st = check_params(c, prm, "pd_kmeans");
     if (st == PD_OK && prm->bary_sharpen) return fail(c, PD_ERR_INVALID, "pd_kmeans: bary_sharpen is not supported");
     if (st != PD_OK) return st;
@@ -794,21 +860,13 @@ extern "C" pd_status pd_kmeans(pd_ctx* c, const uint32_t* hist, const uint32_t* 
         return fail(c, PD_ERR_INVALID, "pd_kmeans: need lambda > 0, rounds >= 0, bary_steps >= 0");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(c, cudaSetDevice(c->device));
-    const int d = prm->d, D = d * d, n1 = D + 1;
+    const int d = prm->d;
     const size_t NK = (size_t)N * k;
-    Arena a{nullptr, 0};
-    auto layout = [&](Arena& ar, double** zmass, double** f, double** g, double** cost, int32_t** pairs,
-                      int32_t** iters, float** err, int32_t** status, int32_t** idx) {
-        *zmass = ar.take<double>(k); *f = ar.take<double>((size_t)N * n1); *g = ar.take<double>((size_t)N * n1);
-        *cost = ar.take<double>(NK); *pairs = ar.take<int32_t>(2 * NK); *iters = ar.take<int32_t>(NK);
-        *err = ar.take<float>(NK); *status = ar.take<int32_t>(NK); *idx = ar.take<int32_t>(k);
-    };
     double *zmass, *f, *g, *cost; int32_t *pairs, *iters, *status, *idx; float* err;
-    layout(a, &zmass, &f, &g, &cost, &pairs, &iters, &err, &status, &idx);
-    st = ensure_buffer(c, &c->ws2, &c->ws2_bytes, a.off, s);
+    st = ensure_buffer(c, &c->ws2, &c->ws2_bytes,
+                       kmeans_layout(nullptr, N, k, d, &zmass, &f, &g, &cost, &pairs, &iters, &err, &status, &idx), s);
     if (st != PD_OK) return st;
-    a = Arena{(char*)c->ws2, 0};
-    layout(a, &zmass, &f, &g, &cost, &pairs, &iters, &err, &status, &idx);
+    kmeans_layout((char*)c->ws2, N, k, d, &zmass, &f, &g, &cost, &pairs, &iters, &err, &status, &idx);
     // seeding: k distinct histograms drawn by splitmix64(seed), draw r mod N, repeats skipped
     std::vector<int32_t> chosen;
     uint64_t stt = seed;
@@ -851,6 +909,64 @@ extern "C" pd_status pd_kmeans(pd_ctx* c, const uint32_t* hist, const uint32_t* 
         }
     }
     CUDA_TRY(c, cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace sizing and caller-supplied workspace.
+
+extern "C" pd_status pd_workspace_query(int op, const pd_sinkhorn_params* prm, int n, int k, size_t* bytes) {
+    if (!bytes || !prm || n < 0 || prm->d < 2 || prm->d > 256) return PD_ERR_INVALID;
+    *bytes = 0;
+    const int d = prm->d, dp = ((d + 63) / 64) * 64;
+    int* counter = nullptr;
+    auto sk = [&](size_t P) { return P == 0 ? (size_t)0 : align256(pd_carve_ws(nullptr, (int)P, d, dp, prm->gamma,
+                                                                                 nullptr, &counter)); };
+    double *f, *g, *cost, *zmass; int32_t *pairs, *iters, *status, *idx; float* err;
+    switch (op) {
+        case PD_OP_SINKHORN:
+        case PD_OP_BOUNDS:
+            *bytes = sk((size_t)n);
+            return PD_OK;
+        case PD_OP_BARYCENTER:
+            if (n < 1) return PD_ERR_INVALID;
+            *bytes = sk((size_t)n) + align256(bary_layout(nullptr, n, d, nullptr));
+            return PD_OK;
+        case PD_OP_BARY_GRAD:
+            if (n < 1) return PD_ERR_INVALID;
+            *bytes = sk((size_t)n) +
+                     align256(grad_layout(nullptr, n, d, true, &f, &g, &cost, &pairs, &iters, &err, &status));
+            return PD_OK;
+        case PD_OP_KMEANS_ASSIGN:
+            if (n < 1 || k < 1 || (size_t)n * k > (size_t)INT32_MAX) return PD_ERR_INVALID;
+            *bytes = sk((size_t)n * k) +
+                     align256(assign_layout(nullptr, (size_t)n * k, true, &cost, &pairs, &iters, &err, &status));
+            return PD_OK;
+        case PD_OP_KMEANS:
+            if (n < 1 || k < 1 || k > n || (size_t)n * k > (size_t)INT32_MAX) return PD_ERR_INVALID;
+            *bytes = sk(std::max((size_t)n * k, (size_t)n)) +
+                     align256(kmeans_layout(nullptr, n, k, d, &zmass, &f, &g, &cost, &pairs, &iters, &err, &status,
+                                            &idx));
+            return PD_OK;
+        default:
+            return PD_ERR_INVALID;
+    }
+}
+
+extern "C" pd_status pd_ctx_set_workspace(pd_ctx* c, void* ws, size_t bytes) {
+    if (!c) return PD_ERR_INVALID;
+    call_begin(c);
+    if (ws && ((uintptr_t)ws & 255u)) return fail(c, PD_ERR_INVALID, "pd_ctx_set_workspace: ws must be 256-byte aligned");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaDeviceSynchronize());   // no call of this context may still use the old workspace
+    if (!c->ext) {
+        if (c->ws) cudaFree(c->ws);
+        if (c->ws2) cudaFree(c->ws2);
+    }
+    c->ws = c->ws2 = nullptr;
+    c->ws_bytes = c->ws2_bytes = 0;
+    c->ext = (char*)ws;
+    c->ext_bytes = ws ? bytes : 0;
     return PD_OK;
 }
 

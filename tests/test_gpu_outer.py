@@ -54,6 +54,71 @@ def test_sharpened_barycenter_matches_oracle(ctx, d, gamma, lam, steps, T):
     assert H <= H0 + 1e-9
 
 
+def test_barycenter_energy_stop_matches_oracle(ctx):
+    """The barycenter experiment's stop |E_t/E_{t-1} - 1| < tol (Sec. 5):
+    the GPU run stops at the same step as the oracle's, with the same energies
+    and measure.  tol is placed halfway (geometrically) between two well
+    separated ratios of a fixed-length oracle run, so the rounding of the two
+    sides cannot move the stop."""
+    d, gamma, lam, T = 16, 1e-2, 2.0, 200
+    b, t, o = inputs.random_diagrams(4, nmin=8, nmax=25, seed=11, log_uniform=False)
+    h, _ = oracle.rasterize(b, t, o, d)
+    steps = 10
+    _, e_all = oracle.barycenter(d, gamma, h, lam, steps, T, 0.0)
+    ratios = np.abs(e_all[1:] / e_all[:-1] - 1.0)
+    order = np.sort(ratios)
+    gaps = order[1:] / np.maximum(order[:-1], 1e-300)
+    q = int(np.argmax(gaps[len(gaps) // 3:])) + len(gaps) // 3    # a wide gap past the first few steps
+    tol = float(np.sqrt(order[q] * order[q + 1]))
+    assert gaps[q] > 1.5
+    z_ref, e_ref = oracle.barycenter(d, gamma, h, lam, steps, T, 0.0, rel_energy_tol=tol)
+    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=T, tol=0.0)
+    z, e = api.pd_barycenter(ctx, hists_to_gpu(h), dev(masses(h).view(np.int32)), p, lam, steps, rel_energy_tol=tol)
+    torch.cuda.synchronize()
+    assert len(e) == len(e_ref) < steps
+    assert np.allclose(e.cpu().numpy(), e_ref, rtol=1e-6, atol=0)
+    assert np.allclose(z.cpu().numpy(), z_ref, rtol=1e-5, atol=1e-9 * z_ref.max())
+
+
+def test_caller_workspace_of_the_queried_size(ctx):
+    """pd_workspace_query gives the bytes a call needs; a context given exactly
+    that much caller-owned memory (pd_ctx_set_workspace) allocates nothing and
+    returns the same results bitwise as a library-allocated context, and 256
+    bytes less is refused with PD_ERR_OOM."""
+    d, gamma = 32, 5e-3
+    b, t, o = inputs.random_diagrams(6, nmin=20, nmax=60, seed=12)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hist, mass = hists_to_gpu(h), dev(masses(h).view(np.int32))
+    p = api.pd_sinkhorn_default_params(gamma, d, max_iter=400, tol=1e-6)
+    ref = api.pd_sinkhorn_batch(ctx, hist[:3], mass[:3], hist[3:], mass[3:], p)
+    zr, er = api.pd_barycenter(ctx, hist, mass, p, 2.0, 3)
+    need_s = api.pd_workspace_query(api.PD_OP_SINKHORN, p, 3)
+    need_b = api.pd_workspace_query(api.PD_OP_BARYCENTER, p, 6)
+    assert need_s > 0 and need_b > need_s
+    c2 = api.Context(0)
+    try:
+        for need, run in ((need_s, lambda: api.pd_sinkhorn_batch(c2, hist[:3], mass[:3], hist[3:], mass[3:], p)),
+                          (need_b, lambda: api.pd_barycenter(c2, hist, mass, p, 2.0, 3))):
+            buf = torch.empty(need, dtype=torch.uint8, device="cuda")
+            api.pd_ctx_set_workspace(c2, buf, need)
+            out = run()
+            torch.cuda.synchronize()
+            if isinstance(out, dict):
+                assert np.array_equal(out["cost"].cpu().numpy(), ref["cost"].cpu().numpy())
+                assert np.array_equal(out["iters"].cpu().numpy(), ref["iters"].cpu().numpy())
+            else:
+                assert np.array_equal(out[0].cpu().numpy(), zr.cpu().numpy())
+                assert np.array_equal(out[1].cpu().numpy(), er.cpu().numpy())
+            api.pd_ctx_set_workspace(c2, buf, need - 256)
+            with pytest.raises(api.PdError) as ex:
+                run()
+            assert ex.value.status == api.PD_ERR_OOM
+            api.pd_ctx_set_workspace(c2, None)
+            del buf
+    finally:
+        c2.close()
+
+
 def test_barycenter_from_given_start_and_zero_steps(ctx):
     d, gamma = 16, 1e-2
     b, t, o = inputs.random_diagrams(3, nmin=10, nmax=10, seed=1)

@@ -362,6 +362,63 @@ def test_kmeans_best_run_recovers_modes():
     assert len(pairs) == 3 and len({p[1] for p in pairs}) == 3
 
 
+def test_kmeans_objective_non_increasing_over_rounds():
+    """Lloyd's alternation: the assignment takes the minimum over centroids and
+    the centroid update (Alg. 2 steps on each cluster) lowers each cluster's
+    energy when the mirror-descent step is small enough, so on well-separated
+    modes the objective sum_n min_c <P, C> does not rise from round to round (a
+    sign error in the update or an argmax in the assignment makes it rise).
+    With lambda = 0.3 the update is in that regime (lambda = 5, the paper's
+    barycenter step, overshoots from centroids seeded on single diagrams and the
+    objective can rise: measured 6.77 -> 9.11 on this data)."""
+    d, gamma = 16, 5e-3
+    b, t, o, lab = inputs.mode_diagrams(12, 3, 40, 60, sigma=0.02, seed=5)
+    hist, _ = oracle.rasterize(b, t, o, d)
+    for seed in (0, 3):
+        _, _, obj = oracle.kmeans(d, gamma, hist, 3, 0.3, 5, 3, 5000, 1e-6, seed)
+        assert np.all(np.diff(obj) <= 1e-9 * obj[:-1]), obj
+        assert obj[-1] < 0.97 * obj[0]
+
+
+def test_kmeans_tie_goes_to_lowest_index_and_empty_cluster_keeps_centroid():
+    """Two identical diagrams and k = 2: seeding takes both, so the two
+    centroids are equal and every assignment is a tie.  The reading of Sec. 5
+    fixes ties to the lowest centroid index, so both diagrams join centroid 0;
+    centroid 1 is then empty and keeps its value (the seeded histogram)
+    exactly, while centroid 0 moves by its Alg. 2 steps."""
+    d, gamma = 12, 1e-2
+    b, t, o = inputs.random_diagrams(1, nmin=7, nmax=7, seed=4)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hists = np.repeat(h, 2, axis=0)
+    assign, cent, obj = oracle.kmeans(d, gamma, hists, 2, 2.0, 1, 2, 5000, 1e-9, 0)
+    assert assign.tolist() == [0, 0]
+    assert np.array_equal(cent[1], h[0].astype(np.float64))
+    assert not np.allclose(cent[0], h[0].astype(np.float64))
+
+
+def test_barycenter_energy_stop_rule():
+    """The barycenter experiment's stop (Sec. 5, Fig. 5): after step t >= 1,
+    stop when |E_t / E_{t-1} - 1| < tol.  From the energies of a fixed-length
+    run, the stopped run must end at the first such t, with the energies and
+    the measure of a fixed run of t + 1 steps; tol = 0 runs every step."""
+    d, gamma, lam = 10, 1e-2, 2.0
+    b, t, o = inputs.random_diagrams(3, nmin=5, nmax=7, seed=8, log_uniform=False)
+    hist, _ = oracle.rasterize(b, t, o, d)
+    T = 8
+    z_all, e_all = oracle.barycenter(d, gamma, hist, lam, T, 20000, 1e-10)
+    assert len(e_all) == T
+    ratios = np.abs(e_all[1:] / e_all[:-1] - 1.0)
+    tol = float(np.sort(ratios)[len(ratios) // 2]) * 1.0001   # stops somewhere inside the run
+    t_stop = 1 + int(np.nonzero(ratios < tol)[0][0])
+    z_s, e_s = oracle.barycenter(d, gamma, hist, lam, T, 20000, 1e-10, rel_energy_tol=tol)
+    assert len(e_s) == t_stop + 1 < T
+    z_ref, e_ref = oracle.barycenter(d, gamma, hist, lam, t_stop + 1, 20000, 1e-10)
+    assert np.array_equal(e_s, e_ref) and np.array_equal(e_s, e_all[:t_stop + 1])
+    assert np.array_equal(z_s, z_ref)
+    z0, e0 = oracle.barycenter(d, gamma, hist, lam, T, 20000, 1e-10, rel_energy_tol=0.0)
+    assert len(e0) == T and np.array_equal(z0, z_all)
+
+
 # --------------------------------------------------------------------------- Prop. 3 rounding upper bound
 @pytest.mark.parametrize("T", [2, 10, 60, None])
 def test_round_bound_plan_is_feasible_and_closes(T):
