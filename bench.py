@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--serve-tol", type=float, default=1e-4)
     ap.add_argument("--serve-nmax", type=int, default=5000, help="largest diagram of the stream (points)")
     ap.add_argument("--serve-inner", type=int, default=64, help="iterations per serving scheduling round")
+    ap.add_argument("--no-compare", action="store_true", help="skip the engine comparison leg")
+    ap.add_argument("--compare-pairs", type=int, default=2048, help="pairs of the engine comparison workload")
+    ap.add_argument("--compare-plain-sample", type=int, default=24,
+                    help="pairs timed with the one-pair-per-launch FP32 engine")
     return ap.parse_args()
 
 
@@ -444,6 +448,9 @@ def run_ours(args):
     serving = None
     if rank == 0 and not args.no_serve:
         serving = serve_leg(args, ctx)
+    compare = None
+    if rank == 0 and not args.no_compare:
+        compare = compare_leg(args, ctx)
     ctx.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -458,12 +465,93 @@ def run_ours(args):
                              "iterations_per_step": int(outs["iters"].cpu().numpy()[status != api.PD_OK].sum()),
                              "value_with_them": value_all_pairs},
                 "max_err": float(errs.max()), "max_err_counted": float(errs[status == api.PD_OK].max()) if
-                (status == api.PD_OK).any() else None, "serving": serving}
+                (status == api.PD_OK).any() else None, "serving": serving, "precision_comparison": compare}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+# --------------------------------------------------------------------------- engine comparison leg
+def compare_leg(args, ctx):
+    """The batched BF16 tensor-core engine (refined by the exact FP32 engine)
+    against the plain FP32 form (one pair per launch) and the batched FP32
+    engines, at equal stated accuracy (every engine stops at relative marginal
+    error 1e-6; costs of a sample checked against the FP64 oracle), on
+    k-means-shaped diagrams: d = 64, gamma = 5e-3, diagrams of 10 modes
+    (30-300 points, sigma 0.03), where the linear domain holds."""
+    import torch
+    import oracle
+    from paper_1805_08331_gb300 import api
+    d, gamma, tol, P = 64, 5e-3, 1e-6, args.compare_pairs
+    b, t, o, _ = inputs.mode_diagrams(2 * P, 10, 30, 300, sigma=0.03, seed=3)
+    db_, dt_, do_ = (torch.from_numpy(x).cuda() for x in (b, t, o))
+    hist, mass = api.pd_rasterize(ctx, db_, dt_, do_, d)
+    pairs = torch.arange(2 * P, dtype=torch.int32, device="cuda").view(P, 2).contiguous()
+    ns = 4
+    href, _ = oracle.rasterize(b[:o[2 * ns]], t[:o[2 * ns]], o[:2 * ns + 1], d)
+    ref = oracle.sinkhorn_pd_batch(d, gamma, href[0::2], href[1::2], 20000, tol)["cost"]
+    cells_per_iter = 2 * (d * d + 1)
+
+    def run(precision, npairs, reps, **kw):
+        prm = api.pd_sinkhorn_default_params(gamma, d, max_iter=20000, tol=tol, precision=precision, **kw)
+        out = None
+        times = []
+        for k in range(reps + 1):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = api.pd_sinkhorn_batch(ctx, hist, mass, hist, mass, prm, pairs=pairs[:npairs])
+            e1.record()
+            torch.cuda.synchronize()
+            if k > 0 or reps == 0:
+                times.append(e0.elapsed_time(e1))
+        ms = float(np.mean(times))
+        it = out["iters"].cpu().numpy()
+        st = out["status"].cpu().numpy()
+        c = out["cost"].cpu().numpy()[:ns]
+        ok = st == api.PD_OK
+        return {"pairs": npairs, "ms": ms, "cell_updates_per_s": float(it[ok].sum()) * cells_per_iter / (ms / 1e3),
+                "iterations": int(it.sum()), "status_counts": {str(int(x)): int((st == x).sum()) for x in np.unique(st)},
+                "max_rel_cost_err_vs_fp64_sample": float(np.max(np.abs(c - ref) / ref))}
+
+    res = {"workload": f"{P} pairs of 10-mode diagrams (30-300 points, sigma 0.03), d={d}, gamma={gamma:g}, "
+                       f"stop at relative marginal error {tol:g}; oracle sample: pairs 0-{ns - 1}",
+           "bf16_tensor_core_refined": run(api.PD_BF16, P, 2, refine_iters=1),
+           "fp32_plain_one_pair_per_launch": run(api.PD_FP32_PLAIN, min(args.compare_plain_sample, P), 0),
+           "fp32_dense_batched": run(api.PD_FP32_DENSE, P, 1),
+           "fp32_log_domain_batched": run(api.PD_FP32, P, 2)}
+    # tensor-core kernel alone: fixed 256 BF16 iterations, no stop, profiled
+    pk, pk_kind = peaks()
+    nfix = 256
+    prm = api.pd_sinkhorn_default_params(gamma, d, max_iter=nfix, tol=0.0, precision=api.PD_BF16)
+    api.pd_sinkhorn_batch(ctx, hist, mass, hist, mass, prm, pairs=pairs)
+    torch.cuda.synchronize()
+    ctx.profile_enable(True)
+    out = api.pd_sinkhorn_batch(ctx, hist, mass, hist, mass, prm, pairs=pairs)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    tc_ms, tc_n = prof.get("tc", (0.0, 0))
+    tc_iters = float(np.minimum(out["iters"].cpu().numpy(), nfix).sum())
+    dpad = 128
+    executed = tc_iters * 8.0 * dpad ** 3
+    algorithmic = tc_iters * 8.0 * d ** 3
+    peak = pk.get("bf16_tflops", 1900.0)
+    res["tensor_core_kernel"] = {
+        "kernel": "sk_iter_bf16_kernel (tcgen05 kind::f16, BF16 operands, FP32 accumulation in TMEM)",
+        "launches": int(tc_n), "ms": tc_ms, "pair_iterations": tc_iters,
+        "executed_tflops": executed / (tc_ms / 1e3) / 1e12 if tc_ms else None,
+        "algorithmic_tflops": algorithmic / (tc_ms / 1e3) / 1e12 if tc_ms else None,
+        "peak_tflops": peak, "peak_source": f"{pk_kind} bf16_tflops (burst)",
+        "executed_frac": executed / (tc_ms / 1e3) / 1e12 / peak if tc_ms else None,
+        "note": f"executed = 8 x {dpad}^3 flop per pair-iteration (four {dpad}x{dpad}x{dpad} MMA GEMMs, the grid "
+                f"zero-padded to {dpad}); algorithmic = 8 x d^3"}
+    bf = res["bf16_tensor_core_refined"]["cell_updates_per_s"]
+    res["bf16_over_fp32_plain"] = bf / res["fp32_plain_one_pair_per_launch"]["cell_updates_per_s"]
+    res["bf16_over_fp32_dense_batched"] = bf / res["fp32_dense_batched"]["cell_updates_per_s"]
+    return res
 
 
 # --------------------------------------------------------------------------- serving leg

@@ -53,8 +53,11 @@ enum {
  *   PD_BF16       absorbed-potential linear-domain separable GEMMs on the tensor cores (tcgen05,
  *                 BF16 operands, FP32 accumulation), then FP32 refinement by the PD_FP32 engine.
  *   PD_FP32_DENSE absorbed-potential linear-domain separable GEMMs on the CUDA cores (FP32),
- *                 one pair per CTA: the plain dense form. */
-enum { PD_FP32 = 0, PD_BF16 = 1, PD_FP32_DENSE = 2 };
+ *                 one pair per CTA, all pairs in each launch: the batched dense form.
+ *   PD_FP32_PLAIN the same FP32 arithmetic as PD_FP32_DENSE with one pair per launch (pairs solved
+ *                 one after the other): the plain FP32 form, kept as the comparator of the
+ *                 batched tensor-core form. */
+enum { PD_FP32 = 0, PD_BF16 = 1, PD_FP32_DENSE = 2, PD_FP32_PLAIN = 3 };
 
 /* Version of this ABI (increments on incompatible change). */
 int pd_abi_version(void);
@@ -90,7 +93,7 @@ typedef struct {
     int d;             /* grid size, 2 <= d <= 256 */
     int max_iter;      /* maximum number of Sinkhorn iterations (each = u-update then v-update), >= 1 */
     double tol;        /* stop after iteration t if err_t / total mass <= tol (0 = run max_iter) */
-    int precision;     /* engine: PD_FP32, PD_BF16 or PD_FP32_DENSE (see above) */
+    int precision;     /* engine: PD_FP32, PD_BF16, PD_FP32_DENSE or PD_FP32_PLAIN (see above) */
     int refine_iters;  /* PD_BF16 only: FP32 iterations run after the BF16 phase stops (0 = none) */
     double absorb_tau; /* re-absorb when |log(u~/a)| or |log(v~/b)| exceeds this (<= 0: default 20) */
     int absorb_every;  /* also re-absorb every this many iterations (<= 0: default 64) */
@@ -402,6 +405,7 @@ enum {
     PD_K_ABSORB = 3,   /* absorption / re-centring */
     PD_K_ITER = 4,     /* linear-domain Sinkhorn iterations (the GEMM kernel) */
     PD_K_FINALIZE = 5, /* transport cost (Prop. 2), marginals, potentials */
+    PD_K_TC = 6,       /* tensor-core (tcgen05) iterations of the PD_BF16 engine */
     PD_K_COUNT = 16
 };
 

@@ -16,7 +16,7 @@ from . import build as _build
 
 PD_OK, PD_ERR_INVALID, PD_ERR_OOM, PD_ERR_CUDA, PD_ERR_TIMEOUT, PD_ERR_QUEUE_FULL = 0, 1, 2, 3, 4, 5
 PD_NOT_CONVERGED, PD_PENDING, PD_ERR_RANGE = 6, 7, 8
-PD_FP32, PD_BF16, PD_FP32_DENSE = 0, 1, 2
+PD_FP32, PD_BF16, PD_FP32_DENSE, PD_FP32_PLAIN = 0, 1, 2, 3
 STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID", 2: "PD_ERR_OOM", 3: "PD_ERR_CUDA", 4: "PD_ERR_TIMEOUT",
                 5: "PD_ERR_QUEUE_FULL", 6: "PD_NOT_CONVERGED", 7: "PD_PENDING", 8: "PD_ERR_RANGE"}
 
@@ -30,8 +30,9 @@ EXPORTED = ["pd_abi_version", "pd_ctx_create", "pd_ctx_destroy", "pd_last_error"
 PD_OP_SINKHORN, PD_OP_BOUNDS, PD_OP_BARYCENTER, PD_OP_BARY_GRAD, PD_OP_KMEANS_ASSIGN, PD_OP_KMEANS = 0, 1, 2, 3, 4, 5
 PD_Q_DISTANCE, PD_Q_NEAREST = 0, 1
 SERVE_D = (32, 64, 128, 256)
-PD_K_RASTER, PD_K_SETUP, PD_K_LOGSTEP, PD_K_ABSORB, PD_K_ITER, PD_K_FINALIZE, PD_K_COUNT = 0, 1, 2, 3, 4, 5, 16
-KERNEL_NAMES = {0: "raster", 1: "setup", 2: "logstep", 3: "absorb", 4: "iter", 5: "finalize"}
+PD_K_RASTER, PD_K_SETUP, PD_K_LOGSTEP, PD_K_ABSORB, PD_K_ITER, PD_K_FINALIZE, PD_K_TC, PD_K_COUNT = (
+    0, 1, 2, 3, 4, 5, 6, 16)
+KERNEL_NAMES = {0: "raster", 1: "setup", 2: "logstep", 3: "absorb", 4: "iter", 5: "finalize", 6: "tc"}
 
 
 class PdError(RuntimeError):

@@ -240,6 +240,30 @@ cudaError_t pd_upload_cost_tables(const SkWS& w, double gamma, cudaStream_t s) {
     return cudaMemcpyAsync(w.ctab, tab.data(), sizeof(float) * 5 * dp, cudaMemcpyHostToDevice, s);
 }
 
+// Host-side view of pair p of a workspace as a one-pair workspace (the same
+// per-pair offsets as the device-side pair_ptrs); used by the one-pair-per-
+// launch engine.  Inputs and the pair list are not offset: only kernels that
+// read per-pair state may be given a view.
+static SkWS ws_view(const SkWS& w, int p) {
+    SkWS v = w;
+    const size_t M = (size_t)w.dp * w.dp, V = (size_t)w.dp, N = (size_t)w.n;
+    float** fm[] = {&v.K1u, &v.K2u, &v.K1v, &v.K2v, &v.ut, &v.vt, &v.Wt, &v.Rt, &v.KDu, &v.KDv, &v.am, &v.bm};
+    for (auto f : fm) *f += p * M;
+    float** fv[] = {&v.rs_u, &v.cf_u, &v.rs_v, &v.cf_v};
+    for (auto f : fv) *f += p * V;
+    double** dv[] = {&v.ap, &v.bp, &v.al, &v.be, &v.Au, &v.Bu, &v.Av, &v.Bv};
+    for (auto f : dv) *f += p * V;
+    v.phi += p * N; v.psi += p * N; v.sc += (size_t)p * SC_N;
+    v.sa += p * M; v.sb += p * M; v.ic += (size_t)p * IC_N;
+    v.L64 += 2 * p * M; v.la += p * M; v.lb += p * M;
+    v.rpa += p * (V + 1); v.rpb += p * (V + 1); v.cpa += p * (V + 1); v.cpb += p * (V + 1);
+    v.cia += p * M; v.cib += p * M;
+    v.P = 1;
+    v.order = nullptr;
+    v.histA = v.histB = nullptr; v.massA = v.massB = nullptr; v.wA = v.wB = nullptr; v.pairs = nullptr;
+    return v;
+}
+
 static SkRun make_run(const pd_sinkhorn_params* prm) {
     SkRun r{};
     r.max_iter = prm->max_iter;
@@ -463,13 +487,16 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     if (!(prm->gamma > 0) || !std::isfinite(prm->gamma)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: gamma must be > 0");
     if (prm->max_iter < 1) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: max_iter must be >= 1");
     if (!(prm->tol >= 0)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: tol must be >= 0");
-    if (prm->precision != PD_FP32 && prm->precision != PD_FP32_DENSE && prm->precision != PD_BF16)
+    if (prm->precision != PD_FP32 && prm->precision != PD_FP32_DENSE && prm->precision != PD_BF16 &&
+        prm->precision != PD_FP32_PLAIN)
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: unknown precision %d", prm->precision);
     if (prm->precision == PD_BF16 && d > 128)
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: PD_BF16 supports d <= 128");
     if (!(prm->p >= 1.0 && prm->p <= 8.0)) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: p must be in [1, 8]");
     if (prm->p != 2.0 && prm->precision != PD_FP32)
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: p != 2 needs the PD_FP32 engine");
+    if (prm->eps_stages > 0 && prm->precision != PD_FP32)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: eps_stages needs the PD_FP32 engine");
     if (P < 0) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: P < 0");
     if (P == 0) return PD_OK;
     if (!cost || !histA || !histB || !massA || !massB) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: NULL input/cost");
@@ -506,7 +533,7 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         for (int round = 0; round < max_rounds_b; ++round) {
             { ProfScope ps(c, PD_K_ABSORB, s); CUDA_TRY(c, sk_launch_absorb(w, rb, s)); }
             CUDA_TRY(c, cudaMemsetAsync(counter, 0, sizeof(int), s));
-            { ProfScope ps(c, PD_K_ITER, s);
+            { ProfScope ps(c, PD_K_TC, s);
               CUDA_TRY(c, sk_launch_iter_bf16(w, rb, rb.absorb_every, counter, c->dflag, s)); }
             CUDA_TRY(c, cudaMemcpyAsync(c->hflag, counter, sizeof(int), cudaMemcpyDeviceToHost, s));
             CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -522,6 +549,33 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         if (refine) rr.max_iter = prm->max_iter;   // total count: BF16 phase + refinement, capped at max_iter
         pd_status st = lse_iterate(c, w, rr, cost, row_marg, col_marg, f, g, iters, err, status, counter, s);
         if (st != PD_OK) return st;
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        return PD_OK;
+    }
+    if (prm->precision == PD_FP32_PLAIN) {
+        // the plain form: every launch of the solve carries one pair (the
+        // support set-up above is one launch for the batch), pairs one after
+        // the other on the stream, the host reading each pair's state between
+        // its iteration launches
+        const size_t n = (size_t)w.n;
+        for (int p = 0; p < P; ++p) {
+            SkWS v = ws_view(w, p);
+            { ProfScope ps(c, PD_K_LOGSTEP, s); CUDA_TRY(c, sk_launch_logstep(v, r, s)); }
+            for (int round = 0; round < prm->max_iter + 8; ++round) {
+                { ProfScope ps(c, PD_K_ABSORB, s); CUDA_TRY(c, sk_launch_absorb(v, r, s)); }
+                CUDA_TRY(c, cudaMemsetAsync(counter, 0, sizeof(int), s));
+                { ProfScope ps(c, PD_K_ITER, s); CUDA_TRY(c, sk_launch_iter_fp32(v, r, r.absorb_every, counter, s)); }
+                CUDA_TRY(c, cudaMemcpyAsync(c->hflag, counter, sizeof(int), cudaMemcpyDeviceToHost, s));
+                CUDA_TRY(c, cudaStreamSynchronize(s));
+                if (c->hflag[0] == 0) break;
+            }
+            { ProfScope ps(c, PD_K_ABSORB, s); CUDA_TRY(c, sk_launch_absorb(v, r, s)); }
+            { ProfScope ps(c, PD_K_FINALIZE, s);
+              CUDA_TRY(c, sk_launch_finalize(v, cost + p, row_marg ? row_marg + p * n : nullptr,
+                                             col_marg ? col_marg + p * n : nullptr, f ? f + p * n : nullptr,
+                                             g ? g + p * n : nullptr, iters ? iters + p : nullptr,
+                                             err ? err + p : nullptr, status ? status + p : nullptr, s)); }
+        }
         CUDA_TRY(c, cudaStreamSynchronize(s));
         return PD_OK;
     }

@@ -54,7 +54,7 @@ def test_raster_empty_diagrams_and_invalid(ctx):
 
 
 # --------------------------------------------------------------------------- Sinkhorn parity
-@pytest.mark.parametrize("engine", [api.PD_FP32, api.PD_FP32_DENSE])
+@pytest.mark.parametrize("engine", [api.PD_FP32, api.PD_FP32_DENSE, api.PD_FP32_PLAIN])
 def test_config1_fp32_300_iterations(ctx, engine):
     """One pair of 20-point diagrams, d=32, gamma=1e-2, exactly 300 iterations."""
     d, gamma = 32, 1e-2
@@ -281,3 +281,22 @@ def test_bf16_unrefined_within_bf16_bar(ctx):
     g = _solve(ctx, h[0::2], h[1::2], d, gamma, 20000, 1e-6, precision=api.PD_BF16, refine_iters=0)
     rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
     assert rel.max() <= 1e-3, rel
+
+
+def test_plain_one_pair_per_launch_equals_batched_dense(ctx):
+    """PD_FP32_PLAIN runs the dense FP32 arithmetic with one pair per launch;
+    a pair's CTA does the same work whatever else is in the launch, so its
+    results are bitwise those of the batched PD_FP32_DENSE engine, and within
+    the FP32 bar of the oracle (k-means-shaped pairs, d = 64, gamma = 5e-3)."""
+    d, gamma = 64, 5e-3
+    b, t, o, _ = inputs.mode_diagrams(8, 10, 30, 300, sigma=0.03, seed=3)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    dense = _solve(ctx, hA, hB, d, gamma, 20000, 1e-6, precision=api.PD_FP32_DENSE)
+    plain = _solve(ctx, hA, hB, d, gamma, 20000, 1e-6, precision=api.PD_FP32_PLAIN)
+    for k in ("cost", "iters", "status", "err"):
+        assert np.array_equal(plain[k], dense[k]), k
+    ref = oracle.sinkhorn_pd_batch(d, gamma, hA, hB, 20000, 1e-6)
+    ok = plain["status"] == api.PD_OK
+    assert ok.all()
+    assert np.all(np.abs(plain["cost"] - ref["cost"]) <= 2e-6 * ref["cost"])
