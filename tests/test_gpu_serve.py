@@ -175,3 +175,47 @@ def test_serve_injected_failure_fails_queries_not_process(ctx):
     ba, da = _diagram(9, 20)
     c, st = _batch_cost(ctx, 32, ba, da, ba[::-1].copy(), da[::-1].copy())
     assert st == api.PD_OK and np.isfinite(c)
+
+
+def test_served_results_match_the_oracle(ctx):
+    """Served results against the FP64 oracle, not only against the batch API:
+    distance queries of mixed grid sizes (cold starts, so the served solve and
+    the oracle stop at the same rule from the same start) and nearest-centroid
+    queries against real-valued resident centroids (the mean histograms the
+    bench loads); every served cost within REL of the oracle's cost of the same
+    pair at the same tolerance, and the served centroid at the oracle's
+    minimum within REL."""
+    import torch
+    import oracle
+    qs = _mixed_queries(8, seed=21)
+    qs = [q for q in qs if q[0] <= 128][:6]
+    with api.Server(ctx, gamma=GAMMA, tol=TOL, max_iter=5000, slots=[8, 8, 8, -1], warm_start=0) as sv:
+        res = [sv.wait(sv.submit_distance(*q), 120000) for q in qs]
+    for (d, ba, da, bb, dbb), r in zip(qs, res):
+        assert r["status"] == api.PD_OK, r
+        ha, _ = oracle.rasterize(ba, da, np.array([0, len(ba)]), d)
+        hb, _ = oracle.rasterize(bb, dbb, np.array([0, len(bb)]), d)
+        ref = oracle.sinkhorn_pd(d, GAMMA, ha[0], hb[0], 5000, TOL)
+        assert abs(r["cost"] - ref["cost"]) <= REL * ref["cost"], (d, r["cost"], ref["cost"])
+    # nearest centroid among k mean histograms of mode diagrams
+    d, k = 32, 4
+    b, t, o, _ = inputs.mode_diagrams(4 * k, n_modes=k, nmin=30, nmax=80, sigma=0.03, seed=9,
+                                      labels=np.repeat(np.arange(k), 4))
+    hz, _ = oracle.rasterize(b, t, o, d)
+    Z = hz.reshape(k, 4, d * d).astype(np.float64).mean(1)
+    queries = [_diagram(900 + i, 25 + 11 * i) for i in range(4)]
+    with api.Server(ctx, gamma=GAMMA, tol=TOL, max_iter=5000, slots=[16, -1, -1, -1], warm_start=0) as sv:
+        sv.load_centroids(d, torch.from_numpy(Z).cuda())
+        res = [sv.wait(sv.submit_nearest(d, qb, qt), 120000) for qb, qt in queries]
+    for (qb, qt), r in zip(queries, res):
+        assert r["status"] == api.PD_OK, r
+        hq, _ = oracle.rasterize(qb, qt, np.array([0, len(qb)]), d)
+        hq = hq[0].ravel().astype(np.float64)
+        costs = []
+        for c in range(k):
+            a = np.concatenate([hq, [Z[c].sum()]])
+            bb = np.concatenate([Z[c], [hq.sum()]])
+            costs.append(oracle.sinkhorn_w(d, GAMMA, a, bb, 5000, TOL)["cost"])
+        costs = np.array(costs)
+        assert abs(r["cost"] - costs[r["centroid"]]) <= REL * costs[r["centroid"]], (r, costs)
+        assert costs[r["centroid"]] <= costs.min() * (1 + 2 * REL), (r, costs)

@@ -88,6 +88,51 @@ def test_small_gamma_fixed_iterations(ctx, d, gamma):
     assert rel.max() <= 1e-6, rel
 
 
+def test_marginals_and_potentials_elementwise_at_d128_gamma1e3(ctx):
+    """The benchmark's grid and gamma, fixed 400 iterations on both sides:
+    row and column marginals of the plan and the potentials f, g on the
+    supports (and Delta) agree element by element with the FP64 oracle."""
+    d, gamma, T = 128, 1e-3, 400
+    b, t, o = inputs.random_diagrams(6, nmin=50, nmax=500, seed=5)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    g = _solve(ctx, hA, hB, d, gamma, T, 0.0, want_marginals=True, want_potentials=True)
+    for p in range(3):
+        r = oracle.sinkhorn_pd(d, gamma, hA[p], hB[p], T, 0.0)
+        a, bb = oracle.augment(hA[p], hB[p])
+        ma, mb = a > 0, bb > 0
+        assert np.allclose(g["row_marg"][p], r["rmarg"], rtol=5e-6, atol=1e-6)
+        assert np.allclose(g["col_marg"][p], r["cmarg"], rtol=5e-6, atol=1e-6)
+        assert np.allclose(g["f"][p][ma], r["f"][ma], rtol=0, atol=gamma * 2e-5)
+        assert np.allclose(g["g"][p][mb], r["g"][mb], rtol=0, atol=gamma * 2e-5)
+        assert abs(g["cost"][p] - r["cost"]) <= 1e-6 * r["cost"]
+
+
+@pytest.mark.parametrize("tier", [None, "gm", "fp64"])
+def test_d256_matches_oracle_on_every_tier(ctx, tier, monkeypatch):
+    """d = 256 (the largest grid) on small diagrams, so the FP64 oracle stays
+    fast: the on-chip kernel, its global-memory variant and the FP64 kernel
+    each match the oracle after 300 iterations (cost 1e-6 relative, marginals
+    and potentials element by element)."""
+    if tier:
+        monkeypatch.setenv("PD_LSE2_TIER", tier)
+    d, gamma, T = 256, 5e-3, 300
+    b, t, o = inputs.random_diagrams(4, nmin=30, nmax=120, seed=256)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    g = _solve(ctx, hA, hB, d, gamma, T, 0.0, want_marginals=True, want_potentials=True)
+    assert np.all(g["iters"] == T)
+    for p in range(2):
+        r = oracle.sinkhorn_pd(d, gamma, hA[p], hB[p], T, 0.0)
+        a, bb = oracle.augment(hA[p], hB[p])
+        ma, mb = a > 0, bb > 0
+        assert abs(g["cost"][p] - r["cost"]) <= 1e-6 * r["cost"]
+        assert np.allclose(g["row_marg"][p], r["rmarg"], rtol=5e-6, atol=1e-6)
+        assert np.allclose(g["col_marg"][p], r["cmarg"], rtol=5e-6, atol=1e-6)
+        assert np.allclose(g["f"][p][ma], r["f"][ma], rtol=0, atol=gamma * 2e-5)
+        assert np.allclose(g["g"][p][mb], r["g"][mb], rtol=0, atol=gamma * 2e-5)
+
+
 def test_cta_width_and_widening_leave_results_bitwise_equal(ctx, monkeypatch):
     """The base-2 kernel sums in the same order at 256, 512 and 1024 threads
     per pair (stage-1 and stage-2 sums are per element or per 4-lane group,
