@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--serve-nmax", type=int, default=5000, help="largest diagram of the stream (points)")
     ap.add_argument("--serve-inner", type=int, default=64, help="iterations per serving scheduling round")
     ap.add_argument("--no-compare", action="store_true", help="skip the engine comparison leg")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuning pass before the warm-up")
+    ap.add_argument("--cta-threads", type=int, default=0, help="fix the iteration kernel's CTA width (0: automatic)")
     ap.add_argument("--compare-pairs", type=int, default=2048, help="pairs of the engine comparison workload")
     ap.add_argument("--compare-plain-sample", type=int, default=24,
                     help="pairs timed with the one-pair-per-launch FP32 engine")
@@ -316,7 +318,7 @@ def run_ours(args):
     b, t, o = workload(args, rank)
     d, P = args.d, args.pairs
     params = api.pd_sinkhorn_default_params(args.gamma, d, max_iter=args.max_iter, tol=args.tol,
-                                            precision=precision)
+                                            precision=precision, cta_threads=args.cta_threads)
     db, dt_, do = torch.from_numpy(b).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(o).cuda()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -327,6 +329,14 @@ def run_ours(args):
         hist, mass = api.pd_rasterize(ctx, db, dt_, do, d)
         return api.pd_sinkhorn_batch(ctx, hist, mass, hist, mass, params, pairs=pairs)
 
+    tuning = None
+    if precision == api.PD_FP32 and not args.no_tune and args.cta_threads == 0:
+        # autotuner: one trial launch per CTA width on this batch; the choice
+        # goes into ctx's table and the timed steps use it
+        hist_t, mass_t = api.pd_rasterize(ctx, db, dt_, do, d)
+        th, trial = api.pd_sinkhorn_tune(ctx, hist_t, mass_t, hist_t, mass_t, params, pairs=pairs, trial_iters=64)
+        tuning = {"chosen_cta_threads": th, "trial_ms": {str(k): v for k, v in trial.items()},
+                  "trial": "one launch per width, all pairs cold-started, 64 iterations each"}
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
@@ -451,6 +461,24 @@ def run_ours(args):
     compare = None
     if rank == 0 and not args.no_compare:
         compare = compare_leg(args, ctx)
+    if tuning is not None and rank == 0:
+        # the same step on a context without a tuning table (built-in rule)
+        c0 = api.Context(local)
+        hist0, mass0 = api.pd_rasterize(c0, db, dt_, do, d)
+        api.pd_sinkhorn_batch(c0, hist0, mass0, hist0, mass0, params, pairs=pairs)
+        tms = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hist0, mass0 = api.pd_rasterize(c0, db, dt_, do, d)
+            api.pd_sinkhorn_batch(c0, hist0, mass0, hist0, mass0, params, pairs=pairs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        c0.close()
+        tuning["untuned_ms_per_step"] = float(np.mean(tms))
+        tuning["tuned_ms_per_step"] = my_ms / args.steps
     ctx.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -465,7 +493,8 @@ def run_ours(args):
                              "iterations_per_step": int(outs["iters"].cpu().numpy()[status != api.PD_OK].sum()),
                              "value_with_them": value_all_pairs},
                 "max_err": float(errs.max()), "max_err_counted": float(errs[status == api.PD_OK].max()) if
-                (status == api.PD_OK).any() else None, "serving": serving, "precision_comparison": compare}
+                (status == api.PD_OK).any() else None, "tuning": tuning, "serving": serving,
+                "precision_comparison": compare}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -112,6 +112,18 @@ typedef struct {
                           the entropy of z/|z| exceeds the largest entropy of the normalised input
                           histograms, z <- |z| w^beta / sum w^beta (w = z/|z|), beta >= 1 chosen to meet
                           it.  0 (default) = off */
+    int cta_threads;   /* PD_FP32 iteration kernel: threads of the CTA that runs one pair, 128, 256, 512 or
+                          1024; 0 (default) = automatic: the context's tuning table (pd_sinkhorn_tune) when it
+                          has an entry for the batch's profile, else the built-in rule (256 while several pairs
+                          share an SM, wider CTAs for the last pairs of a launch).  A fixed width turns the
+                          hand-over of the last pairs to wider CTAs off.  Results do not depend on it: every
+                          sum of the kernel has a fixed order whatever the width */
+    int kernel_tier;   /* PD_FP32: 0 (default) = automatic (on-chip kernel; its global-memory variant for
+                          supports beyond shared memory; the FP64 kernel beyond that or for potentials outside
+                          the exact range); 1 = every pair in the global-memory variant; 2 = every pair in the
+                          FP64 kernel (for checking the tiers against each other) */
+    int max_inner;     /* PD_FP32: iterations per launch at most; 0 (default) = every pair runs to its stop
+                          inside one launch */
 } pd_sinkhorn_params;
 
 /* Fill *p with defaults for (gamma, d): max_iter 20000, tol 1e-6, PD_FP32,
@@ -156,6 +168,37 @@ pd_status pd_sinkhorn_batch(pd_ctx* ctx, const uint32_t* histA, const uint32_t* 
 
 
 /*
+ * pd_sinkhorn_batch_groups -- pd_sinkhorn_batch over pairs of several grid
+ * sizes at once: group g holds P pairs of d x d histograms (its own inputs and
+ * outputs, laid out as in pd_sinkhorn_batch at that d), and the PD_FP32
+ * iterations of every pair of every group run in one persistent launch (each
+ * pair in its own CTA with its own grid size; CTAs handed out largest support
+ * first over all groups).  Each pair's results are those pd_sinkhorn_batch
+ * gives for it (bitwise: a pair's CTA does the same arithmetic whatever else is
+ * in the launch).  A library feature for mixed workloads (e.g. serving several
+ * grid sizes); the paper batches one grid size.
+ *   ngroups   : 1..127; each group's P < 2^24
+ *   params    : host pointer; params->d is ignored (each group has its own d);
+ *               precision must be PD_FP32 and eps_stages 0
+ * Synchronises `stream`.  Errors: as pd_sinkhorn_batch.
+ */
+typedef struct {
+    int d;                                    /* grid size of the group, 2..256 */
+    int P;                                    /* number of pairs (>= 0) */
+    const uint32_t *histA, *massA, *histB, *massB;   /* [N][d][d], [N] (device) */
+    const int32_t* pairs;                     /* [P][2] or NULL (pair p = (p, p)) (device) */
+    const double* g_init;                     /* [P][d*d+1] or NULL (device) */
+    double* cost;                             /* [P] (device, required) */
+    float *row_marg, *col_marg;               /* [P][d*d+1] or NULL (device) */
+    double *f, *g;                            /* [P][d*d+1] or NULL (device) */
+    int32_t* iters;                           /* [P] or NULL (device) */
+    float* err;                               /* [P] or NULL (device) */
+    int32_t* status;                          /* [P] or NULL (device) */
+} pd_sinkhorn_group;
+pd_status pd_sinkhorn_batch_groups(pd_ctx* ctx, int ngroups, const pd_sinkhorn_group* groups_host,
+                                   const pd_sinkhorn_params* params, pd_stream stream);
+
+/*
  * pd_sinkhorn_bounds -- Sec. 3 "Upper and Lower Bounds": the PD_FP32 solve of
  * pd_sinkhorn_batch (same inputs, parameters and cost / iters / err / status
  * outputs), then for each pair, from its final iterate, the bounds
@@ -179,6 +222,36 @@ pd_status pd_sinkhorn_bounds(pd_ctx* ctx, const uint32_t* histA, const uint32_t*
                              const uint32_t* massB, const int32_t* pairs, int P, const pd_sinkhorn_params* params,
                              const double* g_init, double* cost, double* lower, double* upper, int32_t* iters,
                              float* err, int32_t* status, pd_stream stream);
+
+/*
+ * pd_sinkhorn_tune -- autotuner of the PD_FP32 iteration kernel for a batch
+ * profile.  Library feature (the paper has no counterpart).  It runs the
+ * batch's pairs (same arguments as pd_sinkhorn_batch; params->precision must
+ * be PD_FP32) cold-started for exactly trial_iters iterations, once per
+ * candidate width of the CTA that runs one pair (128 threads when d <= 128,
+ * 256, 512; one launch each, timed with CUDA events), and records the fastest
+ * in the context's tuning table under the key (d, support bucket), the
+ * bucket being floor(2 log2(mean support cells per side + 1)).  From then on a
+ * pd_sinkhorn_batch (or bounds / barycenter / k-means solve) on this context
+ * whose batch falls in that key starts with the tuned width (cta_threads = 0),
+ * still handing its last pairs to wider CTAs.  Results never depend on the
+ * width (fixed-order sums), so tuning changes speed only.
+ *   trial_iters   : iterations of each trial (>= 1)
+ *   threads_host  : int (host) or NULL: the chosen width
+ *   trial_ms_host : double[4] (host) or NULL: kernel time of the trials at
+ *                   128, 256, 512, 1024 threads (NaN where not tried)
+ * Synchronises `stream`.  Errors: PD_ERR_INVALID (bad arguments, or gamma
+ * below the base-2 kernel's range), PD_ERR_OOM, PD_ERR_CUDA.
+ */
+pd_status pd_sinkhorn_tune(pd_ctx* ctx, const uint32_t* histA, const uint32_t* massA, const uint32_t* histB,
+                           const uint32_t* massB, const int32_t* pairs, int P, const pd_sinkhorn_params* params,
+                           int trial_iters, int* threads_host, double* trial_ms_host, pd_stream stream);
+/* Write the context's tuning table to a text file (one "d bucket threads" line
+ * per entry) / replace it by the table of such a file.  PD_ERR_INVALID if the
+ * file cannot be written / read or holds a bad entry (the table is then
+ * unchanged). */
+pd_status pd_tune_save(pd_ctx* ctx, const char* path_host);
+pd_status pd_tune_load(pd_ctx* ctx, const char* path_host);
 
 /*
  * pd_workspace_query -- device workspace bytes a context holds for one call of

@@ -26,7 +26,8 @@ EXPORTED = ["pd_abi_version", "pd_ctx_create", "pd_ctx_destroy", "pd_last_error"
             "pd_sinkhorn_batch_noalloc", "pd_barycenter", "pd_kmeans", "pd_serve_default_config",
             "pd_serve_create", "pd_serve_load_centroids", "pd_serve_submit", "pd_serve_poll", "pd_serve_wait",
             "pd_serve_inject_failure", "pd_serve_destroy", "pd_sinkhorn_bounds", "pd_barycenter_grad",
-            "pd_barycenter_apply", "pd_kmeans_assign", "pd_workspace_query", "pd_ctx_set_workspace"]
+            "pd_barycenter_apply", "pd_kmeans_assign", "pd_workspace_query", "pd_ctx_set_workspace",
+            "pd_sinkhorn_tune", "pd_tune_save", "pd_tune_load", "pd_sinkhorn_batch_groups"]
 PD_OP_SINKHORN, PD_OP_BOUNDS, PD_OP_BARYCENTER, PD_OP_BARY_GRAD, PD_OP_KMEANS_ASSIGN, PD_OP_KMEANS = 0, 1, 2, 3, 4, 5
 PD_Q_DISTANCE, PD_Q_NEAREST = 0, 1
 SERVE_D = (32, 64, 128, 256)
@@ -46,7 +47,17 @@ class SinkhornParams(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("d", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int), ("refine_iters", ctypes.c_int),
                 ("absorb_tau", ctypes.c_double), ("absorb_every", ctypes.c_int), ("rel_log_thresh", ctypes.c_double),
-                ("eps_stages", ctypes.c_int), ("p", ctypes.c_double), ("bary_sharpen", ctypes.c_int)]
+                ("eps_stages", ctypes.c_int), ("p", ctypes.c_double), ("bary_sharpen", ctypes.c_int),
+                ("cta_threads", ctypes.c_int), ("kernel_tier", ctypes.c_int), ("max_inner", ctypes.c_int)]
+
+
+class SinkhornGroup(ctypes.Structure):
+    """Mirror of pd_sinkhorn_group."""
+    _fields_ = [("d", ctypes.c_int), ("P", ctypes.c_int), ("histA", ctypes.c_void_p), ("massA", ctypes.c_void_p),
+                ("histB", ctypes.c_void_p), ("massB", ctypes.c_void_p), ("pairs", ctypes.c_void_p),
+                ("g_init", ctypes.c_void_p), ("cost", ctypes.c_void_p), ("row_marg", ctypes.c_void_p),
+                ("col_marg", ctypes.c_void_p), ("f", ctypes.c_void_p), ("g", ctypes.c_void_p),
+                ("iters", ctypes.c_void_p), ("err", ctypes.c_void_p), ("status", ctypes.c_void_p)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -111,6 +122,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.pd_workspace_query.argtypes = [ctypes.c_int, ctypes.POINTER(SinkhornParams), ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_size_t)]
         lib.pd_ctx_set_workspace.argtypes = [_vp, _vp, ctypes.c_size_t]
+        lib.pd_sinkhorn_tune.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(SinkhornParams),
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                         _vp]
+        lib.pd_tune_save.argtypes = [_vp, ctypes.c_char_p]
+        lib.pd_sinkhorn_batch_groups.argtypes = [_vp, ctypes.c_int, _vp, ctypes.POINTER(SinkhornParams), _vp]
+        lib.pd_tune_load.argtypes = [_vp, ctypes.c_char_p]
         lib.pd_kmeans.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SinkhornParams),
                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _vp, _vp, _vp, _vp]
         lib.pd_barycenter_grad.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SinkhornParams),
@@ -236,6 +253,40 @@ def pd_sinkhorn_batch(ctx: Context, histA, massA, histB, massB, params: Sinkhorn
     return o
 
 
+def pd_sinkhorn_batch_groups(ctx: Context, groups, params: SinkhornParams, want_marginals=False,
+                             want_potentials=False, stream=None):
+    """Pairs of several grid sizes in one persistent launch.  groups: list of
+    dicts with d, histA, massA, histB, massB and optional pairs, g_init (CUDA
+    tensors as for pd_sinkhorn_batch).  Returns one output dict per group."""
+    import torch
+    arr = (SinkhornGroup * len(groups))()
+    outs = []
+    for k, gd in enumerate(groups):
+        d, hA = int(gd["d"]), gd["histA"]
+        pairs = gd.get("pairs")
+        P = pairs.shape[0] if pairs is not None else hA.shape[0]
+        n = d * d + 1
+        dev = hA.device
+        o = {"cost": torch.empty(P, dtype=torch.float64, device=dev),
+             "iters": torch.empty(P, dtype=torch.int32, device=dev),
+             "err": torch.empty(P, dtype=torch.float32, device=dev),
+             "status": torch.empty(P, dtype=torch.int32, device=dev)}
+        if want_marginals:
+            o["row_marg"] = torch.empty((P, n), dtype=torch.float32, device=dev)
+            o["col_marg"] = torch.empty((P, n), dtype=torch.float32, device=dev)
+        if want_potentials:
+            o["f"] = torch.empty((P, n), dtype=torch.float64, device=dev)
+            o["g"] = torch.empty((P, n), dtype=torch.float64, device=dev)
+        val = lambda t: None if t is None else t.data_ptr()   # noqa: E731
+        arr[k] = SinkhornGroup(d, int(P), val(hA), val(gd["massA"]), val(gd["histB"]), val(gd["massB"]), val(pairs),
+                               val(gd.get("g_init")), val(o["cost"]), val(o.get("row_marg")), val(o.get("col_marg")),
+                               val(o.get("f")), val(o.get("g")), val(o["iters"]), val(o["err"]), val(o["status"]))
+        outs.append(o)
+    ctx.check(ctx.lib.pd_sinkhorn_batch_groups(ctx.handle, len(groups), ctypes.cast(arr, _vp), ctypes.byref(params),
+                                               _stream(stream)))
+    return outs
+
+
 def pd_sinkhorn_bounds(ctx: Context, histA, massA, histB, massB, params: SinkhornParams, pairs=None,
                        g_init=None, stream=None):
     """pd_sinkhorn_bounds (Sec. 3 bounds): dict with cost, lower (m_t), upper
@@ -271,6 +322,28 @@ def pd_barycenter(ctx: Context, hist, mass, params: SinkhornParams, lam: float, 
                                     float(lam), int(outer_iters), float(rel_energy_tol), _ptr(z_init), _ptr(z),
                                     _ptr(e), ctypes.byref(steps), _stream(stream)))
     return z, e[:steps.value]
+
+
+def pd_sinkhorn_tune(ctx: Context, histA, massA, histB, massB, params: SinkhornParams, pairs=None,
+                     trial_iters: int = 64, stream=None):
+    """Autotune the iteration kernel's CTA width on this batch (see
+    include/pd_ot.h); the choice goes into ctx's tuning table.  Returns
+    (threads, {width: trial ms})."""
+    P = pairs.shape[0] if pairs is not None else histA.shape[0]
+    th = ctypes.c_int(0)
+    ms = (ctypes.c_double * 4)()
+    ctx.check(ctx.lib.pd_sinkhorn_tune(ctx.handle, _ptr(histA), _ptr(massA), _ptr(histB), _ptr(massB), _ptr(pairs),
+                                       int(P), ctypes.byref(params), int(trial_iters), ctypes.byref(th), ms,
+                                       _stream(stream)))
+    return th.value, {w: ms[k] for k, w in enumerate((128, 256, 512, 1024)) if ms[k] == ms[k]}
+
+
+def pd_tune_save(ctx: Context, path: str):
+    ctx.check(ctx.lib.pd_tune_save(ctx.handle, os.fsencode(path)))
+
+
+def pd_tune_load(ctx: Context, path: str):
+    ctx.check(ctx.lib.pd_tune_load(ctx.handle, os.fsencode(path)))
 
 
 def pd_workspace_query(op: int, params: SinkhornParams, n: int, k: int = 0) -> int:

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <cmath>
 #include <atomic>
+#include <map>
+#include <utility>
 
 #include "pd_internal.h"
 #include "../../include/pd_ot.h"
@@ -28,6 +30,8 @@ struct pd_ctx {
     char* ext = nullptr;
     size_t ext_bytes = 0;
     size_t ws2_live = 0;       // bytes of ext used by ws2 in the current call
+    // tuning table: (d, support-size bucket) -> first CTA width of the base-2 kernel
+    std::map<std::pair<int, int>, int> tune;
     // launch profiler
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;   // free events
@@ -178,6 +182,9 @@ extern "C" void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, 
     p->eps_stages = 0;
     p->p = 2.0;
     p->bary_sharpen = 0;
+    p->cta_threads = 0;
+    p->kernel_tier = 0;
+    p->max_inner = 0;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -214,6 +221,8 @@ size_t pd_carve_ws(char* base, int P, int d, int dp, double gamma, SkWS* w, int*
     t.ctab = (float*)take(sizeof(float) * 5 * dp);
     t.order_buf = (int*)take(sizeof(int) * P);
     t.order = nullptr;
+    t.groups = (SkWS*)take(sizeof(SkWS));
+    t.ngroups = 1;
     *counter = (int*)take(sizeof(int) * 8);
     if (w) *w = t;
     return off;
@@ -273,6 +282,9 @@ static SkRun make_run(const pd_sinkhorn_params* prm) {
     r.rel_thresh = prm->rel_log_thresh < 0 ? prm->rel_log_thresh : (prm->precision == PD_BF16 ? -14.0 : -21.0);
     r.pot_support_only = 0;
     r.eps_stages = (prm->precision == PD_FP32 && prm->eps_stages > 0) ? std::min(prm->eps_stages, 16) : 0;
+    r.cta_threads = prm->cta_threads;
+    r.tier = prm->kernel_tier;
+    r.max_inner = prm->max_inner > 0 ? prm->max_inner : 0;
     return r;
 }
 
@@ -323,42 +335,85 @@ static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* r
 // left the base-2 range, until
 // no pair is active.  counter: 8 device ints; hbuf: 4 host ints; c (may be
 // NULL) receives the per-launch profile records.
-static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hbuf, cudaStream_t s) {
+// Support-size profile of a batch for the tuning table: half-octave bucket of
+// the mean number of support cells per side.
+static int support_bucket(double mean_cells) { return (int)std::floor(2.0 * std::log2(mean_cells + 1.0)); }
+
+// gs: the workspaces of the launch (one per grid size; gs[0] alone for a
+// single batch); dev_groups: device array of gs.size() descriptors (filled
+// here); order_buf: device ints for all pairs of all workspaces.
+static cudaError_t lse_rounds_groups(pd_ctx* c, std::vector<SkWS>& gs, SkWS* dev_groups, int* order_buf, SkRun r,
+                                     int* counter, int* hbuf, cudaStream_t s) {
     cudaError_t e;
+    const int G = (int)gs.size();
+    int Ptot = 0, dmax = 0;
+    for (auto& g : gs) { Ptot += g.P; dmax = std::max(dmax, g.d); }
+    if (Ptot == 0) return cudaSuccess;
     // Every pair runs to its stop inside one launch (its CTA iterates until
     // convergence or max_iter), so no round barrier idles the SMs; CTAs are
     // handed out largest support first, which keeps the long solves from
-    // starting last (makespan).  PD_LSE2_INNER caps the iterations per launch
-    // (tuning).
+    // starting last (makespan).  r.max_inner caps the iterations per launch.
     int n_inner = r.max_iter;
-    if (const char* ev = std::getenv("PD_LSE2_INNER")) {
-        const int v = std::atoi(ev);
-        if (v >= 1) n_inner = v;
-    }
-    if (w.P > 1 && w.order_buf) {
-        std::vector<int> ic((size_t)w.P * IC_N);
-        if ((e = cudaMemcpyAsync(ic.data(), w.ic, ic.size() * sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+    if (r.max_inner > 0 && r.max_inner < n_inner) n_inner = r.max_inner;
+    const int* order = nullptr;
+    if ((Ptot > 1 || G > 1) && order_buf) {
+        std::vector<int> code, size;
+        code.reserve(Ptot); size.reserve(Ptot);
+        for (int gi = 0; gi < G; ++gi) {
+            std::vector<int> ic((size_t)gs[gi].P * IC_N);
+            if (gs[gi].P == 0) continue;
+            if ((e = cudaMemcpyAsync(ic.data(), gs[gi].ic, ic.size() * sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess)
+                return e;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            for (int p = 0; p < gs[gi].P; ++p) {
+                code.push_back((gi << 24) | p);
+                size.push_back(ic[(size_t)p * IC_N + IC_NA] + ic[(size_t)p * IC_N + IC_NB]);
+            }
+        }
+        std::vector<int> ord(Ptot);
+        for (int k = 0; k < Ptot; ++k) ord[k] = k;
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return size[a] > size[b]; });
+        std::vector<int> codes(Ptot);
+        for (int k = 0; k < Ptot; ++k) codes[k] = code[ord[k]];
+        if (c && r.cta_threads == 0 && r.base_threads == 0 && !c->tune.empty()) {
+            double tot = 0;
+            for (int k = 0; k < Ptot; ++k) tot += size[k];
+            auto it = c->tune.find({dmax, support_bucket(tot / (2.0 * Ptot))});
+            if (it != c->tune.end()) r.base_threads = it->second;
+        }
+        if ((e = cudaMemcpyAsync(order_buf, codes.data(), sizeof(int) * Ptot, cudaMemcpyHostToDevice, s)) !=
             cudaSuccess)
             return e;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        std::vector<int> ord(w.P);
-        for (int p = 0; p < w.P; ++p) ord[p] = p;
-        auto size = [&](int p) { return ic[(size_t)p * IC_N + IC_NA] + ic[(size_t)p * IC_N + IC_NB]; };
-        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return size(a) > size(b); });
-        if ((e = cudaMemcpyAsync(w.order_buf, ord.data(), sizeof(int) * w.P, cudaMemcpyHostToDevice, s)) !=
-            cudaSuccess)
-            return e;
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        w.order = w.order_buf;
+        order = order_buf;
     }
+    // device descriptors: every workspace with its own pointers (no order)
+    for (int gi = 0; gi < G; ++gi) {
+        SkWS d = gs[gi];
+        d.order = nullptr;
+        d.groups = dev_groups + gi;
+        d.ngroups = 1;
+        gs[gi].groups = dev_groups + gi;
+        gs[gi].ngroups = 1;
+        if ((e = cudaMemcpyAsync(dev_groups + gi, &d, sizeof(SkWS), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    }
+    // the launch over all pairs of all workspaces
+    SkWS wall = gs[0];
+    wall.P = Ptot;
+    wall.order = order;
+    wall.groups = dev_groups;
+    wall.ngroups = G;
+    wall.d = dmax;
     // a pair can spend one round in each of the two hand-overs between kernels
     // and one in each of the two widenings below
     const int max_rounds = r.max_iter / n_inner + 6;
-    const int gbits = sk_lse2_grid_bits(w.gamma);
+    const int gbits = sk_lse2_grid_bits(gs[0].gamma);
     size_t smem = 0;
     if (gbits >= 0) {
         if ((e = cudaMemsetAsync(counter + 2, 0, sizeof(int), s)) != cudaSuccess) return e;
-        if ((e = sk_launch_lse2_need(w, counter + 2, s)) != cudaSuccess) return e;
+        for (int gi = 0; gi < G; ++gi)
+            if ((e = sk_launch_lse2_need(gs[gi], counter + 2, s)) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(hbuf + 2, counter + 2, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return e;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
@@ -366,7 +421,7 @@ static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hb
     }
     // CTA width of the base-2 kernel: 256 threads while there are several pairs
     // per SM, wider CTAs (more warps on one pair) once fewer pairs than SMs
-    // remain.  PD_LSE2_THREADS=256|512|1024 fixes it (tuning).
+    // remain.  r.cta_threads fixes it.
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -376,18 +431,15 @@ static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hb
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     const int fit_per_sm = smem > 0 ? (int)((size_t)smem_sm / (smem + 2048)) : 3;
     int fixed_threads = 0;
-    if (const char* ev = std::getenv("PD_LSE2_THREADS")) {
-        const int v = std::atoi(ev);
-        if (v == 256 || v == 512 || v == 1024) fixed_threads = v;
-    }
-    // PD_LSE2_TIER=gm runs every pair in the global-memory variant, =fp64 in the
-    // FP64 global-memory kernel (tests of the tiers on small pairs).
+    if (r.cta_threads == 128 || r.cta_threads == 256 || r.cta_threads == 512 || r.cta_threads == 1024)
+        fixed_threads = r.cta_threads;
+    if (fixed_threads == 128 && dmax > 128) fixed_threads = 256;
+    // tier 1 runs every pair in the global-memory variant, tier 2 in the FP64
+    // global-memory kernel (checks of the tiers against each other)
     size_t gcap = (size_t)-1;
-    if (const char* ev = std::getenv("PD_LSE2_TIER")) {
-        if (!std::strcmp(ev, "gm")) smem = 0;
-        if (!std::strcmp(ev, "fp64")) { smem = 0; gcap = 0; }
-    }
-    int active = w.P;
+    if (r.tier == 1) smem = 0;
+    if (r.tier == 2) { smem = 0; gcap = 0; }
+    int active = Ptot;
     bool any_gm = false, any_old = false;
     for (int round = 0; round < max_rounds; ++round) {
         if ((e = cudaMemsetAsync(counter, 0, 8 * sizeof(int), s)) != cudaSuccess) return e;
@@ -396,9 +448,11 @@ static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hb
             // 256 threads while several pairs share an SM; wider CTAs once fewer
             // pairs than 2 (1) per SM remain, or when the largest pair's shared
             // memory lets only 2 (1) CTAs onto an SM (e.g. a dense barycenter
-            // side), so that the SM still runs 16-32 warps
-            const int by_active = active > 2 * nsm ? 256 : (active > nsm ? 512 : 1024);
-            const int by_smem = fit_per_sm <= 1 ? 1024 : (fit_per_sm == 2 ? 512 : 256);
+            // side), so that the SM still runs 16-32 warps; the first width
+            // comes from the tuning table (base_threads) or is 256
+            const int base = (r.base_threads == 128 && dmax <= 128) || r.base_threads == 512 ? r.base_threads : 256;
+            const int by_active = active > 2 * nsm ? base : (active > nsm ? std::max(base, 512) : 1024);
+            const int by_smem = fit_per_sm <= 1 ? 1024 : (fit_per_sm == 2 ? 512 : 128);
             const int threads = fixed_threads ? fixed_threads : (by_active > by_smem ? by_active : by_smem);
             // Widening: a pair alone on an SM iterates ~2x faster in a
             // 512/1024-thread CTA than in a 256-thread CTA sharing the SM, so
@@ -407,20 +461,27 @@ static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hb
             SkRun rl = r;
             rl.exit_at = 0;
             if (!fixed_threads && gbits >= 0 && n_inner == r.max_iter) {
-                if (threads == 256) rl.exit_at = active - 2 * nsm;
+                if (threads <= 256) rl.exit_at = active - 2 * nsm;
                 else if (threads == 512) rl.exit_at = active - nsm;
             }
-            e = gbits >= 0 ? sk_launch_lse2(w, rl, n_inner, counter, smem, gbits, threads, s)
-                           : sk_launch_lse_smem(w, r, n_inner, counter, counter + 1, s);
+            if (gbits >= 0) {
+                e = sk_launch_lse2(wall, rl, n_inner, counter, smem, gbits, threads, s);
+            } else {
+                for (int gi = 0; gi < G && e == cudaSuccess; ++gi)
+                    e = sk_launch_lse_smem(gs[gi], r, n_inner, counter, counter + 1, s);
+            }
             if (e != cudaSuccess) return e;
         }
         if (gbits >= 0 && any_gm) {   // pairs whose supports do not fit on chip
             ProfScope ps(c, PD_K_ITER, s);
-            if ((e = sk_launch_lse2_gm(w, r, n_inner, counter, gbits, gcap, s)) != cudaSuccess) return e;
+            for (int gi = 0; gi < G; ++gi)
+                if ((e = sk_launch_lse2_gm(gs[gi], r, n_inner, counter, gbits, gcap, s)) != cudaSuccess) return e;
         }
         if (any_old) {                // the FP64 global-memory kernel
             ProfScope ps(c, PD_K_ITER, s);
-            if ((e = sk_launch_lse_iter(w, r, n_inner, counter, gbits >= 0 ? 2 : 1, s)) != cudaSuccess) return e;
+            for (int gi = 0; gi < G; ++gi)
+                if ((e = sk_launch_lse_iter(gs[gi], r, n_inner, counter, gbits >= 0 ? 2 : 1, s)) != cudaSuccess)
+                    return e;
         }
         if ((e = cudaMemcpyAsync(hbuf, counter, 4 * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return e;
@@ -436,6 +497,16 @@ static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hb
         active = hbuf[0];
     }
     return cudaSuccess;
+}
+
+// Iteration rounds of the log-domain engine for one workspace (see
+// lse_rounds_groups).
+static cudaError_t lse_rounds(pd_ctx* c, SkWS& w, SkRun r, int* counter, int* hbuf, cudaStream_t s) {
+    std::vector<SkWS> gs{w};
+    cudaError_t e = lse_rounds_groups(c, gs, w.groups, w.order_buf, r, counter, hbuf, s);
+    w.groups = gs[0].groups;
+    w.ngroups = 1;
+    return e;
 }
 static pd_status lse_solve(pd_ctx* c, SkWS& w, SkRun r, const double* g_init, double* cost, float* row_marg,
                            float* col_marg, double* f, double* g, int32_t* iters, float* err, int32_t* status,
@@ -497,6 +568,11 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: p != 2 needs the PD_FP32 engine");
     if (prm->eps_stages > 0 && prm->precision != PD_FP32)
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: eps_stages needs the PD_FP32 engine");
+    if (prm->cta_threads != 0 && prm->cta_threads != 128 && prm->cta_threads != 256 && prm->cta_threads != 512 &&
+        prm->cta_threads != 1024)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: cta_threads must be 0, 128, 256, 512 or 1024");
+    if (prm->kernel_tier < 0 || prm->kernel_tier > 2 || prm->max_inner < 0)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: kernel_tier must be 0..2 and max_inner >= 0");
     if (P < 0) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: P < 0");
     if (P == 0) return PD_OK;
     if (!cost || !histA || !histB || !massA || !massB) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: NULL input/cost");
@@ -595,6 +671,78 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     return PD_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Several grid sizes in one batch: one workspace per group, every pair of
+// every group in one persistent launch of the iteration kernel.
+
+extern "C" pd_status pd_sinkhorn_batch_groups(pd_ctx* c, int ngroups, const pd_sinkhorn_group* grp,
+                                              const pd_sinkhorn_params* prm, pd_stream stream) {
+    if (!c) return PD_ERR_INVALID;
+    call_begin(c);
+    if (!prm || !grp || ngroups < 1 || ngroups > 127)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch_groups: need params, groups and 1 <= ngroups <= 127");
+    if (!(prm->gamma > 0) || !std::isfinite(prm->gamma) || prm->max_iter < 1 || !(prm->tol >= 0) ||
+        prm->precision != PD_FP32 || !(prm->p >= 1.0 && prm->p <= 8.0) || prm->eps_stages != 0 ||
+        (prm->cta_threads != 0 && prm->cta_threads != 128 && prm->cta_threads != 256 && prm->cta_threads != 512 &&
+         prm->cta_threads != 1024) || prm->kernel_tier < 0 || prm->kernel_tier > 2 || prm->max_inner < 0)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch_groups: bad params (PD_FP32 only, no eps_stages)");
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const pd_sinkhorn_group& G = grp[gi];
+        if (G.d < 2 || G.d > 256 || G.P < 0 || G.P >= (1 << 24))
+            return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch_groups: group %d: need 2 <= d <= 256, 0 <= P < 2^24", gi);
+        if (G.P > 0 && (!G.cost || !G.histA || !G.histB || !G.massA || !G.massB))
+            return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch_groups: group %d: NULL input/cost", gi);
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    // layout: the groups' workspaces, then the descriptor array and the order
+    std::vector<size_t> off(ngroups);
+    size_t need = 0;
+    int Ptot = 0;
+    int* dummy = nullptr;
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const int d = grp[gi].d, dp = ((d + 63) / 64) * 64;
+        off[gi] = need;
+        need += align256(pd_carve_ws(nullptr, std::max(grp[gi].P, 1), d, dp, prm->gamma, nullptr, &dummy));
+        Ptot += grp[gi].P;
+    }
+    const size_t off_desc = need;
+    need += align256(sizeof(SkWS) * ngroups);
+    const size_t off_order = need;
+    need += align256(sizeof(int) * (size_t)std::max(Ptot, 1));
+    if (Ptot == 0) return PD_OK;
+    pd_status st = ensure_buffer(c, &c->ws, &c->ws_bytes, need, s);
+    if (st != PD_OK) return st;
+    char* base = (char*)c->ws;
+    std::vector<SkWS> gs;
+    int* counter = nullptr;
+    int* counter0 = nullptr;
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const pd_sinkhorn_group& G = grp[gi];
+        const int d = G.d, dp = ((d + 63) / 64) * 64;
+        SkWS w;
+        pd_carve_ws(base + off[gi], std::max(G.P, 1), d, dp, prm->gamma, &w, &counter);
+        if (!counter0) counter0 = counter;
+        w.P = G.P;
+        w.histA = G.histA; w.histB = G.histB; w.massA = G.massA; w.massB = G.massB; w.pairs = G.pairs;
+        w.p = prm->p;
+        CUDA_TRY(c, pd_upload_cost_tables(w, prm->gamma, s));
+        { ProfScope ps(c, PD_K_SETUP, s); CUDA_TRY(c, sk_launch_setup(w, G.g_init, s)); }
+        gs.push_back(w);
+    }
+    SkRun r = make_run(prm);
+    CUDA_TRY(c, lse_rounds_groups(c, gs, (SkWS*)(base + off_desc), (int*)(base + off_order), r, counter0, c->hflag, s));
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const pd_sinkhorn_group& G = grp[gi];
+        if (G.P == 0) continue;
+        ProfScope ps(c, PD_K_FINALIZE, s);
+        CUDA_TRY(c, sk_launch_lse_finalize(gs[gi], G.cost, G.row_marg, G.col_marg, G.f, G.g, G.iters, G.err, G.status,
+                                           r.pot_support_only, s));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return PD_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Outer loops: barycenter (Alg. 2) and k-means (Sec. 5).
@@ -963,6 +1111,114 @@ extern "C" pd_status pd_kmeans(pd_ctx* c, const uint32_t* hist, const uint32_t* 
         }
     }
     CUDA_TRY(c, cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the base-2 iteration kernel's CTA width.
+
+extern "C" pd_status pd_sinkhorn_tune(pd_ctx* c, const uint32_t* histA, const uint32_t* massA,
+                                      const uint32_t* histB, const uint32_t* massB, const int32_t* pairs, int P,
+                                      const pd_sinkhorn_params* prm, int trial_iters, int* threads_host,
+                                      double* trial_ms_host, pd_stream stream) {
+    if (!c) return PD_ERR_INVALID;
+    call_begin(c);
+    if (!prm || prm->precision != PD_FP32 || prm->d < 2 || prm->d > 256 || !(prm->gamma > 0) ||
+        !std::isfinite(prm->gamma) || !(prm->p >= 1.0 && prm->p <= 8.0) || P < 1 || trial_iters < 1 ||
+        !histA || !histB || !massA || !massB)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_tune: need PD_FP32 params, P >= 1, trial_iters >= 1, inputs");
+    if (sk_lse2_grid_bits(prm->gamma) < 0)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_tune: gamma below the base-2 kernel's range (nothing to tune)");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    SkWS w;
+    int* counter;
+    pd_status st = sinkhorn_ws(c, P, prm, &w, &counter, s);
+    if (st != PD_OK) return st;
+    w.histA = histA; w.histB = histB; w.massA = massA; w.massB = massB; w.pairs = pairs;
+    w.p = prm->p;
+    CUDA_TRY(c, pd_upload_cost_tables(w, prm->gamma, s));
+    SkRun r = make_run(prm);
+    r.max_iter = trial_iters;
+    r.max_inner = trial_iters;
+    r.tol = 0.0;
+    const int cands[4] = {128, 256, 512, 1024};
+    double ms[4] = {NAN, NAN, NAN, NAN};
+    const bool prof_was = c->prof;
+    int best = 256;
+    double best_ms = INFINITY;
+    double mean_cells = 0.0;
+    for (int k = 0; k < 3; ++k) {   // 1024 serves only the drain
+        if (cands[k] == 128 && prm->d > 128) continue;
+        // identical trials: the same cold start, the same iterations, one launch of one width
+        CUDA_TRY(c, sk_launch_setup(w, nullptr, s));
+        r.cta_threads = cands[k];
+        for (auto& rc : c->recs) { c->ev_pool.push_back(rc.a); c->ev_pool.push_back(rc.b); }
+        c->recs.clear();
+        c->prof = true;
+        cudaError_t e = lse_rounds(c, w, r, counter, c->hflag, s);
+        c->prof = prof_was;
+        CUDA_TRY(c, e);
+        double t = 0.0;
+        for (auto& rc : c->recs) {
+            if (rc.kind != PD_K_ITER) continue;
+            float x = 0.f;
+            CUDA_TRY(c, cudaEventSynchronize(rc.b));
+            CUDA_TRY(c, cudaEventElapsedTime(&x, rc.a, rc.b));
+            t += x;
+        }
+        for (auto& rc : c->recs) { c->ev_pool.push_back(rc.a); c->ev_pool.push_back(rc.b); }
+        c->recs.clear();
+        ms[k] = t;
+        if (t < best_ms) { best_ms = t; best = cands[k]; }
+    }
+    {
+        std::vector<int> ic((size_t)P * IC_N);
+        CUDA_TRY(c, cudaMemcpyAsync(ic.data(), w.ic, ic.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        for (int p = 0; p < P; ++p) mean_cells += ic[(size_t)p * IC_N + IC_NA] + ic[(size_t)p * IC_N + IC_NB];
+        mean_cells /= 2.0 * P;
+    }
+    c->tune[{prm->d, support_bucket(mean_cells)}] = best;
+    if (threads_host) *threads_host = best;
+    if (trial_ms_host) for (int k = 0; k < 4; ++k) trial_ms_host[k] = ms[k];
+    return PD_OK;
+}
+
+extern "C" pd_status pd_tune_save(pd_ctx* c, const char* path) {
+    if (!c) return PD_ERR_INVALID;
+    call_begin(c);
+    if (!path) return fail(c, PD_ERR_INVALID, "pd_tune_save: NULL path");
+    FILE* fh = std::fopen(path, "w");
+    if (!fh) return fail(c, PD_ERR_INVALID, "pd_tune_save: cannot write %s", path);
+    std::fprintf(fh, "# pd_ot tuning table: d support_bucket cta_threads\n");
+    for (auto& kv : c->tune) std::fprintf(fh, "%d %d %d\n", kv.first.first, kv.first.second, kv.second);
+    std::fclose(fh);
+    return PD_OK;
+}
+
+extern "C" pd_status pd_tune_load(pd_ctx* c, const char* path) {
+    if (!c) return PD_ERR_INVALID;
+    call_begin(c);
+    if (!path) return fail(c, PD_ERR_INVALID, "pd_tune_load: NULL path");
+    FILE* fh = std::fopen(path, "r");
+    if (!fh) return fail(c, PD_ERR_INVALID, "pd_tune_load: cannot read %s", path);
+    std::map<std::pair<int, int>, int> t;
+    char line[256];
+    int lineno = 0;
+    while (std::fgets(line, sizeof(line), fh)) {
+        ++lineno;
+        if (line[0] == '#' || line[0] == '\n') continue;
+        int d = 0, b = 0, th = 0;
+        if (std::sscanf(line, "%d %d %d", &d, &b, &th) != 3 || d < 2 || d > 256 ||
+            (th != 128 && th != 256 && th != 512) || (th == 128 && d > 128)) {
+            std::fclose(fh);
+            return fail(c, PD_ERR_INVALID, "pd_tune_load: bad entry on line %d of %s", lineno, path);
+        }
+        t[{d, b}] = th;
+    }
+    std::fclose(fh);
+    c->tune = t;
     return PD_OK;
 }
 

@@ -64,6 +64,12 @@ struct SkWS {
     float* ctab;                    // [5*dp] hi / lo FP32 splits of c_m/gamma and cD_m/gamma, log c_m
     int* order_buf;                 // [P] launch order of the pairs (filled by the host)
     const int* order;               // NULL: CTA b runs pair b; else CTA b runs pair order[b]
+    // device copies of workspace descriptors read by the base-2 kernel: with
+    // ngroups == 1 groups[0] is this workspace; a launch over several
+    // workspaces (several grid sizes) has ngroups > 1 and order codes
+    // group << 24 | pair
+    struct SkWS* groups;
+    int ngroups;
     // inputs: integer histograms (histA/massA, histB/massB) or, when wA / wB is
     // non-NULL, real-valued weights [N][d*d] for that side (its mass is their sum)
     const uint32_t *histA, *histB, *massA, *massB;
@@ -88,6 +94,10 @@ struct SkRun {
     // state and return, so that the host relaunches them in wider CTAs
     // (0: never)
     int exit_at;
+    int cta_threads;      // fixed CTA width of the base-2 kernel (0: automatic)
+    int base_threads;     // automatic mode: width of the first launch (0: 256; from the tuning table)
+    int tier;             // 0 automatic, 1 global-memory variant, 2 FP64 kernel for every pair
+    int max_inner;        // iterations per launch at most (0: run to the stop)
 };
 
 cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s);

@@ -240,6 +240,9 @@ cudaError_t pool_create(Pool& P, int d, int S, double gamma, bool want_g) {
     P.w.massA = P.w.massB = nullptr;
     P.w.pairs = nullptr;
     if ((e = pd_upload_cost_tables(P.w, gamma, P.stream)) != cudaSuccess) return e;
+    // the iteration kernel reads the pool's workspace descriptor from device memory
+    if ((e = cudaMemcpyAsync(P.w.groups, &P.w, sizeof(SkWS), cudaMemcpyHostToDevice, P.stream)) != cudaSuccess)
+        return e;
     // every slot starts stopped (status != ST_ACTIVE), so iteration launches skip it
     std::vector<int> ic((size_t)IC_N * S, 0);
     for (int s = 0; s < S; ++s) ic[(size_t)s * IC_N + IC_STATUS] = ST_CONVERGED;

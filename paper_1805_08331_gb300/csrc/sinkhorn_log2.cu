@@ -280,17 +280,22 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
     // ---- Delta output, shifted by its previous value
     const bool doD = out.wD > 0.f;
     const float MsD = -out.potD.x;
-    {
+    // lane ln of the fixed L2_DLANES-lane partition is thread ln % NT (one pass
+    // for NT >= L2_DLANES, two for 128 threads), so the per-warp partial sums
+    // and their order are the same at every width
+#pragma unroll
+    for (int base = 0; base < L2_DLANES; base += (NT < L2_DLANES ? NT : L2_DLANES)) {
+        const int ln = base + t;
         float sD = 0.f;
-        if (doD && t < L2_DLANES) {
-            for (int q = t; q < in_n; q += L2_DLANES) {
+        if (doD && ln < L2_DLANES) {
+            for (int q = ln; q < in_n; q += L2_DLANES) {
                 const float2 h = in_hin[q];
                 const float2 c = cdt[abs((int)in_col[q] - (int)in_row[q])];
                 sD += l2_ex2(((h.x - c.x) - MsD) + (h.y - c.y));
             }
         }
         sD = warp_sum(sD);
-        if (lane == 0 && wid < L2_DLANES / 32) redD[wid] = sD;
+        if (lane == 0 && (ln >> 5) < L2_DLANES / 32) redD[ln >> 5] = sD;
     }
     __syncthreads();
     if (t == 0 && doD) {
@@ -487,20 +492,25 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
 // leave at their next 16-iteration check with their state saved (they stay
 // active and the host runs them on in wider CTAs).
 template <int NT, bool GM>
-__global__ void __launch_bounds__(NT, (NT <= 256 ? 3 : (NT <= 512 ? 2 : 1)))
+__global__ void __launch_bounds__(NT, (NT <= 128 ? 6 : (NT <= 256 ? 3 : (NT <= 512 ? 2 : 1))))
 sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t gcap, int gbits) {
     constexpr int NW = NT / 32;
     __shared__ L2Side S[2];
-    __shared__ float redD[NW];
+    __shared__ float redD[NW > L2_DLANES / 32 ? NW : L2_DLANES / 32];
     __shared__ long long redE[NW];
     __shared__ int wcnt[NW > L2_MAXCH ? NW : L2_MAXCH];
     __shared__ int cnt[4];
     __shared__ int range_flag, fits, leave;
     const bool can_leave = !GM && r.exit_at > 0;
-    const int p = w.order ? w.order[blockIdx.x] : blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    PairPtrs q = pair_ptrs(w, p);
+    // the launch order maps this CTA to a pair, and, in a launch over several
+    // workspaces (pairs of several grid sizes), to its workspace: code =
+    // group << 24 | pair; the workspace descriptors are in device memory
+    const int code = w.order ? w.order[blockIdx.x] : blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const SkWS& W = w.groups[w.ngroups > 1 ? (code >> 24) : 0];
+    const int p = w.ngroups > 1 ? (code & 0xFFFFFF) : code;
+    PairPtrs q = pair_ptrs(W, p);
     if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG] != (GM ? 1 : 0)) return;
-    const int d = w.d, dp = w.dp, nA = q.ic[IC_NA], nB = q.ic[IC_NB];
+    const int d = W.d, dp = W.dp, nA = q.ic[IC_NA], nB = q.ic[IC_NB];
     l2_compact(q.rpa, d, nullptr, &cnt[0], nullptr, wcnt);
     l2_compact(q.rpb, d, nullptr, &cnt[1], nullptr, wcnt);
     const int nrA = cnt[0], nrB = cnt[1];
@@ -597,22 +607,22 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
                 const double wD = q.sc[s == 0 ? SC_AD : SC_BD];
                 X.wD = (float)wD;
                 X.lwD = wD > 0 ? l2_split(log(wD) * LOG2E, gsc) : make_float2(-INFINITY, 0.f);
-                X.potD = l2_split(pot[s][w.n - 1] * LOG2E, gsc);
+                X.potD = l2_split(pot[s][W.n - 1] * LOG2E, gsc);
                 X.hinD = wD > 0 ? make_float2(X.lwD.x + X.potD.x, X.lwD.y + X.potD.y) : make_float2(-INFINITY, 0.f);
             }
             __syncthreads();
         }
     }
     {
-        const double sc2 = LOG2E / (w.gamma * (double)d * (double)d);
+        const double sc2 = LOG2E / (W.gamma * (double)d * (double)d);
         float2* ct = smp<float2>(K.ct);
         float2* cdt = smp<float2>(K.cdt);
         for (int m = t; m < 2 * d - 1; m += NT) {
             const double z = (double)(m - (d - 1));
-            ct[m] = l2_split(w.p == 2.0 ? z * z * sc2 : pd_c1p(m, d - 1, d, w.p) * (LOG2E / w.gamma), gsc);
+            ct[m] = l2_split(W.p == 2.0 ? z * z * sc2 : pd_c1p(m, d - 1, d, W.p) * (LOG2E / W.gamma), gsc);
         }
         for (int m = t; m < d; m += NT)
-            cdt[m] = l2_split(w.p == 2.0 ? 0.5 * (double)m * (double)m * sc2 : pd_cdiagp(0, m, d, w.p) * (LOG2E / w.gamma),
+            cdt[m] = l2_split(W.p == 2.0 ? 0.5 * (double)m * (double)m * sc2 : pd_cdiagp(0, m, d, W.p) * (LOG2E / W.gamma),
                               gsc);
     }
     if (t == 0) range_flag = 0;
@@ -660,7 +670,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
         const int* list = s == 0 ? q.sa : q.sb;
         const float2* xpot = sdp<float2, GM>(gb, X.pot);
         for (int e = t; e < X.n; e += NT) pot[list[e]] = ((double)xpot[e].x + (double)xpot[e].y) * LN2;
-        if (t == 0) pot[w.n - 1] = ((double)X.potD.x + (double)X.potD.y) * LN2;
+        if (t == 0) pot[W.n - 1] = ((double)X.potD.x + (double)X.potD.y) * LN2;
     }
     if (t == 0) {
         q.sc[SC_ERR] = (double)errf;
@@ -741,6 +751,9 @@ cudaError_t sk_launch_lse2(const SkWS& w, SkRun r, int n_inner, int* counter, si
                            cudaStream_t s) {
     if (w.P == 0) return cudaSuccess;
     switch (threads) {
+        case 128:   // needs d <= 128 (one thread per grid row while loading)
+            if (w.d > 128) return cudaErrorInvalidValue;
+            return launch_lse2<128, false>(w, r, n_inner, counter, smem, 0, gbits, s);
         case 256: return launch_lse2<256, false>(w, r, n_inner, counter, smem, 0, gbits, s);
         case 512: return launch_lse2<512, false>(w, r, n_inner, counter, smem, 0, gbits, s);
         case 1024: return launch_lse2<1024, false>(w, r, n_inner, counter, smem, 0, gbits, s);

@@ -20,9 +20,9 @@ def ctx():
     c.close()
 
 
-def _solve(ctx, hA, hB, d, gamma, max_iter, tol, precision=api.PD_FP32, pairs=None, refine_iters=0, **kw):
+def _solve(ctx, hA, hB, d, gamma, max_iter, tol, precision=api.PD_FP32, pairs=None, refine_iters=0, prm=None, **kw):
     p = api.pd_sinkhorn_default_params(gamma, d, max_iter=max_iter, tol=tol, precision=precision,
-                                       refine_iters=refine_iters)
+                                       refine_iters=refine_iters, **(prm or {}))
     out = api.pd_sinkhorn_batch(ctx, hists_to_gpu(hA), dev(masses(hA).view(np.int32)), hists_to_gpu(hB),
                                 dev(masses(hB).view(np.int32)), p, pairs=pairs, **kw)
     torch.cuda.synchronize()
@@ -108,19 +108,17 @@ def test_marginals_and_potentials_elementwise_at_d128_gamma1e3(ctx):
         assert abs(g["cost"][p] - r["cost"]) <= 1e-6 * r["cost"]
 
 
-@pytest.mark.parametrize("tier", [None, "gm", "fp64"])
-def test_d256_matches_oracle_on_every_tier(ctx, tier, monkeypatch):
+@pytest.mark.parametrize("tier", [0, 1, 2])
+def test_d256_matches_oracle_on_every_tier(ctx, tier):
     """d = 256 (the largest grid) on small diagrams, so the FP64 oracle stays
     fast: the on-chip kernel, its global-memory variant and the FP64 kernel
     each match the oracle after 300 iterations (cost 1e-6 relative, marginals
     and potentials element by element)."""
-    if tier:
-        monkeypatch.setenv("PD_LSE2_TIER", tier)
     d, gamma, T = 256, 5e-3, 300
     b, t, o = inputs.random_diagrams(4, nmin=30, nmax=120, seed=256)
     h, _ = oracle.rasterize(b, t, o, d)
     hA, hB = h[0::2], h[1::2]
-    g = _solve(ctx, hA, hB, d, gamma, T, 0.0, want_marginals=True, want_potentials=True)
+    g = _solve(ctx, hA, hB, d, gamma, T, 0.0, prm={"kernel_tier": tier}, want_marginals=True, want_potentials=True)
     assert np.all(g["iters"] == T)
     for p in range(2):
         r = oracle.sinkhorn_pd(d, gamma, hA[p], hB[p], T, 0.0)
@@ -133,7 +131,7 @@ def test_d256_matches_oracle_on_every_tier(ctx, tier, monkeypatch):
         assert np.allclose(g["g"][p][mb], r["g"][mb], rtol=0, atol=gamma * 2e-5)
 
 
-def test_cta_width_and_widening_leave_results_bitwise_equal(ctx, monkeypatch):
+def test_cta_width_and_widening_leave_results_bitwise_equal(ctx):
     """The base-2 kernel sums in the same order at 256, 512 and 1024 threads
     per pair (stage-1 and stage-2 sums are per element or per 4-lane group,
     the Delta sum has a fixed 256-lane partition, the marginal error is an
@@ -144,41 +142,37 @@ def test_cta_width_and_widening_leave_results_bitwise_equal(ctx, monkeypatch):
     b, t, o = inputs.random_diagrams(2 * P, nmin=10, nmax=150, seed=77)
     h, _ = oracle.rasterize(b, t, o, d)
     runs = {}
-    for thr in ("256", "512", "1024", None):
-        if thr:
-            monkeypatch.setenv("PD_LSE2_THREADS", thr)
-        else:
-            monkeypatch.delenv("PD_LSE2_THREADS", raising=False)
+    for thr in (256, 128, 512, 1024, 0):
         ctx.profile_enable(True)
         before = ctx.profile_read().get("iter", (0.0, 0))[1]
-        runs[thr] = _solve(ctx, h[0::2], h[1::2], d, gamma, 3000, 1e-6, want_potentials=True)
+        runs[thr] = _solve(ctx, h[0::2], h[1::2], d, gamma, 3000, 1e-6, prm={"cta_threads": thr},
+                           want_potentials=True)
         runs[thr]["launches"] = ctx.profile_read().get("iter", (0.0, 0))[1] - before
         ctx.profile_enable(False)
-    ref = runs["256"]
+    ref = runs[256]
     assert ref["launches"] == 1 and len(set(ref["iters"].tolist())) > 50   # one launch; varied stops
-    assert runs[None]["launches"] > 1                                      # the widening ran
+    assert runs[0]["launches"] > 1                                         # the widening ran
     for thr, r in runs.items():
         for k in ("cost", "iters", "err", "status", "f", "g"):
             assert np.array_equal(r[k], ref[k]), (thr, k)
 
 
-@pytest.mark.parametrize("tier", ["gm", "fp64"])
-def test_kernel_tiers_match_oracle(ctx, tier, monkeypatch):
+@pytest.mark.parametrize("tier", [1, 2])
+def test_kernel_tiers_match_oracle(ctx, tier):
     """Every pair forced into the global-memory variant of the base-2 kernel
     (gm) or into the FP64 global-memory kernel (fp64): same iterates as the
     oracle after 400 iterations at d=128, gamma=1e-3 (relative cost <= 1e-6)."""
-    monkeypatch.setenv("PD_LSE2_TIER", tier)
     d, gamma = 128, 1e-3
     b, t, o = inputs.random_diagrams(4, nmin=50, nmax=500, seed=d)
     h, _ = oracle.rasterize(b, t, o, d)
     ref = oracle.sinkhorn_pd_batch(d, gamma, h[0::2], h[1::2], 400, 0.0)
-    g = _solve(ctx, h[0::2], h[1::2], d, gamma, 400, 0.0)
+    g = _solve(ctx, h[0::2], h[1::2], d, gamma, 400, 0.0, prm={"kernel_tier": tier})
     assert np.all(g["iters"] == 400)
     rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
     assert rel.max() <= 1e-6, rel
 
 
-def test_large_supports_global_variant_vs_fp64_kernel(ctx, monkeypatch):
+def test_large_supports_global_variant_vs_fp64_kernel(ctx):
     """Pairs of 4000-point diagrams at d=256 have supports too large for shared
     memory, so the default path runs them in the global-memory base-2 variant;
     the independent FP64 global-memory kernel gives the same iterates."""
@@ -188,8 +182,7 @@ def test_large_supports_global_variant_vs_fp64_kernel(ctx, monkeypatch):
     nnz = (h.reshape(4, -1) > 0).sum(1)
     assert np.all(nnz[0::2] + nnz[1::2] > 5000)   # beyond the on-chip limit (~4.8k cells at d=256)
     g = _solve(ctx, h[0::2], h[1::2], d, gamma, 150, 0.0)
-    monkeypatch.setenv("PD_LSE2_TIER", "fp64")
-    r = _solve(ctx, h[0::2], h[1::2], d, gamma, 150, 0.0)
+    r = _solve(ctx, h[0::2], h[1::2], d, gamma, 150, 0.0, prm={"kernel_tier": 2})
     assert np.all(g["iters"] == 150) and np.all(r["iters"] == 150)
     rel = np.abs(g["cost"] - r["cost"]) / r["cost"]
     assert rel.max() <= 1e-6, rel
@@ -345,3 +338,71 @@ def test_plain_one_pair_per_launch_equals_batched_dense(ctx):
     ok = plain["status"] == api.PD_OK
     assert ok.all()
     assert np.all(np.abs(plain["cost"] - ref["cost"]) <= 2e-6 * ref["cost"])
+
+
+def test_autotuner_choice_changes_speed_not_results(ctx, tmp_path):
+    """pd_sinkhorn_tune times one launch per CTA width on the batch and keys its
+    choice by (d, support bucket); solves that pick the tuned width give the
+    same results bitwise as the built-in rule (fixed-order sums), and the table
+    survives a save / load round trip; a malformed table is refused."""
+    d, gamma, P = 64, 5e-3, 600
+    b, t, o = inputs.random_diagrams(2 * P, nmin=20, nmax=200, seed=31)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = hists_to_gpu(h[0::2]), hists_to_gpu(h[1::2])
+    mA, mB = dev(masses(h[0::2]).view(np.int32)), dev(masses(h[1::2]).view(np.int32))
+    prm = api.pd_sinkhorn_default_params(gamma, d, max_iter=4000, tol=1e-6)
+    ref = api.pd_sinkhorn_batch(ctx, hA, mA, hB, mB, prm, want_potentials=True)
+    c2 = api.Context(0)
+    try:
+        th, ms = api.pd_sinkhorn_tune(c2, hA, mA, hB, mB, prm, trial_iters=48)
+        assert th in (128, 256, 512) and set(ms) == {128, 256, 512} and all(v > 0 for v in ms.values())
+        assert ms[th] == min(ms.values())
+        path = str(tmp_path / "tune.txt")
+        api.pd_tune_save(c2, path)
+        c3 = api.Context(0)
+        try:
+            api.pd_tune_load(c3, path)
+            for cx in (c2, c3):
+                out = api.pd_sinkhorn_batch(cx, hA, mA, hB, mB, prm, want_potentials=True)
+                for k in ("cost", "iters", "err", "status", "f", "g"):
+                    assert torch.equal(out[k], ref[k]), k
+            with open(path, "w") as fh:
+                fh.write("64 3 333\n")
+            with pytest.raises(api.PdError) as e:
+                api.pd_tune_load(c3, path)
+            assert e.value.status == api.PD_ERR_INVALID
+        finally:
+            c3.close()
+    finally:
+        c2.close()
+
+
+def test_mixed_grid_sizes_in_one_launch_equal_separate_batches(ctx):
+    """pd_sinkhorn_batch_groups runs pairs of d = 32, 64, 128 and 256 in one
+    persistent launch; each pair's results are bitwise those of a
+    pd_sinkhorn_batch of its own grid size (a pair's CTA does the same
+    arithmetic whatever else is in the launch), and a sample agrees with the
+    oracle."""
+    gamma = 5e-3
+    groups, refs, hs = [], [], []
+    for k, (d, P) in enumerate(((32, 40), (64, 30), (128, 20), (256, 6))):
+        b, t, o = inputs.random_diagrams(2 * P, nmin=10, nmax=150, seed=400 + d)
+        h, _ = oracle.rasterize(b, t, o, d)
+        hA, hB = hists_to_gpu(h[0::2]), hists_to_gpu(h[1::2])
+        mA, mB = dev(masses(h[0::2]).view(np.int32)), dev(masses(h[1::2]).view(np.int32))
+        groups.append({"d": d, "histA": hA, "massA": mA, "histB": hB, "massB": mB})
+        prm = api.pd_sinkhorn_default_params(gamma, d, max_iter=3000, tol=1e-6)
+        refs.append(api.pd_sinkhorn_batch(ctx, hA, mA, hB, mB, prm, want_potentials=True))
+        hs.append((h[0::2], h[1::2]))
+    prm = api.pd_sinkhorn_default_params(gamma, 0, max_iter=3000, tol=1e-6)
+    ctx.profile_enable(True)
+    outs = api.pd_sinkhorn_batch_groups(ctx, groups, prm, want_potentials=True)
+    torch.cuda.synchronize()
+    launches = ctx.profile_read().get("iter", (0.0, 0))[1]
+    ctx.profile_enable(False)
+    assert launches <= 3    # one launch for all grid sizes (plus at most the two drain hand-overs)
+    for g, o, r, (hA, hB) in zip(groups, outs, refs, hs):
+        for k in ("cost", "iters", "err", "status", "f", "g"):
+            assert torch.equal(o[k], r[k]), (g["d"], k)
+        ref = oracle.sinkhorn_pd(g["d"], gamma, hA[0], hB[0], 3000, 1e-6)
+        assert abs(float(o["cost"][0]) - ref["cost"]) <= 5e-6 * ref["cost"]
