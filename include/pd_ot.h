@@ -124,6 +124,10 @@ typedef struct {
                           FP64 kernel (for checking the tiers against each other) */
     int max_inner;     /* PD_FP32: iterations per launch at most; 0 (default) = every pair runs to its stop
                           inside one launch */
+    int diag_tc_timeout; /* PD_BF16 diagnostic of the tensor-core kernel's bounded waits: 1 = its first GEMM
+                          is not issued and the wait for it has a spin limit of 0, so the wait gives up at once
+                          with no tensor-core work in flight; the kernel frees its tensor memory and the call
+                          returns PD_ERR_TIMEOUT (the context stays usable).  0 (default) = off */
 } pd_sinkhorn_params;
 
 /* Fill *p with defaults for (gamma, d): max_iter 20000, tol 1e-6, PD_FP32,
@@ -156,7 +160,12 @@ void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, int d);
  *   f, g     : double [P][d*d+1]   potentials; entries whose kernel sum underflows are +inf
  *   iters    : int32  [P]          iterations run
  *   err      : float  [P]          last err_t (relative)
- *   status   : int32  [P]          PD_OK, PD_NOT_CONVERGED or PD_ERR_RANGE
+ *   status   : int32  [P]          PD_OK, PD_NOT_CONVERGED or PD_ERR_RANGE.  The linear-domain
+ *                                  engines (PD_FP32_DENSE, PD_FP32_PLAIN) check every pair they
+ *                                  report PD_OK: the exact log-domain marginals of its final plan
+ *                                  must be within max(10 tol, 1e-5) of (a, b) (relative L1, both
+ *                                  sides), else the pair is PD_ERR_RANGE (its representation
+ *                                  dropped terms that matter, e.g. at small gamma)
  * Synchronises `stream` (the iteration loop checks convergence on the host).
  * Errors: PD_ERR_INVALID (bad params / NULL cost / P < 0), PD_ERR_OOM, PD_ERR_CUDA.
  */

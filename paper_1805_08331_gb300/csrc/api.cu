@@ -185,6 +185,7 @@ extern "C" void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, 
     p->cta_threads = 0;
     p->kernel_tier = 0;
     p->max_inner = 0;
+    p->diag_tc_timeout = 0;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -285,6 +286,7 @@ static SkRun make_run(const pd_sinkhorn_params* prm) {
     r.cta_threads = prm->cta_threads;
     r.tier = prm->kernel_tier;
     r.max_inner = prm->max_inner > 0 ? prm->max_inner : 0;
+    r.diag_tc_timeout = prm->precision == PD_BF16 && prm->diag_tc_timeout != 0;
     return r;
 }
 
@@ -545,6 +547,22 @@ static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* r
     return PD_OK;
 }
 
+// Range check of the linear-domain engines after their finalize: the exact
+// log-domain marginals of each pair's final plan (potentials rebuilt from the
+// residual representation) are compared with a and b; a pair reported PD_OK
+// whose exact marginal error exceeds max(10 tol, 1e-5) gets PD_ERR_RANGE.
+static pd_status linear_range_check(pd_ctx* c, SkWS& w, double tol, int32_t* status, cudaStream_t s) {
+    if (!status) return PD_OK;
+    CUDA_TRY(c, sk_launch_rebuild_potentials(w, s));
+    float* row = reinterpret_cast<float*>(w.L64);          // [P][n] rows, then [P][n] columns (scratch)
+    float* col = row + (size_t)w.P * w.n;
+    double* cost_scratch = w.Au;                             // P doubles of scratch
+    { ProfScope ps(c, PD_K_FINALIZE, s);
+      CUDA_TRY(c, sk_launch_lse_finalize(w, cost_scratch, row, col, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s)); }
+    CUDA_TRY(c, sk_launch_range_check(w, row, col, status, std::max(10.0 * tol, 1e-5), s));
+    return PD_OK;
+}
+
 extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const uint32_t* massA, const uint32_t* histB,
                                        const uint32_t* massB, const int32_t* pairs, int P,
                                        const pd_sinkhorn_params* prm, const double* g_init, double* cost,
@@ -652,6 +670,8 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
                                              g ? g + p * n : nullptr, iters ? iters + p : nullptr,
                                              err ? err + p : nullptr, status ? status + p : nullptr, s)); }
         }
+        pd_status stc = linear_range_check(c, w, prm->tol, status, s);
+        if (stc != PD_OK) return stc;
         CUDA_TRY(c, cudaStreamSynchronize(s));
         return PD_OK;
     }
@@ -667,6 +687,8 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     }
     { ProfScope ps(c, PD_K_ABSORB, s); CUDA_TRY(c, sk_launch_absorb(w, r, s)); }   // pairs that finished inside the log step
     { ProfScope ps(c, PD_K_FINALIZE, s); CUDA_TRY(c, sk_launch_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, s)); }
+    pd_status stc = linear_range_check(c, w, prm->tol, status, s);
+    if (stc != PD_OK) return stc;
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return PD_OK;
 }

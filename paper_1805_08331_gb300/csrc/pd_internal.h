@@ -98,6 +98,7 @@ struct SkRun {
     int base_threads;     // automatic mode: width of the first launch (0: 256; from the tuning table)
     int tier;             // 0 automatic, 1 global-memory variant, 2 FP64 kernel for every pair
     int max_inner;        // iterations per launch at most (0: run to the stop)
+    int diag_tc_timeout;  // tensor-core kernel: skip the first GEMM issue, wait with a spin limit of 0
 };
 
 cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s);
@@ -114,6 +115,11 @@ cudaError_t sk_launch_lse_iter(const SkWS& w, SkRun r, int n_inner, int* active_
 cudaError_t sk_launch_iter_bf16(const SkWS& w, SkRun r, int n_inner, int* active_count, int* error_flag,
                                 cudaStream_t s);
 cudaError_t sk_launch_refine_prep(const SkWS& w, cudaStream_t s);
+// potentials phi, psi from the linear-domain residual representation (pairs keep their status)
+cudaError_t sk_launch_rebuild_potentials(const SkWS& w, cudaStream_t s);
+// PD_OK pairs whose exact marginal error (row / col: [P][d*d+1] exact marginals) exceeds thr -> PD_ERR_RANGE
+cudaError_t sk_launch_range_check(const SkWS& w, const float* row, const float* col, int32_t* status, double thr,
+                                  cudaStream_t s);
 cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count,
                                cudaStream_t s);
 // base-2 on-chip iteration kernel (sinkhorn_log2.cu)

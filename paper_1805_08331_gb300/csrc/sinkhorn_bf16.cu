@@ -70,15 +70,17 @@ struct BfShared {
 };
 
 // Issue one GEMM (thread 0) after making the operand writes visible, then wait
-// for it; returns false on a timed-out wait.
+// for it; returns false on a timed-out wait.  diag (a check of the timeout
+// path): the GEMM is not issued and the wait has a spin limit of 0, so it
+// gives up at once with no tensor-core work in flight.
 __device__ __forceinline__ bool run_gemm(uint32_t tmem, const unsigned char* A, const unsigned char* B, uint64_t* mbar,
-                                         uint32_t& phase) {
+                                         uint32_t& phase, bool diag) {
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (threadIdx.x == 0) gemm128_issue(tmem, smem_u32(A), smem_u32(B), mbar);
-    const bool ok = __syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0) != 0;   // every thread takes the same path
+    if (threadIdx.x == 0 && !diag) gemm128_issue(tmem, smem_u32(A), smem_u32(B), mbar);
+    const bool ok = __syncthreads_and(mbar_wait(mbar, phase, diag ? 0u : (1u << 26)) ? 1 : 0) != 0;   // same path for all
     phase ^= 1u;
     tc_fence_after();
     return ok;
@@ -143,12 +145,12 @@ __global__ void __launch_bounds__(BF_THREADS) sk_iter_bf16_kernel(SkWS w, SkRun 
     float* stg = S.stage + warp * 32 * 33;
     for (int it = 0; it < n_inner; ++it) {
         // ================= u-update
-        if (!run_gemm(tm, S.K1u, S.X, &mbar, phase)) { timeout = 1; break; }
+        if (!run_gemm(tm, S.K1u, S.X, &mbar, phase, r.diag_tc_timeout != 0)) { timeout = 1; break; }
         epi_dense(tm, S.X);                                            // Wt rows j
         float sKv = 0.f;                                               // sum_y KDv vt (for ut_Delta)
         for (int e = t; e < nb; e += BF_THREADS) { int c = q.sb[e]; sKv += q.KDv[c] * q.vt[c]; }
         sKv = block_sum(sKv, shf);
-        if (!run_gemm(tm, S.K2u, S.X, &mbar, phase)) { timeout = 1; break; }
+        if (!run_gemm(tm, S.K2u, S.X, &mbar, phase, r.diag_tc_timeout != 0)) { timeout = 1; break; }
         // R rows i: ut on supp(a) row i, then U' row i = rs_v[i] ut[i, :]
         {
             const int i = t;
@@ -178,12 +180,12 @@ __global__ void __launch_bounds__(BF_THREADS) sk_iter_bf16_kernel(SkWS w, SkRun 
         if (aD > 0.f && !(fabsf(logf(utD_new / aD)) <= tau)) range_sh = 1;
         utD = utD_new;
         // ================= v-update
-        if (!run_gemm(tm, S.K1v, S.X, &mbar, phase)) { timeout = 1; break; }
+        if (!run_gemm(tm, S.K1v, S.X, &mbar, phase, r.diag_tc_timeout != 0)) { timeout = 1; break; }
         epi_dense(tm, S.X);                                            // Wv rows l
         float sKu = 0.f;                                               // sum_x KDu ut (for v_Delta)
         for (int e = t; e < na; e += BF_THREADS) { int c = q.sa[e]; sKu += q.KDu[c] * q.ut[c]; }
         sKu = block_sum(sKu, shf);
-        if (!run_gemm(tm, S.K2v, S.X, &mbar, phase)) { timeout = 1; break; }
+        if (!run_gemm(tm, S.K2v, S.X, &mbar, phase, r.diag_tc_timeout != 0)) { timeout = 1; break; }
         float e_loc = 0.f;
         {
             const int k = t;
@@ -296,6 +298,43 @@ __global__ void sk_reactivate_kernel(SkWS w) {
     if (st == ST_CONVERGED && w.sc[(size_t)p * SC_N + SC_TOTAL] == 0) return;
     ic[IC_STATUS] = ST_ACTIVE;
     ic[IC_BIG] = 0;
+}
+
+cudaError_t sk_launch_rebuild_potentials(const SkWS& w, cudaStream_t s) {
+    if (w.P == 0) return cudaSuccess;
+    sk_rebuild_potentials_kernel<<<w.P, 256, 0, s>>>(w);
+    return cudaGetLastError();
+}
+
+// Range check of the linear-domain engines: row / col hold the exact
+// (log-domain) marginals of every pair's final plan, [P][d*d+1] each; a pair
+// reported PD_OK whose exact marginal error (both sides, relative to the total
+// mass) exceeds thr is reported PD_ERR_RANGE instead (its representation
+// dropped terms that matter).
+__global__ void sk_range_check_kernel(SkWS w, const float* __restrict__ row, const float* __restrict__ col,
+                                      int32_t* __restrict__ status, double thr) {
+    __shared__ double sh[32];
+    const int p = blockIdx.x;
+    if (status[p] != 0) return;
+    PairPtrs q = pair_ptrs(w, p);
+    const int d = w.d, dp = w.dp, n = w.n;
+    const float* rp = row + (size_t)p * n;
+    const float* cp = col + (size_t)p * n;
+    double e = 0.0;
+    for (int x = threadIdx.x; x < d * d; x += blockDim.x) {
+        const int i = x / d, j = x - i * d;
+        e += fabs((double)rp[x] - (double)q.am[i * dp + j]) + fabs((double)cp[x] - (double)q.bm[i * dp + j]);
+    }
+    if (threadIdx.x == 0) e += fabs((double)rp[n - 1] - q.sc[SC_AD]) + fabs((double)cp[n - 1] - q.sc[SC_BD]);
+    e = block_sum(e, sh);
+    if (threadIdx.x == 0 && q.sc[SC_TOTAL] > 0 && !(e / q.sc[SC_TOTAL] <= thr)) status[p] = 8;   // PD_ERR_RANGE
+}
+
+cudaError_t sk_launch_range_check(const SkWS& w, const float* row, const float* col, int32_t* status, double thr,
+                                  cudaStream_t s) {
+    if (w.P == 0 || !status) return cudaSuccess;
+    sk_range_check_kernel<<<w.P, 256, 0, s>>>(w, row, col, status, thr);
+    return cudaGetLastError();
 }
 
 cudaError_t sk_launch_refine_prep(const SkWS& w, cudaStream_t s) {

@@ -406,3 +406,52 @@ def test_mixed_grid_sizes_in_one_launch_equal_separate_batches(ctx):
             assert torch.equal(o[k], r[k]), (g["d"], k)
         ref = oracle.sinkhorn_pd(g["d"], gamma, hA[0], hB[0], 3000, 1e-6)
         assert abs(float(o["cost"][0]) - ref["cost"]) <= 5e-6 * ref["cost"]
+
+
+def test_tensor_core_wait_timeout_path(ctx):
+    """The tcgen05 kernel's bounded mbarrier wait: with the diagnostic set, the
+    kernel issues no GEMM and waits with a spin limit of 0, so the wait gives up
+    with no tensor-core work in flight; the kernel frees its tensor memory and
+    the call reports PD_ERR_TIMEOUT.  The same context then solves normally."""
+    d, gamma = 32, 1e-2
+    b, t, o = inputs.random_diagrams(4, nmin=20, nmax=40, seed=2)
+    h, _ = oracle.rasterize(b, t, o, d)
+    with pytest.raises(api.PdError) as e:
+        _solve(ctx, h[0::2], h[1::2], d, gamma, 500, 1e-6, precision=api.PD_BF16, refine_iters=1,
+               prm={"diag_tc_timeout": 1})
+    assert e.value.status == api.PD_ERR_TIMEOUT
+    ref = oracle.sinkhorn_pd_batch(d, gamma, h[0::2], h[1::2], 20000, 1e-6)
+    for prec in (api.PD_BF16, api.PD_FP32):
+        g = _solve(ctx, h[0::2], h[1::2], d, gamma, 20000, 1e-6, precision=prec, refine_iters=1)
+        assert np.all(g["status"] == api.PD_OK)
+        assert np.all(np.abs(g["cost"] - ref["cost"]) <= 5e-6 * ref["cost"])
+
+
+@pytest.mark.parametrize("engine", [api.PD_FP32_DENSE, api.PD_FP32_PLAIN])
+def test_linear_domain_engines_flag_dropped_terms(ctx, engine):
+    """At d = 128, gamma = 1e-3 the absorbed linear-domain representation can
+    lose terms that matter; such pairs must come back PD_ERR_RANGE, never
+    PD_OK with a wrong answer.  Every pair reported PD_OK has a plan whose
+    marginals, evaluated by the oracle's definition from the returned
+    potentials, are within the check's bound, and its cost is close to the
+    converged FP64 oracle."""
+    d, gamma, P = 128, 1e-3, 16
+    b, t, o = inputs.random_diagrams(2 * P, nmin=50, nmax=500, seed=1)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    g = _solve(ctx, hA, hB, d, gamma, 20000, 1e-6, precision=engine, want_potentials=True)
+    ref = oracle.sinkhorn_pd_batch(d, gamma, hA, hB, 20000, 1e-9)
+    ok = g["status"] == api.PD_OK
+    rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
+    print("status", g["status"].tolist(), "rel", np.round(rel, 8).tolist())
+    assert set(g["status"].tolist()) <= {api.PD_OK, api.PD_NOT_CONVERGED, api.PD_ERR_RANGE}
+    for p in np.nonzero(ok)[0]:
+        a, bb = oracle.augment(hA[p], hB[p])
+        sa, sb = np.nonzero(a > 0)[0], np.nonzero(bb > 0)[0]
+        C = np.array([[oracle.cost(d, x, y) for y in sb] for x in sa])
+        lp = (np.log(a[sa])[:, None] + np.log(bb[sb])[None, :]
+              + (g["f"][p][sa][:, None] + g["g"][p][sb][None, :] - C) / gamma)
+        plan = np.exp(lp)
+        e = (np.abs(plan.sum(1) - a[sa]).sum() + np.abs(plan.sum(0) - bb[sb]).sum()) / a.sum()
+        assert e <= 2e-5, (p, e)
+        assert rel[p] <= 1e-4, (p, rel[p])
