@@ -75,7 +75,7 @@ static pd_status fail(pd_ctx* c, pd_status s, const char* fmt, ...) {
 // Start of every entry point that takes a context: clear the message and the
 // per-call use of a caller-supplied workspace.
 static void call_begin(pd_ctx* c) {
-    call_begin(c);
+    c->err.clear();
     c->ws2_live = 0;
 }
 
