@@ -578,8 +578,9 @@ def compare_leg(args, ctx):
         "note": f"executed = 8 x {dpad}^3 flop per pair-iteration (four {dpad}x{dpad}x{dpad} MMA GEMMs, the grid "
                 f"zero-padded to {dpad}); algorithmic = 8 x d^3"}
     bf = res["bf16_tensor_core_refined"]["cell_updates_per_s"]
-    res["bf16_over_fp32_plain"] = bf / res["fp32_plain_one_pair_per_launch"]["cell_updates_per_s"]
-    res["bf16_over_fp32_dense_batched"] = bf / res["fp32_dense_batched"]["cell_updates_per_s"]
+    for k in ("fp32_plain_one_pair_per_launch", "fp32_dense_batched", "fp32_log_domain_batched"):
+        v = res[k]["cell_updates_per_s"]
+        res["bf16_over_" + k] = bf / v if v > 0 else None
     return res
 
 

@@ -554,8 +554,14 @@ static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* r
 static pd_status linear_range_check(pd_ctx* c, SkWS& w, double tol, int32_t* status, cudaStream_t s) {
     if (!status) return PD_OK;
     CUDA_TRY(c, sk_launch_rebuild_potentials(w, s));
-    float* row = reinterpret_cast<float*>(w.L64);          // [P][n] rows, then [P][n] columns (scratch)
-    float* col = row + (size_t)w.P * w.n;
+    // scratch for the exact marginals, [P][d*d+1] rows then columns: the four
+    // kernel-factor arrays (consecutive in the workspace, no longer needed; the
+    // exact finalize does not touch them -- it uses the FP64 scratch)
+    const size_t M = (size_t)w.dp * w.dp, n_out = (size_t)w.d * w.d + 1;
+    if (w.K2u != w.K1u + w.P * M || w.K1v != w.K2u + w.P * M || w.K2v != w.K1v + w.P * M)
+        return fail(c, PD_ERR_CUDA, "range check: workspace layout changed");
+    float* row = w.K1u;
+    float* col = row + (size_t)w.P * n_out;
     double* cost_scratch = w.Au;                             // P doubles of scratch
     { ProfScope ps(c, PD_K_FINALIZE, s);
       CUDA_TRY(c, sk_launch_lse_finalize(w, cost_scratch, row, col, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s)); }
@@ -623,12 +629,28 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         if (refine) rb.tol = std::max(prm->tol, 1e-4);
         { ProfScope ps(c, PD_K_LOGSTEP, s); CUDA_TRY(c, sk_launch_logstep(w, rb, s)); }
         CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), s));
+        const bool x2 = sk_bf16x2_applies(w);
+        if (x2 && P > 2) {
+            // two pairs per CTA: pair the batch largest support first, so that
+            // the two pairs of a CTA run for similar numbers of iterations
+            std::vector<int> ic((size_t)P * IC_N);
+            CUDA_TRY(c, cudaMemcpyAsync(ic.data(), w.ic, ic.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            std::vector<int> ord(P);
+            for (int p = 0; p < P; ++p) ord[p] = p;
+            auto sz = [&](int p) { return ic[(size_t)p * IC_N + IC_NA] + ic[(size_t)p * IC_N + IC_NB]; };
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return sz(a) > sz(b); });
+            CUDA_TRY(c, cudaMemcpyAsync(w.order_buf, ord.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            w.order = w.order_buf;
+        }
         const int max_rounds_b = prm->max_iter + 8;
         for (int round = 0; round < max_rounds_b; ++round) {
             { ProfScope ps(c, PD_K_ABSORB, s); CUDA_TRY(c, sk_launch_absorb(w, rb, s)); }
             CUDA_TRY(c, cudaMemsetAsync(counter, 0, sizeof(int), s));
             { ProfScope ps(c, PD_K_TC, s);
-              CUDA_TRY(c, sk_launch_iter_bf16(w, rb, rb.absorb_every, counter, c->dflag, s)); }
+              CUDA_TRY(c, x2 ? sk_launch_iter_bf16x2(w, rb, rb.absorb_every, counter, c->dflag, s)
+                             : sk_launch_iter_bf16(w, rb, rb.absorb_every, counter, c->dflag, s)); }
             CUDA_TRY(c, cudaMemcpyAsync(c->hflag, counter, sizeof(int), cudaMemcpyDeviceToHost, s));
             CUDA_TRY(c, cudaStreamSynchronize(s));
             if (c->hflag[0] == 0) break;
@@ -636,6 +658,7 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         CUDA_TRY(c, cudaMemcpyAsync(c->hflag + 1, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(c, cudaStreamSynchronize(s));
         if (c->hflag[1]) return fail(c, PD_ERR_TIMEOUT, "pd_sinkhorn_batch: a tensor-core wait timed out");
+        w.order = nullptr;
         // every pair (including ones that hit the range limit) continues in the exact engine
         { ProfScope ps(c, PD_K_ABSORB, s); CUDA_TRY(c, sk_launch_refine_prep(w, s)); }
         SkRun rr = r;
@@ -651,7 +674,7 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         // support set-up above is one launch for the batch), pairs one after
         // the other on the stream, the host reading each pair's state between
         // its iteration launches
-        const size_t n = (size_t)w.n;
+        const size_t n = (size_t)d * d + 1;   // caller's per-pair output length
         for (int p = 0; p < P; ++p) {
             SkWS v = ws_view(w, p);
             { ProfScope ps(c, PD_K_LOGSTEP, s); CUDA_TRY(c, sk_launch_logstep(v, r, s)); }

@@ -115,6 +115,11 @@ cudaError_t sk_launch_lse_iter(const SkWS& w, SkRun r, int n_inner, int* active_
 cudaError_t sk_launch_iter_bf16(const SkWS& w, SkRun r, int n_inner, int* active_count, int* error_flag,
                                 cudaStream_t s);
 cudaError_t sk_launch_refine_prep(const SkWS& w, cudaStream_t s);
+// PD_BF16 for dp = 64: two pairs per CTA, factors by TMA (sinkhorn_bf16x2.cu);
+// pairs are taken two by two in w.order (or index order)
+bool sk_bf16x2_applies(const SkWS& w);
+cudaError_t sk_launch_iter_bf16x2(const SkWS& w, SkRun r, int n_inner, int* active_count, int* error_flag,
+                                  cudaStream_t s);
 // potentials phi, psi from the linear-domain residual representation (pairs keep their status)
 cudaError_t sk_launch_rebuild_potentials(const SkWS& w, cudaStream_t s);
 // PD_OK pairs whose exact marginal error (row / col: [P][d*d+1] exact marginals) exceeds thr -> PD_ERR_RANGE

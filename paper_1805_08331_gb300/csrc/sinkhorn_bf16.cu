@@ -317,7 +317,7 @@ __global__ void sk_range_check_kernel(SkWS w, const float* __restrict__ row, con
     const int p = blockIdx.x;
     if (status[p] != 0) return;
     PairPtrs q = pair_ptrs(w, p);
-    const int d = w.d, dp = w.dp, n = w.n;
+    const int d = w.d, dp = w.dp, n = d * d + 1;   // marginal rows of d*d + 1 entries, Delta last
     const float* rp = row + (size_t)p * n;
     const float* cp = col + (size_t)p * n;
     double e = 0.0;
