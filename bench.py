@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--serve-inner", type=int, default=64, help="iterations per serving scheduling round")
     ap.add_argument("--no-compare", action="store_true", help="skip the engine comparison leg")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuning pass before the warm-up")
+    ap.add_argument("--compare-only", action="store_true",
+                    help="run only the engine comparison leg (print its JSON; for profiling)")
     ap.add_argument("--cta-threads", type=int, default=0, help="fix the iteration kernel's CTA width (0: automatic)")
     ap.add_argument("--compare-pairs", type=int, default=2048, help="pairs of the engine comparison workload")
     ap.add_argument("--compare-plain-sample", type=int, default=24,
@@ -564,19 +566,20 @@ def compare_leg(args, ctx):
     ctx.profile_enable(False)
     tc_ms, tc_n = prof.get("tc", (0.0, 0))
     tc_iters = float(np.minimum(out["iters"].cpu().numpy(), nfix).sum())
-    dpad = 128
-    executed = tc_iters * 8.0 * dpad ** 3
+    # d <= 64: two pairs share each 128 x 128 x 64 MMA GEMM (four per iteration)
+    executed = tc_iters * 4 * (2.0 * 128 * 128 * 64) / 2
     algorithmic = tc_iters * 8.0 * d ** 3
     peak = pk.get("bf16_tflops", 1900.0)
     res["tensor_core_kernel"] = {
-        "kernel": "sk_iter_bf16_kernel (tcgen05 kind::f16, BF16 operands, FP32 accumulation in TMEM)",
+        "kernel": "sk_iter_bf16x2_kernel (tcgen05 kind::f16, BF16 operands by TMA, FP32 accumulation in TMEM, "
+                  "two pairs per CTA)",
         "launches": int(tc_n), "ms": tc_ms, "pair_iterations": tc_iters,
         "executed_tflops": executed / (tc_ms / 1e3) / 1e12 if tc_ms else None,
         "algorithmic_tflops": algorithmic / (tc_ms / 1e3) / 1e12 if tc_ms else None,
         "peak_tflops": peak, "peak_source": f"{pk_kind} bf16_tflops (burst)",
         "executed_frac": executed / (tc_ms / 1e3) / 1e12 / peak if tc_ms else None,
-        "note": f"executed = 8 x {dpad}^3 flop per pair-iteration (four {dpad}x{dpad}x{dpad} MMA GEMMs, the grid "
-                f"zero-padded to {dpad}); algorithmic = 8 x d^3"}
+        "note": "executed = four 128x128x64 MMA GEMMs per iteration shared by two pairs (each pair's product is a "
+                "diagonal 64x64 block); algorithmic = 8 x d^3 flop per pair-iteration"}
     bf = res["bf16_tensor_core_refined"]["cell_updates_per_s"]
     for k in ("fp32_plain_one_pair_per_launch", "fp32_dense_batched", "fp32_log_domain_batched"):
         v = res[k]["cell_updates_per_s"]
@@ -654,11 +657,21 @@ def serve_leg(args, ctx):
     lat = np.array([r["latency_ms"] for r in done])
     dgrid = np.array([int(grid[i]) for i in range(nq) if results[i] is not None])
     per_d = {}
+    # points of a query's diagrams (the larger of A and, for a distance, B)
+    npts = np.array([max(counts[i], (qb[2][i + 1] - qb[2][i]) if kind[i] == 0 else 0)
+                     for i in range(nq) if results[i] is not None])
     for d in grids:
         ld = lat[dgrid == d]
         if len(ld):
             per_d[str(d)] = {"queries": int(len(ld)), "p50_ms": float(np.percentile(ld, 50)),
                              "p99_ms": float(np.percentile(ld, 99))}
+            small = lat[(dgrid == d) & (npts <= 1000)]
+            big = lat[(dgrid == d) & (npts > 1000)]
+            if len(small):
+                per_d[str(d)]["p99_ms_up_to_1000_points"] = float(np.percentile(small, 99))
+            if len(big):
+                per_d[str(d)]["p99_ms_over_1000_points"] = float(np.percentile(big, 99))
+                per_d[str(d)]["queries_over_1000_points"] = int(len(big))
     st = np.array([r["status"] for r in done])
     it = np.array([r["iters"] for r in done])
     return {"p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
@@ -677,6 +690,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.compare_only:
+        import torch
+        from paper_1805_08331_gb300 import api
+        api.load(build_if_missing=True)
+        ctx = api.Context(0)
+        print(json.dumps({"precision_comparison": compare_leg(args, ctx)}), flush=True)
+        ctx.close()
+        torch.cuda.synchronize()
+        return 0
     return run_ours(args)
 
 

@@ -554,13 +554,14 @@ static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* r
 static pd_status linear_range_check(pd_ctx* c, SkWS& w, double tol, int32_t* status, cudaStream_t s) {
     if (!status) return PD_OK;
     CUDA_TRY(c, sk_launch_rebuild_potentials(w, s));
-    // scratch for the exact marginals, [P][d*d+1] rows then columns: the four
-    // kernel-factor arrays (consecutive in the workspace, no longer needed; the
-    // exact finalize does not touch them -- it uses the FP64 scratch)
+    // scratch for the exact marginals, [P][d*d+1] rows then columns: the
+    // consecutive arrays K1v, K2v, ut, vt (4 P dp^2 floats), which the exact
+    // finalize never touches (its stage buffers are Wt, Rt, K1u, K2u and the
+    // FP64 scratch) and which are free once the potentials are rebuilt
     const size_t M = (size_t)w.dp * w.dp, n_out = (size_t)w.d * w.d + 1;
-    if (w.K2u != w.K1u + w.P * M || w.K1v != w.K2u + w.P * M || w.K2v != w.K1v + w.P * M)
+    if (w.K2v != w.K1v + w.P * M || w.ut != w.K2v + w.P * M || w.vt != w.ut + w.P * M)
         return fail(c, PD_ERR_CUDA, "range check: workspace layout changed");
-    float* row = w.K1u;
+    float* row = w.K1v;
     float* col = row + (size_t)w.P * n_out;
     double* cost_scratch = w.Au;                             // P doubles of scratch
     { ProfScope ps(c, PD_K_FINALIZE, s);
