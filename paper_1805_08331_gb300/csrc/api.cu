@@ -551,7 +551,7 @@ static pd_status lse_iterate(pd_ctx* c, SkWS& w, SkRun r, double* cost, float* r
 // log-domain marginals of each pair's final plan (potentials rebuilt from the
 // residual representation) are compared with a and b; a pair reported PD_OK
 // whose exact marginal error exceeds max(10 tol, 1e-5) gets PD_ERR_RANGE.
-static pd_status linear_range_check(pd_ctx* c, SkWS& w, double tol, int32_t* status, cudaStream_t s) {
+static pd_status linear_range_check(pd_ctx* c, SkWS& w, double tol, int32_t* status, float* err, cudaStream_t s) {
     if (!status) return PD_OK;
     CUDA_TRY(c, sk_launch_rebuild_potentials(w, s));
     // scratch for the exact marginals, [P][d*d+1] rows then columns: the
@@ -566,7 +566,7 @@ static pd_status linear_range_check(pd_ctx* c, SkWS& w, double tol, int32_t* sta
     double* cost_scratch = w.Au;                             // P doubles of scratch
     { ProfScope ps(c, PD_K_FINALIZE, s);
       CUDA_TRY(c, sk_launch_lse_finalize(w, cost_scratch, row, col, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s)); }
-    CUDA_TRY(c, sk_launch_range_check(w, row, col, status, std::max(10.0 * tol, 1e-5), s));
+    CUDA_TRY(c, sk_launch_range_check(w, row, col, status, err, std::max(10.0 * tol, 1e-5), s));
     return PD_OK;
 }
 
@@ -626,11 +626,14 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     if (prm->precision == PD_BF16) {
         // tensor-core phase to err <= max(tol, 1e-4) when refining, then exact FP32 refinement
         const bool refine = prm->refine_iters > 0;
+        const bool x2 = sk_bf16x2_applies(w);
         SkRun rb = r;
-        if (refine) rb.tol = std::max(prm->tol, 1e-4);
+        // the split-operand kernel (d <= 64) reaches the tolerance itself (a pair
+        // whose error stalls leaves for the refinement); the single-rounding
+        // kernel stops at 1e-4, its floor being near it
+        if (refine) rb.tol = x2 ? prm->tol : std::max(prm->tol, 1e-4);
         { ProfScope ps(c, PD_K_LOGSTEP, s); CUDA_TRY(c, sk_launch_logstep(w, rb, s)); }
         CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), s));
-        const bool x2 = sk_bf16x2_applies(w);
         if (x2 && P > 2) {
             // two pairs per CTA: pair the batch largest support first, so that
             // the two pairs of a CTA run for similar numbers of iterations
@@ -694,7 +697,7 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
                                              g ? g + p * n : nullptr, iters ? iters + p : nullptr,
                                              err ? err + p : nullptr, status ? status + p : nullptr, s)); }
         }
-        pd_status stc = linear_range_check(c, w, prm->tol, status, s);
+        pd_status stc = linear_range_check(c, w, prm->tol, status, err, s);
         if (stc != PD_OK) return stc;
         CUDA_TRY(c, cudaStreamSynchronize(s));
         return PD_OK;
@@ -711,7 +714,7 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     }
     { ProfScope ps(c, PD_K_ABSORB, s); CUDA_TRY(c, sk_launch_absorb(w, r, s)); }   // pairs that finished inside the log step
     { ProfScope ps(c, PD_K_FINALIZE, s); CUDA_TRY(c, sk_launch_finalize(w, cost, row_marg, col_marg, f, g, iters, err, status, s)); }
-    pd_status stc = linear_range_check(c, w, prm->tol, status, s);
+    pd_status stc = linear_range_check(c, w, prm->tol, status, err, s);
     if (stc != PD_OK) return stc;
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return PD_OK;

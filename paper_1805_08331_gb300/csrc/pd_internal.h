@@ -123,8 +123,8 @@ cudaError_t sk_launch_iter_bf16x2(const SkWS& w, SkRun r, int n_inner, int* acti
 // potentials phi, psi from the linear-domain residual representation (pairs keep their status)
 cudaError_t sk_launch_rebuild_potentials(const SkWS& w, cudaStream_t s);
 // PD_OK pairs whose exact marginal error (row / col: [P][d*d+1] exact marginals) exceeds thr -> PD_ERR_RANGE
-cudaError_t sk_launch_range_check(const SkWS& w, const float* row, const float* col, int32_t* status, double thr,
-                                  cudaStream_t s);
+cudaError_t sk_launch_range_check(const SkWS& w, const float* row, const float* col, int32_t* status, float* err,
+                                  double thr, cudaStream_t s);
 cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_count, int* big_count,
                                cudaStream_t s);
 // base-2 on-chip iteration kernel (sinkhorn_log2.cu)

@@ -312,7 +312,7 @@ cudaError_t sk_launch_rebuild_potentials(const SkWS& w, cudaStream_t s) {
 // mass) exceeds thr is reported PD_ERR_RANGE instead (its representation
 // dropped terms that matter).
 __global__ void sk_range_check_kernel(SkWS w, const float* __restrict__ row, const float* __restrict__ col,
-                                      int32_t* __restrict__ status, double thr) {
+                                      int32_t* __restrict__ status, float* __restrict__ err, double thr) {
     __shared__ double sh[32];
     const int p = blockIdx.x;
     if (status[p] != 0) return;
@@ -327,13 +327,16 @@ __global__ void sk_range_check_kernel(SkWS w, const float* __restrict__ row, con
     }
     if (threadIdx.x == 0) e += fabs((double)rp[n - 1] - q.sc[SC_AD]) + fabs((double)cp[n - 1] - q.sc[SC_BD]);
     e = block_sum(e, sh);
-    if (threadIdx.x == 0 && q.sc[SC_TOTAL] > 0 && !(e / q.sc[SC_TOTAL] <= thr)) status[p] = 8;   // PD_ERR_RANGE
+    if (threadIdx.x == 0 && q.sc[SC_TOTAL] > 0 && !(e / q.sc[SC_TOTAL] <= thr)) {
+        status[p] = 8;   // PD_ERR_RANGE; err reports the exact marginal error found
+        if (err) err[p] = (float)(e / q.sc[SC_TOTAL]);
+    }
 }
 
-cudaError_t sk_launch_range_check(const SkWS& w, const float* row, const float* col, int32_t* status, double thr,
-                                  cudaStream_t s) {
+cudaError_t sk_launch_range_check(const SkWS& w, const float* row, const float* col, int32_t* status, float* err,
+                                  double thr, cudaStream_t s) {
     if (w.P == 0 || !status) return cudaSuccess;
-    sk_range_check_kernel<<<w.P, 256, 0, s>>>(w, row, col, status, thr);
+    sk_range_check_kernel<<<w.P, 256, 0, s>>>(w, row, col, status, err, thr);
     return cudaGetLastError();
 }
 
