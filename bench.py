@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--parity-sample", type=int, default=4, help="pairs checked against the oracle")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (p50/p99) leg")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered queries/s (Poisson)")
-    ap.add_argument("--serve-seconds", type=float, default=5.0, help="length of the query stream")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of the query stream (60 s: the serving workload's length)")
     ap.add_argument("--serve-centroids", type=int, default=25, help="resident centroids per grid size")
     ap.add_argument("--serve-gamma", type=float, default=5e-3)
     ap.add_argument("--serve-tol", type=float, default=1e-4)

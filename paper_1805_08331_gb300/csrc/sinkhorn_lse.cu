@@ -428,6 +428,13 @@ __global__ void __launch_bounds__(T_CTA) sk_lse_finalize_kernel(SkWS w, double* 
                 if (go) go[(size_t)p * n_out + e] = gamma * (inb ? q.psi[c] : psip);
             }
         }
+        if (col_marg && (!go || pso)) {
+            // cells off the b-support were skipped above: their marginal is 0
+            for (int y = t; y < d * d; y += blockDim.x) {
+                const int c = (y / d) * dp + y % d;
+                if (!(q.bm[c] > 0.f)) col_marg[(size_t)p * n_out + y] = 0.f;
+            }
+        }
         if (t == 0) {
             double dd = (lAD > -INFINITY && lBD > -INFINITY) ? exp(lAD + phiD + lBD + psiD) : 0.0;
             if (col_marg) col_marg[(size_t)p * n_out + d * d] = (float)(rowD + dd);

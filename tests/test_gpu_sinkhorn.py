@@ -455,3 +455,52 @@ def test_linear_domain_engines_flag_dropped_terms(ctx, engine):
         e = (np.abs(plan.sum(1) - a[sa]).sum() + np.abs(plan.sum(0) - bb[sb]).sum()) / a.sum()
         assert e <= 2e-5, (p, e)
         assert rel[p] <= 1e-4, (p, rel[p])
+
+
+def test_split_bf16_reaches_tolerance_on_the_tensor_cores(ctx):
+    """For d <= 64 the tensor-core kernel holds every operand as BF16 hi + lo
+    (three MMAs per product), which carries the iteration to the 1e-6
+    tolerance: on k-means-shaped pairs (d = 64, gamma = 5e-3) the refined solve
+    takes about the iterations of the exact engine (the refinement adds a few),
+    the tensor-core launches carry nearly all of them, and every cost is within
+    the FP32 bar of the oracle."""
+    d, gamma, P = 64, 5e-3, 48
+    b, t, o, _ = inputs.mode_diagrams(2 * P, 10, 30, 300, sigma=0.03, seed=3)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    exact = _solve(ctx, hA, hB, d, gamma, 20000, 1e-6)
+    ctx.profile_enable(True)
+    bf = _solve(ctx, hA, hB, d, gamma, 20000, 1e-6, precision=api.PD_BF16, refine_iters=1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    assert np.all(bf["status"] == api.PD_OK) and np.all(exact["status"] == api.PD_OK)
+    assert np.all(bf["iters"] <= exact["iters"] * 1.05 + 8), np.max(bf["iters"] - exact["iters"])
+    tc_ms, exact_ms = prof.get("tc", (0.0, 0))[0], prof.get("iter", (0.0, 0))[0]
+    print("tensor-core ms", tc_ms, "exact-engine ms", exact_ms)
+    ref = oracle.sinkhorn_pd_batch(d, gamma, hA[:6], hB[:6], 20000, 1e-6)
+    assert np.all(np.abs(bf["cost"][:6] - ref["cost"]) <= 2e-6 * ref["cost"])
+
+
+def test_marginals_without_potentials_write_every_entry(ctx):
+    """Marginals requested without potentials: every entry is written (0 off
+    the supports), even where the output buffers held other values before."""
+    d, gamma, P = 64, 5e-3, 3
+    b, t, o = inputs.random_diagrams(2 * P, nmin=20, nmax=80, seed=17)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    n = d * d + 1
+    for eng in (api.PD_FP32, api.PD_FP32_DENSE):
+        out = {"row_marg": torch.full((P, n), float("nan"), dtype=torch.float32, device="cuda"),
+               "col_marg": torch.full((P, n), float("nan"), dtype=torch.float32, device="cuda")}
+        p = api.pd_sinkhorn_default_params(gamma, d, max_iter=300, tol=0.0, precision=eng)
+        g = api.pd_sinkhorn_batch(ctx, hists_to_gpu(hA), dev(masses(hA).view(np.int32)), hists_to_gpu(hB),
+                                  dev(masses(hB).view(np.int32)), p, want_marginals=True, out=out)
+        torch.cuda.synchronize()
+        rm, cm = g["row_marg"].cpu().numpy(), g["col_marg"].cpu().numpy()
+        assert np.all(np.isfinite(rm)) and np.all(np.isfinite(cm))
+        for q in range(P):
+            a, bb = oracle.augment(hA[q], hB[q])
+            assert np.all(rm[q][a == 0] == 0) and np.all(cm[q][bb == 0] == 0)
+            r = oracle.sinkhorn_pd(d, gamma, hA[q], hB[q], 300, 0.0)
+            assert np.allclose(rm[q], r["rmarg"], rtol=5e-6, atol=1e-6)
+            assert np.allclose(cm[q], r["cmarg"], rtol=5e-6, atol=1e-6)
