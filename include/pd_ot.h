@@ -96,7 +96,8 @@ typedef struct {
     int precision;     /* engine: PD_FP32, PD_BF16, PD_FP32_DENSE or PD_FP32_PLAIN (see above) */
     int refine_iters;  /* PD_BF16 only: FP32 iterations run after the BF16 phase stops (0 = none) */
     double absorb_tau; /* re-absorb when |log(u~/a)| or |log(v~/b)| exceeds this (<= 0: default 20) */
-    int absorb_every;  /* also re-absorb every this many iterations (<= 0: default 64) */
+    int absorb_every;  /* also re-absorb every this many iterations (<= 0: default 64; the PD_BF16 kernel
+                          for d <= 64, whose split operands keep their precision, uses at least 512) */
     double rel_log_thresh; /* a term counts as relevant to an output when it is within exp(rel_log_thresh)
                               of the output's sum; the absorbed representation keeps every relevant
                               term in range (>= 0: default, -21 for PD_FP32 and -14 for PD_BF16) */

@@ -632,6 +632,10 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         // whose error stalls leaves for the refinement); the single-rounding
         // kernel stops at 1e-4, its floor being near it
         if (refine) rb.tol = x2 ? prm->tol : std::max(prm->tol, 1e-4);
+        // the split operands keep precision between absorptions (a pair whose
+        // scalings leave the range is absorbed at once), so the two-pair kernel
+        // re-absorbs every 512 iterations at most: fewer host rounds
+        if (x2) rb.absorb_every = std::max(rb.absorb_every, 512);
         { ProfScope ps(c, PD_K_LOGSTEP, s); CUDA_TRY(c, sk_launch_logstep(w, rb, s)); }
         CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), s));
         if (x2 && P > 2) {
