@@ -283,19 +283,32 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
     // lane ln of the fixed L2_DLANES-lane partition is thread ln % NT (one pass
     // for NT >= L2_DLANES, two for 128 threads), so the per-warp partial sums
     // and their order are the same at every width
-#pragma unroll
-    for (int base = 0; base < L2_DLANES; base += (NT < L2_DLANES ? NT : L2_DLANES)) {
-        const int ln = base + t;
+    if constexpr (NT >= L2_DLANES) {
         float sD = 0.f;
-        if (doD && ln < L2_DLANES) {
-            for (int q = ln; q < in_n; q += L2_DLANES) {
+        if (doD && t < L2_DLANES) {
+            for (int q = t; q < in_n; q += L2_DLANES) {
                 const float2 h = in_hin[q];
                 const float2 c = cdt[abs((int)in_col[q] - (int)in_row[q])];
                 sD += l2_ex2(((h.x - c.x) - MsD) + (h.y - c.y));
             }
         }
         sD = warp_sum(sD);
-        if (lane == 0 && (ln >> 5) < L2_DLANES / 32) redD[ln >> 5] = sD;
+        if (lane == 0 && wid < L2_DLANES / 32) redD[wid] = sD;
+    } else {
+#pragma unroll
+        for (int base = 0; base < L2_DLANES; base += NT) {
+            const int ln = base + t;
+            float sD = 0.f;
+            if (doD) {
+                for (int q = ln; q < in_n; q += L2_DLANES) {
+                    const float2 h = in_hin[q];
+                    const float2 c = cdt[abs((int)in_col[q] - (int)in_row[q])];
+                    sD += l2_ex2(((h.x - c.x) - MsD) + (h.y - c.y));
+                }
+            }
+            sD = warp_sum(sD);
+            if (lane == 0) redD[ln >> 5] = sD;
+        }
     }
     __syncthreads();
     if (t == 0 && doD) {
@@ -491,7 +504,11 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
 // stopped or moved.  Once it reaches r.exit_at, the pairs still iterating
 // leave at their next 16-iteration check with their state saved (they stay
 // active and the host runs them on in wider CTAs).
-template <int NT, bool GM>
+// MULTI = false: one workspace, its descriptor is the kernel parameter w
+// (parameter-space reads, which the compiler can repeat instead of keeping
+// the pair's pointers in registers); MULTI = true: a launch over several
+// workspaces, the pair's descriptor copied from w.groups into shared memory.
+template <int NT, bool GM, bool MULTI>
 __global__ void __launch_bounds__(NT, (NT <= 128 ? 6 : (NT <= 256 ? 3 : (NT <= 512 ? 2 : 1))))
 sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t gcap, int gbits) {
     constexpr int NW = NT / 32;
@@ -506,8 +523,15 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     // workspaces (pairs of several grid sizes), to its workspace: code =
     // group << 24 | pair; the workspace descriptors are in device memory
     const int code = w.order ? w.order[blockIdx.x] : blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const SkWS& W = w.groups[w.ngroups > 1 ? (code >> 24) : 0];
-    const int p = w.ngroups > 1 ? (code & 0xFFFFFF) : code;
+    __shared__ SkWS Wsh;   // MULTI: the pair's workspace descriptor, copied once
+    if constexpr (MULTI) {
+        static_assert(sizeof(SkWS) % 4 == 0 && sizeof(SkWS) / 4 <= 128, "descriptor copy: one word per thread");
+        const int* src = reinterpret_cast<const int*>(w.groups + (code >> 24));
+        if (t < (int)(sizeof(SkWS) / 4)) reinterpret_cast<int*>(&Wsh)[t] = src[t];
+        __syncthreads();
+    }
+    const SkWS& W = MULTI ? Wsh : w;
+    const int p = MULTI ? (code & 0xFFFFFF) : code;
     PairPtrs q = pair_ptrs(W, p);
     if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG] != (GM ? 1 : 0)) return;
     const int d = W.d, dp = W.dp, nA = q.ic[IC_NA], nB = q.ic[IC_NB];
@@ -662,26 +686,34 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
         if (!isfinite(errf)) { status = ST_RANGE; break; }
         if (leave) break;   // status stays ST_ACTIVE: relaunched in a wider CTA
     }
-    // ---- store the potentials (FP64, natural units)
+    // ---- store the potentials (FP64, natural units); the pair's arrays come
+    // anew from the shared descriptor (not kept in registers across the loop)
     const double LN2 = 0.6931471805599453;
+    const size_t Nn = (size_t)W.n, Mm = (size_t)W.dp * W.dp;
+    double* s_phi = W.phi + p * Nn;
+    double* s_psi = W.psi + p * Nn;
+    const int* s_sa = W.sa + p * Mm;
+    const int* s_sb = W.sb + p * Mm;
+    double* s_sc = W.sc + (size_t)p * SC_N;
+    int* s_ic = W.ic + (size_t)p * IC_N;
     for (int s = 0; s < 2; ++s) {
         const L2Side& X = S[s];
-        double* pot = s == 0 ? q.phi : q.psi;
-        const int* list = s == 0 ? q.sa : q.sb;
+        double* pot = s == 0 ? s_phi : s_psi;
+        const int* list = s == 0 ? s_sa : s_sb;
         const float2* xpot = sdp<float2, GM>(gb, X.pot);
         for (int e = t; e < X.n; e += NT) pot[list[e]] = ((double)xpot[e].x + (double)xpot[e].y) * LN2;
-        if (t == 0) pot[W.n - 1] = ((double)X.potD.x + (double)X.potD.y) * LN2;
+        if (t == 0) pot[Nn - 1] = ((double)X.potD.x + (double)X.potD.y) * LN2;
     }
     if (t == 0) {
-        q.sc[SC_ERR] = (double)errf;
-        q.ic[IC_ITERS] = iters;
+        s_sc[SC_ERR] = (double)errf;
+        s_ic[IC_ITERS] = iters;
         if (moved) {
             // the exact-range guard tripped: the FP64 global-memory kernel takes the pair over
-            q.ic[IC_BIG] = 2;
+            s_ic[IC_BIG] = 2;
             atomicAdd(&counter[3], 1);
             atomicAdd(&counter[0], 1);
         } else {
-            q.ic[IC_STATUS] = status;
+            s_ic[IC_STATUS] = status;
             if (status == ST_ACTIVE) atomicAdd(&counter[0], 1);
         }
         if (can_leave && (moved || status != ST_ACTIVE)) atomicAdd(&counter[4], 1);
@@ -731,20 +763,26 @@ size_t sk_lse2_smem_cap() {
     return (size_t)cap - 1024;   // static shared memory of the kernel
 }
 
-template <int NT, bool GM>
-static cudaError_t launch_lse2(const SkWS& w, SkRun r, int n_inner, int* counter, size_t smem, size_t gcap, int gbits,
-                               cudaStream_t s) {
+template <int NT, bool GM, bool MULTI>
+static cudaError_t launch_lse2_v(const SkWS& w, SkRun r, int n_inner, int* counter, size_t smem, size_t gcap,
+                                 int gbits, cudaStream_t s) {
     static std::atomic<size_t> configured{0};
     const size_t cap = sk_lse2_smem_cap();
     if (configured != cap) {
-        cudaError_t e = cudaFuncSetAttribute(sk_lse2_kernel<NT, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)cap);
+        cudaError_t e = cudaFuncSetAttribute(sk_lse2_kernel<NT, GM, MULTI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
         if (e != cudaSuccess) return e;
         configured = cap;
     }
     if (smem > cap) smem = cap;
-    sk_lse2_kernel<NT, GM><<<w.P, NT, smem, s>>>(w, r, n_inner, counter, (int)smem, gcap, gbits);
+    sk_lse2_kernel<NT, GM, MULTI><<<w.P, NT, smem, s>>>(w, r, n_inner, counter, (int)smem, gcap, gbits);
     return cudaGetLastError();
+}
+template <int NT, bool GM>
+static cudaError_t launch_lse2(const SkWS& w, SkRun r, int n_inner, int* counter, size_t smem, size_t gcap, int gbits,
+                               cudaStream_t s) {
+    if (!GM && w.ngroups > 1) return launch_lse2_v<NT, false, true>(w, r, n_inner, counter, smem, gcap, gbits, s);
+    return launch_lse2_v<NT, GM, false>(w, r, n_inner, counter, smem, gcap, gbits, s);
 }
 
 cudaError_t sk_launch_lse2(const SkWS& w, SkRun r, int n_inner, int* counter, size_t smem, int gbits, int threads,
