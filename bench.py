@@ -541,11 +541,26 @@ def compare_leg(args, ctx):
         ms = float(np.mean(times))
         it = out["iters"].cpu().numpy()
         st = out["status"].cpu().numpy()
-        c = out["cost"].cpu().numpy()[:ns]
+        m = min(ns, npairs)
+        c = out["cost"].cpu().numpy()[:m]
         ok = st == api.PD_OK
         return {"pairs": npairs, "ms": ms, "cell_updates_per_s": float(it[ok].sum()) * cells_per_iter / (ms / 1e3),
                 "iterations": int(it.sum()), "status_counts": {str(int(x)): int((st == x).sum()) for x in np.unique(st)},
-                "max_rel_cost_err_vs_fp64_sample": float(np.max(np.abs(c - ref) / ref))}
+                "max_rel_cost_err_vs_fp64_sample": float(np.max(np.abs(c - ref[:m]) / ref[:m]))}
+
+    def by_class(precision, **kw):
+        """Kernel time per launch class of one profiled solve (the library's CUDA-event profiler)."""
+        prm = api.pd_sinkhorn_default_params(gamma, d, max_iter=20000, tol=tol, precision=precision, **kw)
+        torch.cuda.synchronize()
+        ctx.profile_enable(True)
+        t0 = time.perf_counter()
+        api.pd_sinkhorn_batch(ctx, hist, mass, hist, mass, prm, pairs=pairs)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) * 1e3
+        prof = ctx.profile_read()
+        ctx.profile_enable(False)
+        return {"wall_ms": wall, "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
+                "launches": {k: int(v[1]) for k, v in prof.items()}}
 
     res = {"workload": f"{P} pairs of 10-mode diagrams (30-300 points, sigma 0.03), d={d}, gamma={gamma:g}, "
                        f"stop at relative marginal error {tol:g}; oracle sample: pairs 0-{ns - 1}",
@@ -553,6 +568,8 @@ def compare_leg(args, ctx):
            "fp32_plain_one_pair_per_launch": run(api.PD_FP32_PLAIN, min(args.compare_plain_sample, P), 0),
            "fp32_dense_batched": run(api.PD_FP32_DENSE, P, 1),
            "fp32_log_domain_batched": run(api.PD_FP32, P, 2)}
+    res["bf16_tensor_core_refined"]["breakdown"] = by_class(api.PD_BF16, refine_iters=1)
+    res["fp32_log_domain_batched"]["breakdown"] = by_class(api.PD_FP32)
     # tensor-core kernel alone: fixed 256 BF16 iterations, no stop, profiled
     pk, pk_kind = peaks()
     nfix = 256
