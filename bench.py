@@ -166,10 +166,10 @@ def fp32_peak_tflops(sm_mhz):
 
 # DRAM bytes (read + write) of the base-2 iteration kernel per pair and
 # launch, from one ncu capture (512 pairs of this workload, one launch:
-# 54.43 MB read + 0.33 MB written).  The kernel keeps every pair's state on
+# 54.38 MB read + 0.30 MB written).  The kernel keeps every pair's state on
 # chip; these bytes are the launch's load and store of the potentials, weights
 # and support lists, whatever the number of iterations.
-LSE2_DRAM_BYTES_PER_PAIR_LAUNCH = (54.430976e6 + 0.329472e6) / 512
+LSE2_DRAM_BYTES_PER_PAIR_LAUNCH = (54.381824e6 + 0.298496e6) / 512
 
 
 def mufu_peak_gexp(sm_mhz):
