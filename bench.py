@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--compare-only", action="store_true",
                     help="run only the engine comparison leg (print its JSON; for profiling)")
     ap.add_argument("--cta-threads", type=int, default=0, help="fix the iteration kernel's CTA width (0: automatic)")
+    ap.add_argument("--eps-stages", type=int, default=0,
+                    help="gamma-continuation stages before the target gamma (0: plain Sinkhorn, Alg. 1)")
     ap.add_argument("--compare-pairs", type=int, default=2048, help="pairs of the engine comparison workload")
     ap.add_argument("--compare-plain-sample", type=int, default=24,
                     help="pairs timed with the one-pair-per-launch FP32 engine")
@@ -86,7 +88,8 @@ def config_dict(args, precision):
                         f"death=min(1,birth+Exp(0.2)); d={args.d}; gamma={args.gamma:g} log-stabilised; "
                         f"stop at relative marginal L1 error {args.tol:g}",
             "pairs_per_gpu": args.pairs, "d": args.d, "gamma": args.gamma, "tol": args.tol,
-            "precision": precision, "l2": "flushed (512 MiB write) before every timed step"}
+            "precision": precision, "eps_stages": args.eps_stages,
+            "l2": "flushed (512 MiB write) before every timed step"}
 
 
 # --------------------------------------------------------------------------- clocks
@@ -320,7 +323,8 @@ def run_ours(args):
     b, t, o = workload(args, rank)
     d, P = args.d, args.pairs
     params = api.pd_sinkhorn_default_params(args.gamma, d, max_iter=args.max_iter, tol=args.tol,
-                                            precision=precision, cta_threads=args.cta_threads)
+                                            precision=precision, cta_threads=args.cta_threads,
+                                            eps_stages=args.eps_stages)
     db, dt_, do = torch.from_numpy(b).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(o).cuda()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()

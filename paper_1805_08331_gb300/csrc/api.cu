@@ -514,8 +514,20 @@ static pd_status lse_solve(pd_ctx* c, SkWS& w, SkRun r, const double* g_init, do
                            float* col_marg, double* f, double* g, int32_t* iters, float* err, int32_t* status,
                            int* counter, cudaStream_t s) {
     { ProfScope ps(c, PD_K_SETUP, s); CUDA_TRY(c, sk_launch_setup(w, g_init, s)); }
+    if (r.eps_stages > 0 && sk_lse2_grid_bits(w.gamma) >= 0) {
+        // gamma-continuation inside the iteration kernel: every pair starts at
+        // gamma * 4^K and moves to the next stage on its own once its error is
+        // <= max(tol, 1e-4) (no batch-wide barrier between stages); warm-start
+        // potentials are brought to the first stage's units
+        CUDA_TRY(c, sk_launch_set_stage(w, r.eps_stages, s));
+        CUDA_TRY(c, sk_launch_regamma(w, std::ldexp(1.0, -2 * r.eps_stages), r.max_iter, s));
+        r.kstages = r.eps_stages;
+        r.stage_tol = std::max(r.tol, 1e-4);
+        return lse_iterate(c, w, r, cost, row_marg, col_marg, f, g, iters, err, status, counter, s);
+    }
     if (r.eps_stages > 0) {
-        // gamma-continuation: stages at gamma * 4^k, k = eps_stages..1, each to
+        // gamma below the base-2 kernel's range: stages run one after the other
+        // (batch-wide), at gamma * 4^k, k = eps_stages..1, each to
         // err <= max(tol, 1e-4), carrying f and g (phi = f / gamma is rescaled)
         const double g_target = w.gamma;
         double g_prev = g_target;

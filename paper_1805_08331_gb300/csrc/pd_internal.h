@@ -29,6 +29,7 @@ enum {
     IC_RANGE,    // consecutive range failures
     IC_SINCE,    // iterations since the last absorption
     IC_BIG,      // 1 = supports too large for the on-chip log-domain kernel
+    IC_STAGE,    // gamma-continuation inside the base-2 kernel: current stage k (gamma * 4^k)
     IC_N
 };
 enum { ST_ACTIVE = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_RANGE = 3, ST_INVALID = 4 };
@@ -99,6 +100,11 @@ struct SkRun {
     int tier;             // 0 automatic, 1 global-memory variant, 2 FP64 kernel for every pair
     int max_inner;        // iterations per launch at most (0: run to the stop)
     int diag_tc_timeout;  // tensor-core kernel: skip the first GEMM issue, wait with a spin limit of 0
+    // base-2 kernel: gamma-continuation inside the launch (0: off); each pair
+    // starts at stage ic[IC_STAGE] (gamma * 4^k) and moves to the next stage
+    // once its error is <= stage_tol
+    int kstages;
+    double stage_tol;
 };
 
 cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s);
@@ -129,6 +135,8 @@ cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_
                                cudaStream_t s);
 // base-2 on-chip iteration kernel (sinkhorn_log2.cu)
 int sk_lse2_grid_bits(double gamma);
+// gamma-continuation inside the iteration kernel: ic[IC_STAGE] = K for every pair
+cudaError_t sk_launch_set_stage(const SkWS& w, int K, cudaStream_t s);
 cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, cudaStream_t s);
 // counter: [0] active pairs, [1] pairs moved to the global-memory variant,
 // [2] (need kernel) max shared bytes, [3] pairs moved to the FP64 kernel.

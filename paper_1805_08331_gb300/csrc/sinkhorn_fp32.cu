@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(T_CTA) sk_setup_kernel(SkWS w, const double* _
         q.sc[SC_FD] = 0; q.sc[SC_GD] = 0; q.sc[SC_UTD] = 0; q.sc[SC_VTD] = 0; q.sc[SC_DD] = 0;
         q.sc[SC_AD] = nB; q.sc[SC_BD] = nA; q.sc[SC_TOTAL] = nA + nB; q.sc[SC_ERR] = INFINITY;
         q.ic[IC_ITERS] = 0; q.ic[IC_ABSORB] = 1; q.ic[IC_FROMLIN] = 0; q.ic[IC_RANGE] = 0; q.ic[IC_BIG] = 0;
+        q.ic[IC_STAGE] = 0;
         int st = ST_ACTIVE;
         if ((!rA && sA != nA) || (!rB && sB != nB)) st = ST_INVALID;
         else if (nA + nB == 0) { st = ST_CONVERGED; q.sc[SC_ERR] = 0; }

@@ -204,6 +204,21 @@ static __device__ __forceinline__ void l2_sort_rows(short* rows, int nr, const i
     __syncthreads();
 }
 
+// Cost tables in log2 units, (grid, rest) split: ct[m] = c_(m-(d-1))/gamma for
+// the grid axis, cdt[m] = cD_m/gamma for the diagonal bin, at this gamma.
+template <int NT>
+__device__ void l2_tables(float2* ct, float2* cdt, int d, double gamma, double pw, double gsc) {
+    const double LOG2E = 1.4426950408889634;
+    const double sc2 = LOG2E / (gamma * (double)d * (double)d);
+    const int t = threadIdx.x;
+    for (int m = t; m < 2 * d - 1; m += NT) {
+        const double z = (double)(m - (d - 1));
+        ct[m] = l2_split(pw == 2.0 ? z * z * sc2 : pd_c1p(m, d - 1, d, pw) * (LOG2E / gamma), gsc);
+    }
+    for (int m = t; m < d; m += NT)
+        cdt[m] = l2_split(pw == 2.0 ? 0.5 * (double)m * (double)m * sc2 : pd_cdiagp(0, m, d, pw) * (LOG2E / gamma), gsc);
+}
+
 struct L2Consts {
     uint32_t ct;     // float2 [2d-1] c_m/gamma in log2 units (hi, lo), m = (i - k) + d - 1
     uint32_t cdt;    // float2 [d] cD_m/gamma in log2 units, m = |j - i|
@@ -494,6 +509,43 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
     if (out_nch == 0) __syncthreads();
 }
 
+// gamma-continuation step inside the launch: gamma -> gamma / 4.  Potentials
+// in log2 units of the new gamma are 4x the old ones: 4 hi is exact on the grid,
+// 4 lo is re-split; h = log2 weight + potential follows; the cost tables are
+// rebuilt for the new gamma.  Sets *range_flag if a potential leaves the exact
+// range (the pair then moves to the FP64 kernel).
+template <int NT, bool GM>
+static __device__ void l2_next_stage(L2Side* S, const L2Consts& K, double gamma_new, double pw, int d,
+                                     int* range_flag, unsigned char* gb) {
+    const int t = threadIdx.x;
+    for (int s = 0; s < 2; ++s) {
+        L2Side& X = S[s];
+        float2* xpot = sdp<float2, GM>(gb, X.pot);
+        float2* xhin = sdp<float2, GM>(gb, X.hin);
+        const float2* xlw = sdp<float2, GM>(gb, X.lw);
+        for (int e = t; e < X.n; e += NT) {
+            const float2 po = xpot[e];
+            const float v = po.y * 4.f, rv = l2_round(v, K.gsc, K.ginv);
+            const float2 pn = make_float2(po.x * 4.f + rv, v - rv);
+            if (!(fabsf(pn.x) < K.lim)) atomicOr(range_flag, 1);
+            xpot[e] = pn;
+            xhin[e] = make_float2(xlw[e].x + pn.x, xlw[e].y + pn.y);
+        }
+    }
+    __syncthreads();   // every thread has read the sides' Delta state (hinD in the half-steps) before t == 0 writes it
+    if (t == 0) {
+        for (int s = 0; s < 2; ++s) {
+            L2Side& X = S[s];
+            const float v = X.potD.y * 4.f, rv = l2_round(v, K.gsc, K.ginv);
+            X.potD = make_float2(X.potD.x * 4.f + rv, v - rv);
+            if (!(fabsf(X.potD.x) < K.lim)) atomicOr(range_flag, 1);
+            X.hinD = X.wD > 0.f ? make_float2(X.lwD.x + X.potD.x, X.lwD.y + X.potD.y) : make_float2(-INFINITY, 0.f);
+        }
+    }
+    l2_tables<NT>(smp<float2>(K.ct), smp<float2>(K.cdt), d, gamma_new, pw, (double)K.gsc);
+    __syncthreads();
+}
+
 // GM = false: pairs with IC_BIG == 0, everything on chip; a pair that does
 // not fit moves to IC_BIG = 1.  GM = true: pairs with IC_BIG == 1, per-side
 // arrays in the pair's FP64 scratch L64 (gcap bytes); a pair whose arrays
@@ -535,6 +587,9 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     PairPtrs q = pair_ptrs(W, p);
     if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG] != (GM ? 1 : 0)) return;
     const int d = W.d, dp = W.dp, nA = q.ic[IC_NA], nB = q.ic[IC_NB];
+    // gamma-continuation inside the launch: this pair's stage and gamma
+    int stage = r.kstages > 0 ? q.ic[IC_STAGE] : 0;
+    const double gamma_k = ldexp(W.gamma, 2 * stage);
     l2_compact(q.rpa, d, nullptr, &cnt[0], nullptr, wcnt);
     l2_compact(q.rpb, d, nullptr, &cnt[1], nullptr, wcnt);
     const int nrA = cnt[0], nrB = cnt[1];
@@ -547,6 +602,14 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     }
     __syncthreads();
     if (!fits) {
+        if (GM && stage > 0) {
+            // to the FP64 kernel, which runs the target gamma only: potentials
+            // in the target's units (f / gamma = 4^stage f / gamma_k)
+            const double sc = ldexp(1.0, 2 * stage);
+            for (int e = t; e < nA; e += NT) q.phi[q.sa[e]] *= sc;
+            for (int e = t; e < nB; e += NT) q.psi[q.sb[e]] *= sc;
+            if (t == 0) { q.phi[W.n - 1] *= sc; q.psi[W.n - 1] *= sc; q.ic[IC_STAGE] = 0; }
+        }
         if (t == 0) {
             q.ic[IC_BIG] = GM ? 2 : 1;
             atomicAdd(&counter[GM ? 3 : 1], 1);
@@ -637,18 +700,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
             __syncthreads();
         }
     }
-    {
-        const double sc2 = LOG2E / (W.gamma * (double)d * (double)d);
-        float2* ct = smp<float2>(K.ct);
-        float2* cdt = smp<float2>(K.cdt);
-        for (int m = t; m < 2 * d - 1; m += NT) {
-            const double z = (double)(m - (d - 1));
-            ct[m] = l2_split(W.p == 2.0 ? z * z * sc2 : pd_c1p(m, d - 1, d, W.p) * (LOG2E / W.gamma), gsc);
-        }
-        for (int m = t; m < d; m += NT)
-            cdt[m] = l2_split(W.p == 2.0 ? 0.5 * (double)m * (double)m * sc2 : pd_cdiagp(0, m, d, W.p) * (LOG2E / W.gamma),
-                              gsc);
-    }
+    l2_tables<NT>(smp<float2>(K.ct), smp<float2>(K.cdt), d, gamma_k, W.p, gsc);
     if (t == 0) range_flag = 0;
     __syncthreads();
     l2_chunks<GM>(S[0], wcnt, gb);
@@ -657,7 +709,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     K.gsc = (float)gsc; K.ginv = (float)(1.0 / gsc);
     K.lim = (float)ldexp(1.0, 21 - gbits);   // |potential| bound keeping every sum of grid words exact
     K.escale = q.sc[SC_TOTAL] > 0 ? (float)(ldexp(1.0, 40) / q.sc[SC_TOTAL]) : 0.f;
-    const float tolf = (float)r.tol;
+    const float tolf = (float)r.tol, stage_tolf = (float)r.stage_tol;
     int iters = q.ic[IC_ITERS];
     float errf = (float)q.sc[SC_ERR];
     int status = ST_ACTIVE;
@@ -681,9 +733,16 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
         errf = bad ? INFINITY : (float)((double)e * 0x1p-40);
         ++iters;
         if (range_flag) { moved = true; break; }
-        if (r.tol > 0 && errf <= tolf) { status = ST_CONVERGED; break; }
+        // a coarse stage that reached its tolerance moves on (never "converged")
+        const bool stage_done = stage > 0 && errf <= stage_tolf;
+        if (!stage_done && r.tol > 0 && errf <= tolf) { status = ST_CONVERGED; break; }
         if (iters >= r.max_iter) { status = ST_MAXITER; break; }
         if (!isfinite(errf)) { status = ST_RANGE; break; }
+        if (stage_done) {
+            --stage;
+            l2_next_stage<NT, GM>(S, K, ldexp(W.gamma, 2 * stage), W.p, d, &range_flag, gb);
+            if (range_flag) { moved = true; break; }
+        }
         if (leave) break;   // status stays ST_ACTIVE: relaunched in a wider CTA
     }
     // ---- store the potentials (FP64, natural units); the pair's arrays come
@@ -696,14 +755,19 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     const int* s_sb = W.sb + p * Mm;
     double* s_sc = W.sc + (size_t)p * SC_N;
     int* s_ic = W.ic + (size_t)p * IC_N;
+    // a pair handed on to a wider CTA keeps its stage; one that stops (or moves
+    // to the FP64 kernel) is stored in the target gamma's units
+    const bool keep_stage = status == ST_ACTIVE && !moved;
+    const double units = LN2 * (keep_stage ? 1.0 : ldexp(1.0, 2 * stage));
     for (int s = 0; s < 2; ++s) {
         const L2Side& X = S[s];
         double* pot = s == 0 ? s_phi : s_psi;
         const int* list = s == 0 ? s_sa : s_sb;
         const float2* xpot = sdp<float2, GM>(gb, X.pot);
-        for (int e = t; e < X.n; e += NT) pot[list[e]] = ((double)xpot[e].x + (double)xpot[e].y) * LN2;
-        if (t == 0) pot[Nn - 1] = ((double)X.potD.x + (double)X.potD.y) * LN2;
+        for (int e = t; e < X.n; e += NT) pot[list[e]] = ((double)xpot[e].x + (double)xpot[e].y) * units;
+        if (t == 0) pot[Nn - 1] = ((double)X.potD.x + (double)X.potD.y) * units;
     }
+    if (t == 0 && r.kstages > 0) s_ic[IC_STAGE] = keep_stage ? stage : 0;
     if (t == 0) {
         s_sc[SC_ERR] = (double)errf;
         s_ic[IC_ITERS] = iters;
@@ -718,6 +782,18 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
         }
         if (can_leave && (moved || status != ST_ACTIVE)) atomicAdd(&counter[4], 1);
     }
+}
+
+// gamma-continuation inside the iteration kernel: every pair starts at stage K.
+__global__ void sk_set_stage_kernel(SkWS w, int K) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < w.P) w.ic[(size_t)p * IC_N + IC_STAGE] = K;
+}
+
+cudaError_t sk_launch_set_stage(const SkWS& w, int K, cudaStream_t s) {
+    if (w.P == 0) return cudaSuccess;
+    sk_set_stage_kernel<<<(w.P + 255) / 256, 256, 0, s>>>(w, K);
+    return cudaGetLastError();
 }
 
 // Maximum shared-memory need over the active on-chip pairs (one thread per pair).
