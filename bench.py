@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--compare-only", action="store_true",
                     help="run only the engine comparison leg (print its JSON; for profiling)")
     ap.add_argument("--cta-threads", type=int, default=0, help="fix the iteration kernel's CTA width (0: automatic)")
+    ap.add_argument("--lse-form", type=int, default=0,
+                    help="log-sum-exp form of the iteration kernel: 0 automatic per half-step, 1 separable, "
+                         "2 pairwise over the supports")
     ap.add_argument("--eps-stages", type=int, default=0,
                     help="gamma-continuation stages before the target gamma (0: plain Sinkhorn, Alg. 1)")
     ap.add_argument("--compare-pairs", type=int, default=2048, help="pairs of the engine comparison workload")
@@ -88,7 +91,7 @@ def config_dict(args, precision):
                         f"death=min(1,birth+Exp(0.2)); d={args.d}; gamma={args.gamma:g} log-stabilised; "
                         f"stop at relative marginal L1 error {args.tol:g}",
             "pairs_per_gpu": args.pairs, "d": args.d, "gamma": args.gamma, "tol": args.tol,
-            "precision": precision, "eps_stages": args.eps_stages,
+            "precision": precision, "eps_stages": args.eps_stages, "lse_form": args.lse_form,
             "l2": "flushed (512 MiB write) before every timed step"}
 
 
@@ -180,19 +183,30 @@ def mufu_peak_gexp(sm_mhz):
     return num_sms() * MUFU_PER_SM * sm_mhz * 1e6 / 1e9
 
 
-def lse_terms_per_iteration(hist, pairs, d):
+PW_RATIO = 2   # the iteration kernel's form rule (pairwise while <= 2x the separable terms)
+
+
+def lse_terms_per_iteration(hist, pairs, d, form=0, p2=True):
     """Log-sum-exp terms (one exponential each) of one iteration of the
-    log-domain engine for every pair: for each half-step, stage 1 has
-    nnz(in) x |columns of out| terms, stage 2 nnz(out) x |rows of in|, plus the
-    Delta terms."""
+    log-domain engine for every pair, in the form each half-step takes:
+    separable = stage 1 nnz(in) x |columns of out| + stage 2 nnz(out) x |rows
+    of in|; pairwise (p = 2) = nnz(in) x nnz(out); plus the Delta terms.
+    Returns (terms of the forms taken, terms of the separable form)."""
     nz = hist.reshape(hist.shape[0], d, d) > 0
-    nnz = nz.reshape(nz.shape[0], -1).sum(1)
+    nnz = nz.reshape(nz.shape[0], -1).sum(1).astype(np.float64)
     rows = nz.any(2).sum(1)
     cols = nz.any(1).sum(1)
     a, b = pairs[:, 0], pairs[:, 1]
-    u = nnz[b] * cols[a] + nnz[a] * rows[b] + nnz[a] + nnz[b] + 1
-    v = nnz[a] * cols[b] + nnz[b] * rows[a] + nnz[b] + nnz[a] + 1
-    return (u + v).astype(np.float64)
+    taken = np.zeros(len(a))
+    sep_all = np.zeros(len(a))
+    for o, i in ((a, b), (b, a)):   # u-update (out A, in B), v-update (out B, in A)
+        sep = nnz[i] * cols[o] + rows[i] * nnz[o]
+        direct = nnz[i] * nnz[o]
+        pw = np.full(len(a), p2 and form == 2) | ((form == 0) & p2 & (direct <= PW_RATIO * sep))
+        delta = nnz[o] + nnz[i] + 1
+        taken += np.where(pw, direct, sep) + delta
+        sep_all += sep + delta
+    return taken, sep_all
 
 
 # --------------------------------------------------------------------------- distributed helpers
@@ -324,7 +338,7 @@ def run_ours(args):
     d, P = args.d, args.pairs
     params = api.pd_sinkhorn_default_params(args.gamma, d, max_iter=args.max_iter, tol=args.tol,
                                             precision=precision, cta_threads=args.cta_threads,
-                                            eps_stages=args.eps_stages)
+                                            eps_stages=args.eps_stages, lse_form=args.lse_form)
     db, dt_, do = torch.from_numpy(b).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(o).cuda()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -347,7 +361,7 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     hist0, _ = api.pd_rasterize(ctx, db, dt_, do, d)
-    terms = lse_terms_per_iteration(hist0.cpu().numpy(), pairs.cpu().numpy(), d)
+    terms, terms_sep = lse_terms_per_iteration(hist0.cpu().numpy(), pairs.cpu().numpy(), d, args.lse_form)
     barrier(ws)
     clocks = ClockSampler(local)
     clocks.start()
@@ -358,6 +372,7 @@ def run_ours(args):
     iters_in_iter_kernel = 0
     pair_launches = 0.0
     lse_terms = 0.0
+    lse_terms_sep = 0.0
     outs = None
     torch.cuda.synchronize()
     barrier(ws)
@@ -376,6 +391,7 @@ def run_ours(args):
         cells_all += float(it.sum()) * 2 * (d * d + 1)
         iters_in_iter_kernel += int(np.maximum(it - 1, 0).sum())
         lse_terms += float((it * terms).sum())
+        lse_terms_sep += float((it * terms_sep).sum())
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop()
@@ -428,9 +444,10 @@ def run_ours(args):
         src = f"{pk_kind} sm_max_mhz x {num_sms()} SMs x 128 FP32 lanes x 2"
     else:
         peak = mufu_peak_gexp(pk.get("sm_max_mhz", 2070.0))
-        bound, unit, kname = "alu", "Gexp/s", "sk_lse2_kernel (on-chip base-2 log-domain separable Sinkhorn)"
+        bound, unit, kname = "alu", "Gexp/s", "sk_lse2_kernel (on-chip base-2 log-domain Sinkhorn)"
         achieved = lse_terms / (iter_ms / 1e3) / 1e9 if iter_ms > 0 else 0.0
-        src = f"{pk_kind} sm_max_mhz x {num_sms()} SMs x 16 MUFU ex2/clk (one exponential per log-sum-exp term)"
+        src = (f"{pk_kind} sm_max_mhz x {num_sms()} SMs x 16 MUFU ex2/clk (one exponential per log-sum-exp "
+               f"term of the form each half-step takes)")
     traffic = None
     if precision == api.PD_FP32 and iter_launches:
         # pair loads: the first launch of a step loads every pair; the
@@ -452,6 +469,11 @@ def run_ours(args):
             "frac": achieved / peak if peak else None, "traffic": traffic, "kernel": kname, "peak_source": src,
             "launches": iter_launches, "kernel_ms": iter_ms,
             "share_of_step": iter_ms / my_ms if my_ms else None, "tensor_unit": tensor_unit}
+    if precision == api.PD_FP32:
+        roof["terms"] = {"taken": lse_terms, "separable": lse_terms_sep, "lse_form": args.lse_form,
+                         "separable_equivalent_gexp_per_s": lse_terms_sep / (iter_ms / 1e3) / 1e9 if iter_ms else None,
+                         "note": "terms of all timed steps; achieved counts the terms the kernel evaluates "
+                                 "(pairwise n_in x n_out where the form rule takes it)"}
     launches = int(sum(n for _, n in prof.values()))
 
     # ---- parity sample and CPU baseline (rank 0 only)

@@ -129,6 +129,13 @@ typedef struct {
                           is not issued and the wait for it has a spin limit of 0, so the wait gives up at once
                           with no tensor-core work in flight; the kernel frees its tensor memory and the call
                           returns PD_ERR_TIMEOUT (the context stays usable).  0 (default) = off */
+    int lse_form;      /* PD_FP32 iteration kernel (on chip), form of each half-step's log-sum-exp (Prop. 1
+                          restricted to the supports): 1 = separable (stage 1 over the input's cells and the
+                          output's columns, stage 2 over the input's rows and the output's cells); 2 = pairwise
+                          over the two supports, c_xy = |x - y|^2 / d^2 computed exactly per term, wherever
+                          p = 2; 0 (default) = per half-step, pairwise while it has at most twice the separable
+                          form's terms (p = 2), else separable.  Both forms are exact sums of the same terms in
+                          FP32; results agree within rounding */
 } pd_sinkhorn_params;
 
 /* Fill *p with defaults for (gamma, d): max_iter 20000, tol 1e-6, PD_FP32,

@@ -49,7 +49,7 @@ class SinkhornParams(ctypes.Structure):
                 ("absorb_tau", ctypes.c_double), ("absorb_every", ctypes.c_int), ("rel_log_thresh", ctypes.c_double),
                 ("eps_stages", ctypes.c_int), ("p", ctypes.c_double), ("bary_sharpen", ctypes.c_int),
                 ("cta_threads", ctypes.c_int), ("kernel_tier", ctypes.c_int), ("max_inner", ctypes.c_int),
-                ("diag_tc_timeout", ctypes.c_int)]
+                ("diag_tc_timeout", ctypes.c_int), ("lse_form", ctypes.c_int)]
 
 
 class SinkhornGroup(ctypes.Structure):

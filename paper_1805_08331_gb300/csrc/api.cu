@@ -79,7 +79,7 @@ static void call_begin(pd_ctx* c) {
     c->ws2_live = 0;
 }
 
-extern "C" int pd_abi_version(void) { return 2; }
+extern "C" int pd_abi_version(void) { return 3; }
 
 extern "C" pd_status pd_ctx_create(int device, pd_ctx** out) {
     if (!out) return PD_ERR_INVALID;
@@ -186,6 +186,7 @@ extern "C" void pd_sinkhorn_default_params(pd_sinkhorn_params* p, double gamma, 
     p->kernel_tier = 0;
     p->max_inner = 0;
     p->diag_tc_timeout = 0;
+    p->lse_form = 0;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -287,6 +288,7 @@ static SkRun make_run(const pd_sinkhorn_params* prm) {
     r.tier = prm->kernel_tier;
     r.max_inner = prm->max_inner > 0 ? prm->max_inner : 0;
     r.diag_tc_timeout = prm->precision == PD_BF16 && prm->diag_tc_timeout != 0;
+    r.form = prm->lse_form;
     return r;
 }
 
@@ -415,7 +417,7 @@ static cudaError_t lse_rounds_groups(pd_ctx* c, std::vector<SkWS>& gs, SkWS* dev
     if (gbits >= 0) {
         if ((e = cudaMemsetAsync(counter + 2, 0, sizeof(int), s)) != cudaSuccess) return e;
         for (int gi = 0; gi < G; ++gi)
-            if ((e = sk_launch_lse2_need(gs[gi], counter + 2, s)) != cudaSuccess) return e;
+            if ((e = sk_launch_lse2_need(gs[gi], counter + 2, r.form, s)) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(hbuf + 2, counter + 2, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return e;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
@@ -608,8 +610,8 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
     if (prm->cta_threads != 0 && prm->cta_threads != 128 && prm->cta_threads != 256 && prm->cta_threads != 512 &&
         prm->cta_threads != 1024)
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: cta_threads must be 0, 128, 256, 512 or 1024");
-    if (prm->kernel_tier < 0 || prm->kernel_tier > 2 || prm->max_inner < 0)
-        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: kernel_tier must be 0..2 and max_inner >= 0");
+    if (prm->kernel_tier < 0 || prm->kernel_tier > 2 || prm->max_inner < 0 || prm->lse_form < 0 || prm->lse_form > 2)
+        return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: kernel_tier and lse_form must be 0..2, max_inner >= 0");
     if (P < 0) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: P < 0");
     if (P == 0) return PD_OK;
     if (!cost || !histA || !histB || !massA || !massB) return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch: NULL input/cost");
@@ -650,6 +652,12 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
         if (x2) rb.absorb_every = std::max(rb.absorb_every, 512);
         { ProfScope ps(c, PD_K_LOGSTEP, s); CUDA_TRY(c, sk_launch_logstep(w, rb, s)); }
         CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), s));
+        int nsm = 152;
+        {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        }
         if (x2 && P > 2) {
             // two pairs per CTA: pair the batch largest support first, so that
             // the two pairs of a CTA run for similar numbers of iterations
@@ -674,6 +682,10 @@ extern "C" pd_status pd_sinkhorn_batch(pd_ctx* c, const uint32_t* histA, const u
             CUDA_TRY(c, cudaMemcpyAsync(c->hflag, counter, sizeof(int), cudaMemcpyDeviceToHost, s));
             CUDA_TRY(c, cudaStreamSynchronize(s));
             if (c->hflag[0] == 0) break;
+            // the two-pair kernel's tail: once at most two pairs per SM still
+            // iterate, the exact engine (one pair per wide CTA, faster per
+            // iteration for a lone pair) finishes them from their current state
+            if (x2 && refine && c->hflag[0] <= 2 * nsm) break;
         }
         CUDA_TRY(c, cudaMemcpyAsync(c->hflag + 1, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -750,7 +762,8 @@ extern "C" pd_status pd_sinkhorn_batch_groups(pd_ctx* c, int ngroups, const pd_s
     if (!(prm->gamma > 0) || !std::isfinite(prm->gamma) || prm->max_iter < 1 || !(prm->tol >= 0) ||
         prm->precision != PD_FP32 || !(prm->p >= 1.0 && prm->p <= 8.0) || prm->eps_stages != 0 ||
         (prm->cta_threads != 0 && prm->cta_threads != 128 && prm->cta_threads != 256 && prm->cta_threads != 512 &&
-         prm->cta_threads != 1024) || prm->kernel_tier < 0 || prm->kernel_tier > 2 || prm->max_inner < 0)
+         prm->cta_threads != 1024) || prm->kernel_tier < 0 || prm->kernel_tier > 2 || prm->max_inner < 0 ||
+        prm->lse_form < 0 || prm->lse_form > 2)
         return fail(c, PD_ERR_INVALID, "pd_sinkhorn_batch_groups: bad params (PD_FP32 only, no eps_stages)");
     for (int gi = 0; gi < ngroups; ++gi) {
         const pd_sinkhorn_group& G = grp[gi];

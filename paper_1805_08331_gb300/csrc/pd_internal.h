@@ -105,6 +105,7 @@ struct SkRun {
     // once its error is <= stage_tol
     int kstages;
     double stage_tol;
+    int form;             // base-2 kernel: 0 automatic, 1 separable only, 2 pairwise wherever p = 2
 };
 
 cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s);
@@ -137,7 +138,7 @@ cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_
 int sk_lse2_grid_bits(double gamma);
 // gamma-continuation inside the iteration kernel: ic[IC_STAGE] = K for every pair
 cudaError_t sk_launch_set_stage(const SkWS& w, int K, cudaStream_t s);
-cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, cudaStream_t s);
+cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, int form, cudaStream_t s);
 // counter: [0] active pairs, [1] pairs moved to the global-memory variant,
 // [2] (need kernel) max shared bytes, [3] pairs moved to the FP64 kernel.
 cudaError_t sk_launch_lse2(const SkWS& w, SkRun r, int n_inner, int* counter, size_t smem, int gbits, int threads,

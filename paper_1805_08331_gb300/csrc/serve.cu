@@ -363,7 +363,7 @@ cudaError_t serve_round(pd_server* sv, int pi, std::vector<Req*>& pending) {
     SV_TRY(pool_admit(sv, P, diags, inits));
     SV_TRY(P.h_cnt.ensure(sizeof(int) * 4));
     SV_TRY(cudaMemsetAsync(P.counter, 0, sizeof(int) * 4, P.stream));
-    if (P.gbits >= 0) SV_TRY(sk_launch_lse2_need(P.w, P.counter + 2, P.stream));
+    if (P.gbits >= 0) SV_TRY(sk_launch_lse2_need(P.w, P.counter + 2, sv->run.form, P.stream));
     SV_TRY(cudaMemcpyAsync(P.h_cnt.p, P.counter, sizeof(int) * 4, cudaMemcpyDeviceToHost, P.stream));
     SV_TRY(cudaStreamSynchronize(P.stream));
     // ---- 3. one round of iterations, then the slots' status

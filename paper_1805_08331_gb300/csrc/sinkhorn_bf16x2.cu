@@ -126,6 +126,19 @@ __device__ __forceinline__ float x2_slot_sum(float v, float* sh) {
     return (sh[2 * s] + sh[2 * s + 1]) + (sh[2 * s + 4] + sh[2 * s + 5]);
 }
 
+// Two sums over the 128 threads of a slot at once; sh: 8 float2.
+__device__ __forceinline__ float2 x2_slot_sum2(float a, float b, float2* sh) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int warp = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[warp] = make_float2(a, b);
+    __syncthreads();
+    const int s = (warp & 3) >> 1;
+    const float2 p0 = sh[2 * s], p1 = sh[2 * s + 1], p4 = sh[2 * s + 4], p5 = sh[2 * s + 5];
+    return make_float2((p0.x + p1.x) + (p4.x + p5.x), (p0.y + p1.y) + (p4.y + p5.y));
+}
+
 // TMA: load box (64 x 64 BF16, 128-byte swizzle) of 4-D tensor map coordinate
 // (0, 0, part, pair) into shared memory, completing on mbar.
 __device__ __forceinline__ void x2_tma_load(uint32_t dst, const CUtensorMap* map, int part, int pair, uint64_t* mbar) {
@@ -138,12 +151,16 @@ __device__ __forceinline__ void x2_expect_tx(uint64_t* mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
 }
 
+// First thread of a slot.
+__device__ __forceinline__ int st0(int slot) { return slot * 64; }
+
 // Pair slot state, one copy per slot in shared memory.
 struct X2Slot {
     int p;              // pair index, -1: none
     int live;           // still iterating in this launch
     int status, absorb, iters, since, range, stall;
     float utD, vtD, err, best;
+    float sKv, sKu;     // sum_y KDv vt and sum_x KDu ut of the current scalings (Delta updates)
 };
 
 // |log x| <= lim without a logarithm: e^-lim <= x <= e^lim (false for NaN)
@@ -157,7 +174,7 @@ sk_iter_bf16x2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int* erro
     __shared__ uint32_t tbase;
     __shared__ X2Slot S[2];
     __shared__ float shf[8];
-    __shared__ int any_live;
+    __shared__ float2 shf2[8];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int lr = t & 127, slot = lr >> 6, row = lr & 63, half = t >> 7;
     const bool diag = r.diag_tc_timeout != 0;
@@ -232,12 +249,17 @@ sk_iter_bf16x2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int* erro
         S[t].status = ST_ACTIVE; S[t].absorb = 0; S[t].range = 0;
         S[t].best = INFINITY; S[t].stall = 0;
     }
+    {   // sum_y KDv vt of the loaded scalings (later sums come from the epilogues)
+        float v0 = 0.f;
+        if (p >= 0) for (int e = row + 64 * half; e < q.ic[IC_NB]; e += 128) { const int c = q.sb[e]; v0 += q.KDv[c] * q.vt[c]; }
+        v0 = x2_slot_sum(v0, shf);
+        if (t == st0(slot)) S[slot].sKv = v0;
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tm = tbase;
     uint32_t phase = 0;
-    const int na = p >= 0 ? q.ic[IC_NA] : 0, nb = p >= 0 ? q.ic[IC_NB] : 0;
     const float aD = p >= 0 ? (float)q.sc[SC_AD] : 0.f, bD = p >= 0 ? (float)q.sc[SC_BD] : 0.f;
     const float total = p >= 0 ? (float)q.sc[SC_TOTAL] : 1.f;
     const float DD = p >= 0 ? (float)q.sc[SC_DD] : 0.f, tau = p >= 0 ? (float)q.sc[SC_TAU] : 0.f;
@@ -249,9 +271,12 @@ sk_iter_bf16x2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int* erro
     const unsigned char* A1v[2] = {F[4], F[5]};
     const unsigned char* A2v[2] = {F[6], F[7]};
     const unsigned char* BX[2] = {X[0], X[1]};
+    int live_next = S[slot].live;   // thread st: its slot still iterates (the loop-top barrier ORs them)
     for (int it = 0; it < n_inner && !timeout; ++it) {
-        const bool live = S[slot].live != 0;   // read before this iteration's writes (barrier-separated)
+        if (!__syncthreads_or(t == st && live_next)) break;
+        const bool live = S[slot].live != 0;   // written before the barrier above
         const float vtD = S[slot].vtD;
+        const float sKv = S[slot].sKv;
         // ================= u-update
         if (!x2_run(tm, A1u, BX, &mbar, phase, diag)) { timeout = 1; break; }
         {                                                                  // Wt rows j
@@ -259,10 +284,8 @@ sk_iter_bf16x2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int* erro
             tmem_ld32(x2_taddr(tm), v);
             x2_store_chunk(X[0], X[1], lr, half, v, live ? 1.f : 0.f);
         }
-        float sKv = 0.f;                                                   // sum_y KDv vt (ut_Delta)
-        if (live) for (int e = row + 64 * half; e < nb; e += 128) { const int c = q.sb[e]; sKv += q.KDv[c] * q.vt[c]; }
-        sKv = x2_slot_sum(sKv, shf);
         if (!x2_run(tm, A2u, BX, &mbar, phase, diag)) { timeout = 1; break; }
+        float ku_loc = 0.f;                                                // sum_x KDu ut (v_Delta)
         {
             const int i = row;
             const float rsv = rs_v[lr];
@@ -277,23 +300,21 @@ sk_iter_bf16x2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int* erro
             for (int e = e0; e < e1; ++e) {
                 const int c = q.sa[e], j = c % dp;
                 if ((j >> 5) != half) continue;
-                const float den = cf_u[st + j] * stg[lane * 33 + (j & 31)] + q.KDu[c] * vtD;
+                const float kdu = q.KDu[c];
+                const float den = cf_u[st + j] * stg[lane * 33 + (j & 31)] + kdu * vtD;
                 const float a = q.am[c];
                 const float uu = a / den;
                 if (!x2_in(uu / a, etau, etaui) || !x2_in(uu * rsv, e85, e85i)) rng = true;
                 q.ut[c] = uu;
+                ku_loc += kdu * uu;
                 x2_store_one(X[0], X[1], lr, j, uu * rsv);
             }
             __syncwarp();
             if (rng) S[slot].range = 1;
         }
-        if (live && t == st) {
-            const float utD_new = (aD > 0.f) ? aD / (sKv + DD * vtD) : 0.f;
-            if (aD > 0.f && !x2_in(utD_new / aD, etau, etaui)) S[slot].range = 1;
-            S[slot].utD = utD_new;
-        }
-        __syncthreads();
-        const float utD = S[slot].utD;
+        const float sKu = x2_slot_sum(ku_loc, shf);
+        const float utD = (aD > 0.f) ? aD / (sKv + DD * vtD) : 0.f;        // every thread of the slot
+        if (live && t == st && aD > 0.f && !x2_in(utD / aD, etau, etaui)) S[slot].range = 1;
         // ================= v-update
         if (!x2_run(tm, A1v, BX, &mbar, phase, diag)) { timeout = 1; break; }
         {                                                                  // Wv rows l
@@ -301,11 +322,8 @@ sk_iter_bf16x2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int* erro
             tmem_ld32(x2_taddr(tm), v);
             x2_store_chunk(X[0], X[1], lr, half, v, live ? 1.f : 0.f);
         }
-        float sKu = 0.f;                                                   // sum_x KDu ut (v_Delta)
-        if (live) for (int e = row + 64 * half; e < na; e += 128) { const int c = q.sa[e]; sKu += q.KDu[c] * q.ut[c]; }
-        sKu = x2_slot_sum(sKu, shf);
         if (!x2_run(tm, A2v, BX, &mbar, phase, diag)) { timeout = 1; break; }
-        float e_loc = 0.f;
+        float e_loc = 0.f, kv_loc = 0.f;
         {
             const int k = row;
             const float rsu = rs_u[lr];
@@ -320,22 +338,27 @@ sk_iter_bf16x2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int* erro
             for (int e = e0; e < e1; ++e) {
                 const int c = q.sb[e], l = c % dp;
                 if ((l >> 5) != half) continue;
-                const float qv = cf_v[st + l] * stg[lane * 33 + (l & 31)] + q.KDv[c] * utD;
+                const float kdv = q.KDv[c];
+                const float qv = cf_v[st + l] * stg[lane * 33 + (l & 31)] + kdv * utD;
                 const float b = q.bm[c];
                 e_loc += fabsf(q.vt[c] * qv - b);
                 const float vv = b / qv;
                 if (!x2_in(vv / b, etau, etaui) || !x2_in(vv * rsu, e85, e85i)) rng = true;
                 q.vt[c] = vv;
+                kv_loc += kdv * vv;
                 x2_store_one(X[0], X[1], lr, l, vv * rsu);
             }
             __syncwarp();
             if (rng) S[slot].range = 1;
         }
-        const float errs = x2_slot_sum(e_loc, shf);
+        const float2 ek = x2_slot_sum2(e_loc, kv_loc, shf2);
         if (live && t == st) {
             X2Slot& Z = S[slot];
-            float ee = errs;
+            float ee = ek.x;
             const float qD = sKu + DD * utD;
+            Z.utD = utD;
+            Z.sKu = sKu;
+            Z.sKv = ek.y;
             if (bD > 0.f) {
                 ee += fabsf(vtD * qD - bD);
                 const float vv = bD / qD;
@@ -351,11 +374,7 @@ sk_iter_bf16x2_kernel(SkWS w, SkRun r, int n_inner, int* active_count, int* erro
             else if (Z.stall >= X2_STALL) { Z.status = ST_MAXITER; Z.live = 0; }   // precision floor: refine
             else if (Z.range || Z.since >= r.absorb_every) { Z.absorb = 1; Z.live = 0; }
         }
-        if (t == 0) any_live = 0;
-        __syncthreads();
-        if (t < 2 && S[t].live) any_live = 1;
-        __syncthreads();
-        if (!any_live) break;
+        if (t == st) live_next = S[slot].live;
     }
     tc_fence_before();
     __syncthreads();

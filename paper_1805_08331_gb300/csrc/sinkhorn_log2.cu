@@ -58,6 +58,7 @@ struct L2Side {
     uint32_t lw;      // float2 [n] log2 weight (hi, lo)
     uint32_t pot;     // float2 [n] potential/gamma in log2 units (hi, lo)
     uint32_t hin;     // float2 [n] lw + pot, the side's h when it is the input
+    uint32_t rec;     // float4 [n] (hin.x, hin.y, row, column): a cell as the pairwise form reads it
     uint32_t w;       // float  [n] weight (marginal error)
     uint32_t rp;      // int    [d+1] row pointers into the support while loading; then, per
                       //        non-empty row r: first cell | one-past-last cell << 16
@@ -74,24 +75,42 @@ struct L2Side {
 
 __host__ __device__ __forceinline__ size_t l2_al(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Bytes of the per-side arrays of a pair.
-__host__ __device__ __forceinline__ size_t l2_side_bytes(int nA, int nB, int d) {
+// Bytes of the per-side arrays of a pair (rec: the pairwise form's records).
+__host__ __device__ __forceinline__ size_t l2_side_bytes(int nA, int nB, int d, bool rec) {
     size_t b = 0;
     const int ns[2] = {nA, nB};
     for (int s = 0; s < 2; ++s) {
         const size_t n = (size_t)ns[s];
-        b += l2_al(24 * n) + l2_al(4 * n) + l2_al(4 * (size_t)(d + 1)) + l2_al(6 * n) + l2_al(6 * (size_t)d);
+        b += l2_al(24 * n) + (rec ? l2_al(16 * n) : 0) + l2_al(4 * n) + l2_al(4 * (size_t)(d + 1)) + l2_al(6 * n) +
+             l2_al(6 * (size_t)d);
     }
     return b;
 }
-// Bytes of the cost tables and the stage-1 buffer (nrmax non-empty input rows).
-__host__ __device__ __forceinline__ size_t l2_table_bytes(int nrmax, int d) {
-    return l2_al(8 * (size_t)(2 * d - 1)) + l2_al(8 * (size_t)d) + l2_al(8 * (size_t)L2_CW * nrmax);
+// Bytes of the cost tables and the stage-1 buffer (nrmax non-empty input rows;
+// none when no half-step of the pair takes the separable form).
+__host__ __device__ __forceinline__ size_t l2_table_bytes(int nrmax, int d, bool sep = true) {
+    return l2_al(8 * (size_t)(2 * d - 1)) + l2_al(8 * (size_t)d) + (sep ? l2_al(8 * (size_t)L2_CW * nrmax) : 0);
+}
+
+// Form of a half-step (in = input side, out = output side).  Separable: stage
+// 1 has n_in x nc_out terms, stage 2 nr_in x n_out.  Pairwise (p = 2 only):
+// n_in x n_out terms, each about 2.5x cheaper (no tables, no stage buffer, two
+// barriers per half-step), so it is taken while it has at most L2_PW_RATIO
+// times the separable form's terms.  form: 0 automatic, 1 separable only, 2
+// pairwise wherever p = 2.
+#define L2_PW_RATIO 2
+__host__ __device__ __forceinline__ bool l2_pw_half(int n_in, int nr_in, int n_out, int nc_out, int form, bool p2) {
+    if (!p2 || form == 1) return false;
+    if (form == 2) return true;
+    const long long direct = (long long)n_in * n_out;
+    const long long sep = (long long)n_in * nc_out + (long long)nr_in * n_out;
+    return direct <= L2_PW_RATIO * sep;
 }
 // Shared-memory bytes of a pair in the on-chip variant (the host sizes the
-// launch with the maximum over the pairs).
-__device__ __forceinline__ size_t l2_need(int nA, int nB, int nrA, int nrB, int d) {
-    return l2_side_bytes(nA, nB, d) + l2_table_bytes(nrA > nrB ? nrA : nrB, d);
+// launch with the maximum over the pairs); pwU / pwV: the forms of its
+// u- and v-updates.
+__host__ __device__ __forceinline__ size_t l2_need(int nA, int nB, int nrA, int nrB, int d, bool pwU, bool pwV) {
+    return l2_side_bytes(nA, nB, d, pwU || pwV) + l2_table_bytes(nrA > nrB ? nrA : nrB, d, !(pwU && pwV));
 }
 
 // (hi, lo) split of an FP64 value on the 2^-G grid (gsc = 2^G).
@@ -226,7 +245,51 @@ struct L2Consts {
     int d;
     float gsc, ginv, lim;
     float escale;    // 2^40 / total mass (marginal-error terms in fixed point)
+    float s1, s2;    // pairwise form (p = 2): c_xy/gamma in log2 units = (s1 + s2) D, D = |x - y|^2 in cells
+    bool pw_ok;      // the pairwise form is exact at this gamma (p = 2)
+    int form;        // 0 automatic, 1 separable only, 2 pairwise wherever pw_ok
 };
+
+// Pairwise-form constants at this gamma (p = 2): c_xy/gamma in log2 units is
+// s D with D = (i-k)^2 + (j-l)^2 <= 2 (d-1)^2, an integer exact in FP32, and
+// s = log2(e) / (gamma d^2).  s = s1 + s2 with s1 on the finest grid 2^-Gs
+// (Gs >= G) such that s1 D is exact and every hi word (h_y - Ms) - s1 D lies
+// below 2^(24-Gs) (potentials below 2^(21-G), log2 weights below 64), so the
+// hi words are exact; s2 D joins the rest word.  pw_ok = false otherwise.
+__device__ __forceinline__ void l2_pw_consts(L2Consts& K, double gamma, int d, int gbits, double pw) {
+    K.pw_ok = false;
+    K.s1 = 0.f;
+    K.s2 = 0.f;
+    if (pw != 2.0) return;
+    const double s = 1.4426950408889634 / (gamma * (double)d * (double)d);
+    const double dmax = 2.0 * (double)(d - 1) * (double)(d - 1);
+    const double bhi = ldexp(1.0, 22 - gbits) + 64.0 + s * dmax;
+    for (int gs = gbits + 8; gs >= gbits; --gs) {
+        const double n1 = rint(ldexp(s, gs));
+        if (ldexp(1.0, 24 - gs) >= bhi && n1 * dmax < 16777216.0) {
+            K.s1 = (float)ldexp(n1, -gs);
+            K.s2 = (float)(s - ldexp(n1, -gs));
+            K.pw_ok = true;
+            return;
+        }
+    }
+}
+
+// Packed FP32 pair arithmetic (two lanes of one 64-bit register pair).
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 ra, rb, rr;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rr, ra, rb;\n\tmov.b64 {%0, %1}, rr;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    float2 r;
+    asm("{.reg .b64 ra, rb, rc, rr;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rr, ra, rb, rc;\n\tmov.b64 {%0, %1}, rr;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
 
 // Lanes of the Delta-output sum: a fixed partition (thread t < L2_DLANES sums
 // the input cells t, t + L2_DLANES, ...), so the sum, like every other sum of
@@ -275,24 +338,19 @@ __device__ __forceinline__ bool l2_update(float tot, float shift, float Ms, floa
     return fabsf(pn.x) < K.lim;
 }
 
-// One half-step: out.pot <- -LSE over the input side.  Adds the marginal-error
-// terms of `out` to errq when want_err.  Sets *range_flag if a potential left
-// the exact range (the pair then moves to the FP64 kernel).
+// Delta output of a half-step, shifted by its previous value: partial sums
+// over a fixed L2_DLANES-lane partition of the input cells, one barrier, then
+// thread 0 finishes the sum and updates out.potD (the other threads go on).
 template <int NT, bool GM>
-static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool want_err, long long& errq,
-                               bool& errbad, float* redD, int* range_flag, unsigned char* gb) {
+static __device__ __forceinline__ void l2_delta_out(L2Side& in, L2Side& out, const L2Consts& K, bool want_err,
+                                                    long long& errq, bool& errbad, float* redD, int* range_flag,
+                                                    unsigned char* gb) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int d = K.d;
-    const int in_n = in.n, in_nr = in.nr;
+    const int in_n = in.n;
     const float2* in_hin = sdp<float2, GM>(gb, in.hin);
     const short* in_row = sdp<short, GM>(gb, in.row);
     const short* in_col = sdp<short, GM>(gb, in.col);
-    const short* in_rows = sdp<short, GM>(gb, in.rows);
-    const int* in_rq = sdp<int, GM>(gb, in.rp);
-    const float2* ct = smp<float2>(K.ct);
     const float2* cdt = smp<float2>(K.cdt);
-    float2* L1 = smp<float2>(K.L1);
-    // ---- Delta output, shifted by its previous value
     const bool doD = out.wD > 0.f;
     const float MsD = -out.potD.x;
     // lane ln of the fixed L2_DLANES-lane partition is thread ln % NT (one pass
@@ -352,6 +410,25 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
             atomicOr(range_flag, 1);
         }
     }
+}
+
+// One half-step: out.pot <- -LSE over the input side.  Adds the marginal-error
+// terms of `out` to errq when want_err.  Sets *range_flag if a potential left
+// the exact range (the pair then moves to the FP64 kernel).
+template <int NT, bool GM>
+static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool want_err, long long& errq,
+                               bool& errbad, float* redD, int* range_flag, unsigned char* gb) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int d = K.d;
+    const int in_nr = in.nr;
+    const float2* in_hin = sdp<float2, GM>(gb, in.hin);
+    const short* in_col = sdp<short, GM>(gb, in.col);
+    const short* in_rows = sdp<short, GM>(gb, in.rows);
+    const int* in_rq = sdp<int, GM>(gb, in.rp);
+    const float2* ct = smp<float2>(K.ct);
+    const float2* cdt = smp<float2>(K.cdt);
+    float2* L1 = smp<float2>(K.L1);
+    l2_delta_out<NT, GM>(in, out, K, want_err, errq, errbad, redD, range_flag, gb);
     const float2 hD = in.hinD;   // input Delta term (not written in this half-step)
     constexpr int L2_G = L2Lanes<NT>::G;
     const unsigned gmask = ((1u << L2_G) - 1u) << (lane & ~(L2_G - 1));
@@ -497,7 +574,9 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
                                   pn)) {
                         out_pot[qo] = pn;
                         const float2 lw = sdp<float2, GM>(gb, out.lw)[qo];
-                        sdp<float2, GM>(gb, out.hin)[qo] = make_float2(lw.x + pn.x, lw.y + pn.y);
+                        const float2 hn = make_float2(lw.x + pn.x, lw.y + pn.y);
+                        sdp<float2, GM>(gb, out.hin)[qo] = hn;
+                        if (!GM && K.pw_ok) *smp<float2>(out.rec + 16 * qo) = hn;
                     } else {
                         atomicOr(range_flag, 1);
                     }
@@ -507,6 +586,131 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
         __syncthreads();
     }
     if (out_nch == 0) __syncthreads();
+}
+
+// Lanes per output cell of the pairwise form: the fewest (passes x input
+// cells per lane) at a reference width of 256 threads.  It depends on the
+// supports only, so the partition of every sum, and the result, is the same
+// at every CTA width.
+__device__ __forceinline__ int l2_pw_lanes(int n_in, int m) {
+    int G = 1, best = 0x7fffffff;
+    for (int gg = 1, lg = 0; gg <= 8; gg <<= 1, ++lg) {
+        const int passes = (m * gg + 255) / 256;
+        const int c = passes * ((n_in + gg - 1) / gg + 8 * lg + 24);
+        if (c < best) { best = c; G = gg; }
+    }
+    return G;
+}
+
+// Pairwise form of a half-step (p = 2, on chip): the same log-sum-exp as the
+// separable form, summed over the input support directly,
+//   out_x = -LSE( { h_y - s D_xy : y in supp(in) } u { h_D - cD_x/gamma } ),
+// with the shift Ms = -(previous out_x) and the exact hi words of
+// l2_pw_consts: per term two packed differences give (i-k, j-l), D is exact,
+// one packed FMA gives (h_y.hi - s1 D, h_y.lo - s2 D), then ex2.  G lanes per
+// output cell split the input cells (y = g, g + G, ...); a lane adds blocks of
+// four terms and sums the blocks compensated (Kahan); the G partial sums meet
+// in a fixed shuffle tree.
+template <int NT>
+static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bool want_err, long long& errq,
+                                  bool& errbad, float* redD, int* range_flag) {
+    l2_delta_out<NT, false>(in, out, K, want_err, errq, errbad, redD, range_flag, nullptr);
+    const int t = threadIdx.x, lane = t & 31;
+    const int n_in = in.n, m = out.n;
+    const float4* rec_in = smp<float4>(in.rec);
+    const float4* rec_out = smp<float4>(out.rec);
+    float2* out_pot = smp<float2>(out.pot);
+    const float2* cdt = smp<float2>(K.cdt);
+    const float2 hD = in.hinD;   // input Delta term (not written in this half-step)
+    const int G = l2_pw_lanes(n_in, m);
+    const int g = lane & (G - 1);
+    const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
+    const float2 ns = make_float2(-K.s1, -K.s2);
+    for (int e0 = 0; e0 < m; e0 += NT / G) {
+        const int e = e0 + t / G;
+        const bool live = e < m;
+        float2 xij = make_float2(0.f, 0.f), po = make_float2(0.f, 0.f);
+        if (live) {
+            const float4 rx = rec_out[e];
+            xij = make_float2(rx.z, rx.w);
+            po = out_pot[e];
+        }
+        const float Ms = -po.x;
+        float tot = 0.f;
+        if (live) {
+            float sm = 0.f, cm = 0.f;
+            int y = g;
+            for (; y + 3 * G < n_in; y += 4 * G) {
+                float ev[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float4 r = rec_in[y + u * G];
+                    const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
+                    const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
+                    const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
+                    ev[u] = l2_ex2((hl.x - Ms) + hl.y);
+                }
+                kahan_add(sm, cm, (ev[0] + ev[1]) + (ev[2] + ev[3]));
+            }
+            float rest = 0.f;
+            for (; y < n_in; y += G) {
+                const float4 r = rec_in[y];
+                const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
+                const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
+                const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
+                rest += l2_ex2((hl.x - Ms) + hl.y);
+            }
+            if (g == 0 && hD.x > -INFINITY) {
+                const float2 c = cdt[abs((int)xij.y - (int)xij.x)];
+                rest += l2_ex2(((hD.x - c.x) - Ms) + (hD.y - c.y));
+            }
+            kahan_add(sm, cm, rest);
+            tot = sm - cm;
+        }
+        for (int o = 1; o < G; o <<= 1) tot += __shfl_xor_sync(gmask, tot, o);
+        float shift = Ms;
+        if (live && !(tot >= 0x1p-100f && tot <= 0x1p100f)) {
+            // exact maximum of the terms; an integer shift (on every grid) at or
+            // above it keeps every term at most 1 and the largest above 1/2
+            float mx = -INFINITY;
+            for (int y = g; y < n_in; y += G) {
+                const float4 r = rec_in[y];
+                const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
+                const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
+                mx = fmaxf(mx, fmaf(ns.x, D, r.x));
+            }
+            if (g == 0 && hD.x > -INFINITY) mx = fmaxf(mx, hD.x - cdt[abs((int)xij.y - (int)xij.x)].x);
+            for (int o = 1; o < G; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(gmask, mx, o));
+            shift = ceilf(mx);
+            float sm = 0.f, cm = 0.f;
+            for (int y = g; y < n_in; y += G) {
+                const float4 r = rec_in[y];
+                const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
+                const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
+                const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
+                kahan_add(sm, cm, l2_ex2((hl.x - shift) + hl.y));
+            }
+            if (g == 0 && hD.x > -INFINITY) {
+                const float2 c = cdt[abs((int)xij.y - (int)xij.x)];
+                kahan_add(sm, cm, l2_ex2(((hD.x - c.x) - shift) + (hD.y - c.y)));
+            }
+            tot = sm - cm;
+            for (int o = 1; o < G; o <<= 1) tot += __shfl_xor_sync(gmask, tot, o);
+        }
+        if (live && g == 0) {
+            float2 pn;
+            if (l2_update(tot, shift, Ms, po, smp<float>(out.w)[e], want_err, K, errq, errbad, pn)) {
+                out_pot[e] = pn;
+                const float2 lw = smp<float2>(out.lw)[e];
+                const float2 hn = make_float2(lw.x + pn.x, lw.y + pn.y);
+                smp<float2>(out.hin)[e] = hn;
+                *smp<float2>(out.rec + 16 * e) = hn;
+            } else {
+                atomicOr(range_flag, 1);
+            }
+        }
+    }
+    __syncthreads();
 }
 
 // gamma-continuation step inside the launch: gamma -> gamma / 4.  Potentials
@@ -529,7 +733,9 @@ static __device__ void l2_next_stage(L2Side* S, const L2Consts& K, double gamma_
             const float2 pn = make_float2(po.x * 4.f + rv, v - rv);
             if (!(fabsf(pn.x) < K.lim)) atomicOr(range_flag, 1);
             xpot[e] = pn;
-            xhin[e] = make_float2(xlw[e].x + pn.x, xlw[e].y + pn.y);
+            const float2 hn = make_float2(xlw[e].x + pn.x, xlw[e].y + pn.y);
+            xhin[e] = hn;
+            if (!GM && K.pw_ok) *smp<float2>(X.rec + 16 * e) = hn;
         }
     }
     __syncthreads();   // every thread has read the sides' Delta state (hinD in the half-steps) before t == 0 writes it
@@ -556,6 +762,24 @@ static __device__ void l2_next_stage(L2Side* S, const L2Consts& K, double gamma_
 // stopped or moved.  Once it reaches r.exit_at, the pairs still iterating
 // leave at their next 16-iteration check with their state saved (they stay
 // active and the host runs them on in wider CTAs).
+// The workspace descriptor of a CTA's pair: the kernel parameter itself (one
+// workspace), or, in a launch over several workspaces, the pair's entry of
+// w.groups copied once into shared memory (only that instantiation holds the
+// copy).
+template <bool MULTI> struct L2Desc {
+    static __device__ __forceinline__ const SkWS& get(const SkWS& w, int) { return w; }
+};
+template <> struct L2Desc<true> {
+    static __device__ __forceinline__ const SkWS& get(const SkWS& w, int code) {
+        __shared__ SkWS Wsh;
+        static_assert(sizeof(SkWS) % 4 == 0 && sizeof(SkWS) / 4 <= 128, "descriptor copy: one word per thread");
+        const int* src = reinterpret_cast<const int*>(w.groups + (code >> 24));
+        if ((int)threadIdx.x < (int)(sizeof(SkWS) / 4)) reinterpret_cast<int*>(&Wsh)[threadIdx.x] = src[threadIdx.x];
+        __syncthreads();
+        return Wsh;
+    }
+};
+
 // MULTI = false: one workspace, its descriptor is the kernel parameter w
 // (parameter-space reads, which the compiler can repeat instead of keeping
 // the pair's pointers in registers); MULTI = true: a launch over several
@@ -575,14 +799,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     // workspaces (pairs of several grid sizes), to its workspace: code =
     // group << 24 | pair; the workspace descriptors are in device memory
     const int code = w.order ? w.order[blockIdx.x] : blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    __shared__ SkWS Wsh;   // MULTI: the pair's workspace descriptor, copied once
-    if constexpr (MULTI) {
-        static_assert(sizeof(SkWS) % 4 == 0 && sizeof(SkWS) / 4 <= 128, "descriptor copy: one word per thread");
-        const int* src = reinterpret_cast<const int*>(w.groups + (code >> 24));
-        if (t < (int)(sizeof(SkWS) / 4)) reinterpret_cast<int*>(&Wsh)[t] = src[t];
-        __syncthreads();
-    }
-    const SkWS& W = MULTI ? Wsh : w;
+    const SkWS& W = L2Desc<MULTI>::get(w, code);
     const int p = MULTI ? (code & 0xFFFFFF) : code;
     PairPtrs q = pair_ptrs(W, p);
     if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG] != (GM ? 1 : 0)) return;
@@ -593,11 +810,20 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     l2_compact(q.rpa, d, nullptr, &cnt[0], nullptr, wcnt);
     l2_compact(q.rpb, d, nullptr, &cnt[1], nullptr, wcnt);
     const int nrA = cnt[0], nrB = cnt[1];
+    // the form of each half-step (the pairwise form runs on chip only)
+    bool pwU = false, pwV = false;
+    if constexpr (!GM) {
+        l2_compact(q.cpa, d, nullptr, &cnt[2], nullptr, wcnt);
+        l2_compact(q.cpb, d, nullptr, &cnt[3], nullptr, wcnt);
+        pwU = l2_pw_half(nB, nrB, nA, cnt[2], r.form, W.p == 2.0);
+        pwV = l2_pw_half(nA, nrA, nB, cnt[3], r.form, W.p == 2.0);
+    }
     if (t == 0) {
         if (GM)
-            fits = l2_side_bytes(nA, nB, d) <= gcap && l2_table_bytes(nrA > nrB ? nrA : nrB, d) <= (size_t)smem_cap;
+            fits = l2_side_bytes(nA, nB, d, false) <= gcap &&
+                   l2_table_bytes(nrA > nrB ? nrA : nrB, d) <= (size_t)smem_cap;
         else
-            fits = l2_need(nA, nB, nrA, nrB, d) <= (size_t)smem_cap;
+            fits = l2_need(nA, nB, nrA, nrB, d, pwU, pwV) <= (size_t)smem_cap;
         fits = fits && nA < 32768 && nB < 32768;   // cell indices are 16-bit (chl, packed row ranges)
     }
     __syncthreads();
@@ -626,12 +852,13 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     const int ns[2] = {nA, nB};
     for (int s = 0; s < 2; ++s) {
         const int n = ns[s];
-        const uint32_t o_lw = take(24 * (size_t)n), o_w = take(4 * (size_t)n), o_rp = take(4 * (size_t)(d + 1));
+        const uint32_t o_lw = take(24 * (size_t)n), o_rec = take((pwU || pwV) ? 16 * (size_t)n : 0),
+                       o_w = take(4 * (size_t)n), o_rp = take(4 * (size_t)(d + 1));
         const uint32_t o_row = take(6 * (size_t)n), o_rows = take(6 * (size_t)d);
         if (t == 0) {
             L2Side& X = S[s];
             X.n = n;
-            X.lw = o_lw; X.pot = o_lw + 8 * n; X.hin = o_lw + 16 * n;
+            X.lw = o_lw; X.pot = o_lw + 8 * n; X.hin = o_lw + 16 * n; X.rec = o_rec;
             X.w = o_w; X.rp = o_rp;
             X.row = o_row; X.col = o_row + 2 * n; X.chl = o_row + 4 * n;
             X.rows = o_rows; X.cols = o_rows + 2 * d; X.colpos = o_rows + 4 * d;
@@ -642,7 +869,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     K.ct = take(8 * (size_t)(2 * d - 1));
     K.cdt = take(8 * (size_t)d);
     const int nrmax = nrA > nrB ? nrA : nrB;
-    K.L1 = take(8 * (size_t)L2_CW * nrmax);
+    K.L1 = take((pwU && pwV) ? 0 : 8 * (size_t)L2_CW * nrmax);
     __syncthreads();
     // ---- load
     const double gsc = ldexp(1.0, gbits);
@@ -673,6 +900,8 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
                 const float2 p2 = l2_split(pot[s][c] * LOG2E, gsc);
                 xlw[e] = l2; xpot[e] = p2;
                 xhin[e] = make_float2(l2.x + p2.x, l2.y + p2.y);
+                if (!GM && (pwU || pwV))
+                    smp<float4>(X.rec)[e] = make_float4(l2.x + p2.x, l2.y + p2.y, (float)i, (float)j);
                 xw[e] = wt[s][c];
             }
             for (int i = t; i <= d; i += NT) xrp[i] = rps[s][i];
@@ -709,6 +938,9 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     K.gsc = (float)gsc; K.ginv = (float)(1.0 / gsc);
     K.lim = (float)ldexp(1.0, 21 - gbits);   // |potential| bound keeping every sum of grid words exact
     K.escale = q.sc[SC_TOTAL] > 0 ? (float)(ldexp(1.0, 40) / q.sc[SC_TOTAL]) : 0.f;
+    K.form = r.form;
+    l2_pw_consts(K, gamma_k, d, gbits, W.p);
+    K.pw_ok = K.pw_ok && (pwU || pwV);
     const float tolf = (float)r.tol, stage_tolf = (float)r.stage_tol;
     int iters = q.ic[IC_ITERS];
     float errf = (float)q.sc[SC_ERR];
@@ -720,8 +952,12 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
         // u-update (phi from psi), then v-update (psi from phi, err_t): one copy
         // of the half-step code serves both (instruction cache)
 #pragma unroll 1
-        for (int hs = 0; hs < 2; ++hs)
-            l2_half<NT, GM>(S[1 - hs], S[hs], K, hs == 1, errq, errbad, redD, &range_flag, gb);
+        for (int hs = 0; hs < 2; ++hs) {
+            if (!GM && K.pw_ok && (hs == 0 ? pwU : pwV))
+                l2_half_pw<NT>(S[1 - hs], S[hs], K, hs == 1, errq, errbad, redD, &range_flag);
+            else
+                l2_half<NT, GM>(S[1 - hs], S[hs], K, hs == 1, errq, errbad, redD, &range_flag, gb);
+        }
         errq = warp_sum(errq);
         if (lane == 0) redE[wid] = errq;
         // written next to redE and read after the same barrier (the next write
@@ -741,6 +977,11 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
         if (stage_done) {
             --stage;
             l2_next_stage<NT, GM>(S, K, ldexp(W.gamma, 2 * stage), W.p, d, &range_flag, gb);
+            {
+                const bool keep = K.pw_ok;
+                l2_pw_consts(K, ldexp(W.gamma, 2 * stage), d, gbits, W.p);
+                K.pw_ok = K.pw_ok && keep;
+            }
             if (range_flag) { moved = true; break; }
         }
         if (leave) break;   // status stays ST_ACTIVE: relaunched in a wider CTA
@@ -797,23 +1038,27 @@ cudaError_t sk_launch_set_stage(const SkWS& w, int K, cudaStream_t s) {
 }
 
 // Maximum shared-memory need over the active on-chip pairs (one thread per pair).
-__global__ void sk_lse2_need_kernel(SkWS w, int* max_need) {
+__global__ void sk_lse2_need_kernel(SkWS w, int* max_need, int form) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= w.P) return;
     PairPtrs q = pair_ptrs(w, p);
     if (q.ic[IC_STATUS] != ST_ACTIVE || q.ic[IC_BIG]) return;
-    int nrA = 0, nrB = 0;
+    int nrA = 0, nrB = 0, ncA = 0, ncB = 0;
     for (int i = 0; i < w.d; ++i) {
         nrA += q.rpa[i + 1] > q.rpa[i];
         nrB += q.rpb[i + 1] > q.rpb[i];
+        ncA += q.cpa[i + 1] > q.cpa[i];
+        ncB += q.cpb[i + 1] > q.cpb[i];
     }
-    const size_t need = l2_need(q.ic[IC_NA], q.ic[IC_NB], nrA, nrB, w.d);
+    const int nA = q.ic[IC_NA], nB = q.ic[IC_NB];
+    const size_t need = l2_need(nA, nB, nrA, nrB, w.d, l2_pw_half(nB, nrB, nA, ncA, form, w.p == 2.0),
+                                l2_pw_half(nA, nrA, nB, ncB, form, w.p == 2.0));
     atomicMax(max_need, (int)(need > 0x7fffffff ? 0x7fffffff : need));
 }
 
-cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, cudaStream_t s) {
+cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, int form, cudaStream_t s) {
     if (w.P == 0) return cudaSuccess;
-    sk_lse2_need_kernel<<<(w.P + 255) / 256, 256, 0, s>>>(w, max_need);
+    sk_lse2_need_kernel<<<(w.P + 255) / 256, 256, 0, s>>>(w, max_need, form);
     return cudaGetLastError();
 }
 
@@ -836,14 +1081,26 @@ size_t sk_lse2_smem_cap() {
     int dev = 0, cap = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return (size_t)cap - 1024;   // static shared memory of the kernel
+    return (size_t)cap - 1024;   // the widest kernel's static shared memory (<= 1 KB)
+}
+
+// Dynamic shared memory an instantiation may request: the per-block opt-in
+// limit less its own static shared memory.
+template <class F>
+static size_t lse2_dyn_cap(F* kernel) {
+    int dev = 0, cap = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return sk_lse2_smem_cap();
+    return (size_t)cap - fa.sharedSizeBytes;
 }
 
 template <int NT, bool GM, bool MULTI>
 static cudaError_t launch_lse2_v(const SkWS& w, SkRun r, int n_inner, int* counter, size_t smem, size_t gcap,
                                  int gbits, cudaStream_t s) {
     static std::atomic<size_t> configured{0};
-    const size_t cap = sk_lse2_smem_cap();
+    const size_t cap = lse2_dyn_cap(sk_lse2_kernel<NT, GM, MULTI>);
     if (configured != cap) {
         cudaError_t e = cudaFuncSetAttribute(sk_lse2_kernel<NT, GM, MULTI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);

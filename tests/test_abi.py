@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_abi_version_and_params_defaults():
     lib = api.load()
-    assert lib.pd_abi_version() == 2
+    assert lib.pd_abi_version() == 3
     p = api.pd_sinkhorn_default_params(1e-3, 100)
     assert p.gamma == 1e-3 and p.d == 100 and p.max_iter == 20000 and p.tol == 1e-6
     assert p.precision == api.PD_FP32 and p.absorb_every == 64

@@ -108,6 +108,90 @@ def test_marginals_and_potentials_elementwise_at_d128_gamma1e3(ctx):
         assert abs(g["cost"][p] - r["cost"]) <= 1e-6 * r["cost"]
 
 
+def _pw_rule(h, pairs_a, pairs_b, ratio=2):
+    """The automatic form rule of the iteration kernel, restated: a half-step
+    (input side i, output side o) is pairwise while nnz(i) nnz(o) <=
+    ratio (nnz(i) cols(o) + rows(i) nnz(o))."""
+    nz = h > 0
+    nnz = nz.reshape(len(h), -1).sum(1)
+    rows, cols = nz.any(2).sum(1), nz.any(1).sum(1)
+    out = []
+    for a, b in zip(pairs_a, pairs_b):
+        for i, o in ((b, a), (a, b)):
+            out.append(nnz[i] * nnz[o] <= ratio * (nnz[i] * cols[o] + rows[i] * nnz[o]))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_lse_forms_match_oracle_elementwise_at_d128_gamma1e3(ctx, form):
+    """The separable (1) and pairwise (2) log-sum-exp forms each match the FP64
+    oracle at the benchmark's grid and gamma after 400 fixed iterations:
+    cost 1e-6 relative, marginals and potentials element by element."""
+    d, gamma, T = 128, 1e-3, 400
+    b, t, o = inputs.random_diagrams(8, nmin=50, nmax=500, seed=11)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    g = _solve(ctx, hA, hB, d, gamma, T, 0.0, prm={"lse_form": form}, want_marginals=True, want_potentials=True)
+    assert np.all(g["iters"] == T)
+    for p in range(4):
+        r = oracle.sinkhorn_pd(d, gamma, hA[p], hB[p], T, 0.0)
+        a, bb = oracle.augment(hA[p], hB[p])
+        ma, mb = a > 0, bb > 0
+        assert abs(g["cost"][p] - r["cost"]) <= 1e-6 * r["cost"]
+        assert np.allclose(g["row_marg"][p], r["rmarg"], rtol=5e-6, atol=1e-6)
+        assert np.allclose(g["col_marg"][p], r["cmarg"], rtol=5e-6, atol=1e-6)
+        assert np.allclose(g["f"][p][ma], r["f"][ma], rtol=0, atol=gamma * 2e-5)
+        assert np.allclose(g["g"][p][mb], r["g"][mb], rtol=0, atol=gamma * 2e-5)
+
+
+@pytest.mark.parametrize("d,gamma,nmin,nmax", [(32, 1e-2, 5, 60), (64, 5e-3, 30, 300), (256, 2e-3, 20, 150)])
+def test_lse_forms_converged_against_oracle(ctx, d, gamma, nmin, nmax):
+    """Both forms run to a 1e-6 stop on small and large grids, as the oracle
+    does: costs within 5e-6 of the oracle's and of each other (the stop's own
+    effect), iteration counts within 15 %."""
+    b, t, o = inputs.random_diagrams(8, nmin=nmin, nmax=nmax, seed=d + 3)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    ref = oracle.sinkhorn_pd_batch(d, gamma, hA, hB, 20000, 1e-6)
+    res = {f: _solve(ctx, hA, hB, d, gamma, 20000, 1e-6, prm={"lse_form": f}) for f in (1, 2)}
+    for f, g in res.items():
+        assert np.all(g["status"] == api.PD_OK) and np.all(g["err"] <= 1e-6), (f, g["status"])
+        rel = np.abs(g["cost"] - ref["cost"]) / ref["cost"]
+        assert rel.max() <= 5e-6, (f, rel)
+        assert np.all(np.abs(g["iters"] - ref["iters"]) <= 0.15 * ref["iters"] + 2), (f, g["iters"], ref["iters"])
+    assert (np.abs(res[1]["cost"] - res[2]["cost"]) / ref["cost"]).max() <= 5e-6
+
+
+def test_automatic_form_follows_the_rule(ctx):
+    """Form 0 chooses per half-step: on sparse diagrams at d = 128 (every
+    half-step pairwise by the rule) it equals form 2 bit for bit; on dense
+    histograms at d = 32 (every half-step separable) it equals form 1; for
+    p != 2 the pairwise form is not used, so form 2 equals form 1."""
+    d, gamma = 128, 1e-3
+    b, t, o = inputs.random_diagrams(8, nmin=50, nmax=500, seed=12)
+    h, _ = oracle.rasterize(b, t, o, d)
+    assert _pw_rule(h, range(0, 8, 2), range(1, 8, 2)).all()
+    r0, r1, r2 = (_solve(ctx, h[0::2], h[1::2], d, gamma, 200, 0.0, prm={"lse_form": f}, want_potentials=True)
+                  for f in (0, 1, 2))
+    for k in ("cost", "f", "g", "err"):
+        assert np.array_equal(r0[k], r2[k]), k
+    assert not np.array_equal(r0["f"], r1["f"])   # the forms round differently
+    d = 32
+    b, t, o = inputs.random_diagrams(4, nmin=3000, nmax=3000, seed=13)
+    h, _ = oracle.rasterize(b, t, o, d)
+    assert not _pw_rule(h, [0, 2], [1, 3]).any()
+    r0, r1 = (_solve(ctx, h[0::2], h[1::2], d, 1e-2, 150, 0.0, prm={"lse_form": f}, want_potentials=True)
+              for f in (0, 1))
+    for k in ("cost", "f", "g", "err"):
+        assert np.array_equal(r0[k], r1[k]), k
+    b, t, o = inputs.random_diagrams(4, nmin=50, nmax=200, seed=14)
+    h, _ = oracle.rasterize(b, t, o, 64)
+    r1, r2 = (_solve(ctx, h[0::2], h[1::2], 64, 5e-3, 150, 0.0, prm={"lse_form": f, "p": 1.5}, want_potentials=True)
+              for f in (1, 2))
+    for k in ("cost", "f", "g", "err"):
+        assert np.array_equal(r1[k], r2[k]), k
+
+
 @pytest.mark.parametrize("tier", [0, 1, 2])
 def test_d256_matches_oracle_on_every_tier(ctx, tier):
     """d = 256 (the largest grid) on small diagrams, so the FP64 oracle stays
@@ -131,13 +215,16 @@ def test_d256_matches_oracle_on_every_tier(ctx, tier):
         assert np.allclose(g["g"][p][mb], r["g"][mb], rtol=0, atol=gamma * 2e-5)
 
 
-def test_cta_width_and_widening_leave_results_bitwise_equal(ctx):
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_cta_width_and_widening_leave_results_bitwise_equal(ctx, form):
     """The base-2 kernel sums in the same order at 256, 512 and 1024 threads
     per pair (stage-1 and stage-2 sums are per element or per 4-lane group,
     the Delta sum has a fixed 256-lane partition, the marginal error is an
-    exact fixed-point sum), so costs, potentials, errors and iteration counts
-    are bitwise equal across CTA widths, and handing the last pairs of a
-    launch to wider CTAs (which pairs depends on timing) changes no result."""
+    exact fixed-point sum; the pairwise form's lanes per cell are chosen from
+    the supports at a fixed reference width), so costs, potentials, errors
+    and iteration counts are bitwise equal across CTA widths, and handing the
+    last pairs of a launch to wider CTAs (which pairs depends on timing)
+    changes no result.  Every log-sum-exp form."""
     d, gamma, P = 32, 1e-2, 400
     b, t, o = inputs.random_diagrams(2 * P, nmin=10, nmax=150, seed=77)
     h, _ = oracle.rasterize(b, t, o, d)
@@ -145,7 +232,7 @@ def test_cta_width_and_widening_leave_results_bitwise_equal(ctx):
     for thr in (256, 128, 512, 1024, 0):
         ctx.profile_enable(True)
         before = ctx.profile_read().get("iter", (0.0, 0))[1]
-        runs[thr] = _solve(ctx, h[0::2], h[1::2], d, gamma, 3000, 1e-6, prm={"cta_threads": thr},
+        runs[thr] = _solve(ctx, h[0::2], h[1::2], d, gamma, 3000, 1e-6, prm={"cta_threads": thr, "lse_form": form},
                            want_potentials=True)
         runs[thr]["launches"] = ctx.profile_read().get("iter", (0.0, 0))[1] - before
         ctx.profile_enable(False)
@@ -285,7 +372,7 @@ def test_pairs_index_and_edge_cases(ctx):
 
 def test_invalid_params(ctx):
     h = np.zeros((1, 8, 8), np.uint32); h[0, 1, 2] = 1
-    for kw in (dict(gamma=-1.0), dict(d=300), dict(max_iter=0)):
+    for kw in (dict(gamma=-1.0), dict(d=300), dict(max_iter=0), dict(lse_form=3), dict(lse_form=-1)):
         p = api.pd_sinkhorn_default_params(1e-2, 8)
         for k, v in kw.items():
             setattr(p, k, v)
