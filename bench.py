@@ -354,9 +354,10 @@ def run_ours(args):
         # autotuner: one trial launch per CTA width on this batch; the choice
         # goes into ctx's table and the timed steps use it
         hist_t, mass_t = api.pd_rasterize(ctx, db, dt_, do, d)
-        th, trial = api.pd_sinkhorn_tune(ctx, hist_t, mass_t, hist_t, mass_t, params, pairs=pairs, trial_iters=64)
+        th, trial = api.pd_sinkhorn_tune(ctx, hist_t, mass_t, hist_t, mass_t, params, pairs=pairs,
+                                         trial_iters=args.max_iter)
         tuning = {"chosen_cta_threads": th, "trial_ms": {str(k): v for k, v in trial.items()},
-                  "trial": "one launch per width, all pairs cold-started, 64 iterations each"}
+                  "trial": "one launch per width: the full solve of the batch, cold-started"}
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()

@@ -116,7 +116,8 @@ typedef struct {
     int cta_threads;   /* PD_FP32 iteration kernel: threads of the CTA that runs one pair, 128, 256, 512 or
                           1024; 0 (default) = automatic: the context's tuning table (pd_sinkhorn_tune) when it
                           has an entry for the batch's profile, else the built-in rule (256 while several pairs
-                          share an SM, wider CTAs for the last pairs of a launch).  A fixed width turns the
+                          share an SM, wider CTAs for the last pairs of a launch unless every pair takes the
+                          pairwise form in both half-steps, see lse_form).  A fixed width turns the
                           hand-over of the last pairs to wider CTAs off.  Results do not depend on it: every
                           sum of the kernel has a fixed order whatever the width */
     int kernel_tier;   /* PD_FP32: 0 (default) = automatic (on-chip kernel; its global-memory variant for
@@ -244,16 +245,20 @@ pd_status pd_sinkhorn_bounds(pd_ctx* ctx, const uint32_t* histA, const uint32_t*
  * pd_sinkhorn_tune -- autotuner of the PD_FP32 iteration kernel for a batch
  * profile.  Library feature (the paper has no counterpart).  It runs the
  * batch's pairs (same arguments as pd_sinkhorn_batch; params->precision must
- * be PD_FP32) cold-started for exactly trial_iters iterations, once per
- * candidate width of the CTA that runs one pair (128 threads when d <= 128,
- * 256, 512; one launch each, timed with CUDA events), and records the fastest
+ * be PD_FP32) cold-started, each pair until params->tol or trial_iters
+ * iterations, once per candidate width of the CTA that runs one pair (128
+ * threads when d <= 128, 256, 512; one launch each, timed with CUDA events),
+ * and records the fastest
  * in the context's tuning table under the key (d, support bucket), the
  * bucket being floor(2 log2(mean support cells per side + 1)).  From then on a
  * pd_sinkhorn_batch (or bounds / barycenter / k-means solve) on this context
  * whose batch falls in that key starts with the tuned width (cta_threads = 0),
- * still handing its last pairs to wider CTAs.  Results never depend on the
+ * still handing its last pairs to wider CTAs where the built-in rule does.  Results never depend on the
  * width (fixed-order sums), so tuning changes speed only.
- *   trial_iters   : iterations of each trial (>= 1)
+ *   trial_iters   : iteration cap of each trial (>= 1); params->max_iter makes
+ *                   every trial a full solve, which includes the end of the
+ *                   solve where few pairs are left (a short cold trial of all
+ *                   pairs at once can favour a width that is slower there)
  *   threads_host  : int (host) or NULL: the chosen width
  *   trial_ms_host : double[4] (host) or NULL: kernel time of the trials at
  *                   128, 256, 512, 1024 threads (NaN where not tried)

@@ -414,14 +414,16 @@ static cudaError_t lse_rounds_groups(pd_ctx* c, std::vector<SkWS>& gs, SkWS* dev
     const int max_rounds = r.max_iter / n_inner + 6;
     const int gbits = sk_lse2_grid_bits(gs[0].gamma);
     size_t smem = 0;
+    bool pw_all = false;   // every on-chip pair pairwise in both half-steps
     if (gbits >= 0) {
-        if ((e = cudaMemsetAsync(counter + 2, 0, sizeof(int), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(counter + 2, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
         for (int gi = 0; gi < G; ++gi)
             if ((e = sk_launch_lse2_need(gs[gi], counter + 2, r.form, s)) != cudaSuccess) return e;
-        if ((e = cudaMemcpyAsync(hbuf + 2, counter + 2, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        if ((e = cudaMemcpyAsync(hbuf + 2, counter + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return e;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
         smem = (size_t)hbuf[2];
+        pw_all = hbuf[3] == 0;
     }
     // CTA width of the base-2 kernel: 256 threads while there are several pairs
     // per SM, wider CTAs (more warps on one pair) once fewer pairs than SMs
@@ -455,7 +457,11 @@ static cudaError_t lse_rounds_groups(pd_ctx* c, std::vector<SkWS>& gs, SkWS* dev
             // side), so that the SM still runs 16-32 warps; the first width
             // comes from the tuning table (base_threads) or is 256
             const int base = (r.base_threads == 128 && dmax <= 128) || r.base_threads == 512 ? r.base_threads : 256;
-            const int by_active = active > 2 * nsm ? base : (active > nsm ? std::max(base, 512) : 1024);
+            // (pairwise form only: a pair keeps its width; one pair nearly
+            // fills an SM's issue slots in that form, a wider CTA was measured
+            // no faster, and each hand-over costs a reload)
+            const int by_active =
+                pw_all || active > 2 * nsm ? base : (active > nsm ? std::max(base, 512) : 1024);
             const int by_smem = fit_per_sm <= 1 ? 1024 : (fit_per_sm == 2 ? 512 : 128);
             const int threads = fixed_threads ? fixed_threads : (by_active > by_smem ? by_active : by_smem);
             // Widening: a pair alone on an SM iterates ~2x faster in a
@@ -464,7 +470,7 @@ static cudaError_t lse_rounds_groups(pd_ctx* c, std::vector<SkWS>& gs, SkWS* dev
             // them over to 512 (1024)-thread CTAs.
             SkRun rl = r;
             rl.exit_at = 0;
-            if (!fixed_threads && gbits >= 0 && n_inner == r.max_iter) {
+            if (!fixed_threads && !pw_all && gbits >= 0 && n_inner == r.max_iter) {
                 if (threads <= 256) rl.exit_at = active - 2 * nsm;
                 else if (threads == 512) rl.exit_at = active - nsm;
             }
@@ -1219,7 +1225,6 @@ extern "C" pd_status pd_sinkhorn_tune(pd_ctx* c, const uint32_t* histA, const ui
     SkRun r = make_run(prm);
     r.max_iter = trial_iters;
     r.max_inner = trial_iters;
-    r.tol = 0.0;
     const int cands[4] = {128, 256, 512, 1024};
     double ms[4] = {NAN, NAN, NAN, NAN};
     const bool prof_was = c->prof;
@@ -1228,7 +1233,7 @@ extern "C" pd_status pd_sinkhorn_tune(pd_ctx* c, const uint32_t* histA, const ui
     double mean_cells = 0.0;
     for (int k = 0; k < 3; ++k) {   // 1024 serves only the drain
         if (cands[k] == 128 && prm->d > 128) continue;
-        // identical trials: the same cold start, the same iterations, one launch of one width
+        // identical trials: the same cold start, each pair to tol or trial_iters, one launch of one width
         CUDA_TRY(c, sk_launch_setup(w, nullptr, s));
         r.cta_threads = cands[k];
         for (auto& rc : c->recs) { c->ev_pool.push_back(rc.a); c->ev_pool.push_back(rc.b); }

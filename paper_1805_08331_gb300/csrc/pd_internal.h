@@ -138,6 +138,8 @@ cudaError_t sk_launch_lse_smem(const SkWS& w, SkRun r, int n_inner, int* active_
 int sk_lse2_grid_bits(double gamma);
 // gamma-continuation inside the iteration kernel: ic[IC_STAGE] = K for every pair
 cudaError_t sk_launch_set_stage(const SkWS& w, int K, cudaStream_t s);
+// Shared memory of the on-chip pairs: max_need[0] = the largest need;
+// max_need[1] += pairs not pairwise in both half-steps.
 cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, int form, cudaStream_t s);
 // counter: [0] active pairs, [1] pairs moved to the global-memory variant,
 // [2] (need kernel) max shared bytes, [3] pairs moved to the FP64 kernel.

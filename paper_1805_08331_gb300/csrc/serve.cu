@@ -377,7 +377,8 @@ cudaError_t serve_round(pd_server* sv, int pi, std::vector<Req*>& pending) {
     int smem_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, sv->device);
     const int fit_per_sm = smem > 0 ? (int)((size_t)smem_sm / (smem + 2048)) : 3;
-    const int by_active = na > 2 * nsm ? 256 : (na > nsm ? 512 : 1024);
+    const bool pw_all = ((int*)P.h_cnt.p)[3] == 0;   // every pair pairwise: no widening
+    const int by_active = pw_all || na > 2 * nsm ? 256 : (na > nsm ? 512 : 1024);
     const int by_smem = fit_per_sm <= 1 ? 1024 : (fit_per_sm == 2 ? 512 : 256);
     const int threads = by_active > by_smem ? by_active : by_smem;
     SV_TRY(cudaMemsetAsync(P.counter, 0, sizeof(int) * 4, P.stream));

@@ -588,46 +588,33 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
     if (out_nch == 0) __syncthreads();
 }
 
-// Lanes per output cell of the pairwise form: the fewest (passes x input
-// cells per lane) at a reference width of 256 threads.  It depends on the
-// supports only, so the partition of every sum, and the result, is the same
-// at every CTA width.
-__device__ __forceinline__ int l2_pw_lanes(int n_in, int m) {
-    int G = 1, best = 0x7fffffff;
-    for (int gg = 1, lg = 0; gg <= 8; gg <<= 1, ++lg) {
-        const int passes = (m * gg + 255) / 256;
-        const int c = passes * ((n_in + gg - 1) / gg + 8 * lg + 24);
-        if (c < best) { best = c; G = gg; }
-    }
-    return G;
-}
-
 // Pairwise form of a half-step (p = 2, on chip): the same log-sum-exp as the
 // separable form, summed over the input support directly,
 //   out_x = -LSE( { h_y - s D_xy : y in supp(in) } u { h_D - cD_x/gamma } ),
 // with the shift Ms = -(previous out_x) and the exact hi words of
 // l2_pw_consts: per term two packed differences give (i-k, j-l), D is exact,
-// one packed FMA gives (h_y.hi - s1 D, h_y.lo - s2 D), then ex2.  G lanes per
-// output cell split the input cells (y = g, g + G, ...); a lane adds blocks of
-// four terms and sums the blocks compensated (Kahan); the G partial sums meet
-// in a fixed shuffle tree.
+// one packed FMA gives (h_y.hi - s1 D, h_y.lo - s2 D), then ex2.  One lane per
+// output cell runs over all input cells in order (every lane of a warp reads
+// the same record: one broadcast load); it adds blocks of eight terms (then
+// one of four), left to right, and sums the blocks compensated (Kahan), then
+// the last records and the Delta term.  The partition does not depend on the
+// CTA width, so neither does any result.  (Measured slower on the benchmark
+// batch: several lanes per cell over strided parts of the input, 10 %; two
+// cells per lane in packed arithmetic, 25 %: half the warps busy.)
 template <int NT>
 static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bool want_err, long long& errq,
                                   bool& errbad, float* redD, int* range_flag) {
     l2_delta_out<NT, false>(in, out, K, want_err, errq, errbad, redD, range_flag, nullptr);
-    const int t = threadIdx.x, lane = t & 31;
+    const int t = threadIdx.x;
     const int n_in = in.n, m = out.n;
     const float4* rec_in = smp<float4>(in.rec);
     const float4* rec_out = smp<float4>(out.rec);
     float2* out_pot = smp<float2>(out.pot);
     const float2* cdt = smp<float2>(K.cdt);
     const float2 hD = in.hinD;   // input Delta term (not written in this half-step)
-    const int G = l2_pw_lanes(n_in, m);
-    const int g = lane & (G - 1);
-    const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
     const float2 ns = make_float2(-K.s1, -K.s2);
-    for (int e0 = 0; e0 < m; e0 += NT / G) {
-        const int e = e0 + t / G;
+    for (int e0 = 0; e0 < m; e0 += NT) {
+        const int e = e0 + t;
         const bool live = e < m;
         float2 xij = make_float2(0.f, 0.f), po = make_float2(0.f, 0.f);
         if (live) {
@@ -639,12 +626,24 @@ static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bo
         float tot = 0.f;
         if (live) {
             float sm = 0.f, cm = 0.f;
-            int y = g;
-            for (; y + 3 * G < n_in; y += 4 * G) {
+            int y = 0;
+            for (; y + 7 < n_in; y += 8) {
+                float ev[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float4 r = rec_in[y + u];
+                    const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
+                    const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
+                    const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
+                    ev[u] = l2_ex2((hl.x - Ms) + hl.y);
+                }
+                kahan_add(sm, cm, ((ev[0] + ev[1]) + (ev[2] + ev[3])) + ((ev[4] + ev[5]) + (ev[6] + ev[7])));
+            }
+            for (; y + 3 < n_in; y += 4) {
                 float ev[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const float4 r = rec_in[y + u * G];
+                    const float4 r = rec_in[y + u];
                     const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
                     const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
                     const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
@@ -653,51 +652,51 @@ static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bo
                 kahan_add(sm, cm, (ev[0] + ev[1]) + (ev[2] + ev[3]));
             }
             float rest = 0.f;
-            for (; y < n_in; y += G) {
+#pragma unroll 1
+            for (; y < n_in; ++y) {
                 const float4 r = rec_in[y];
                 const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
                 const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
                 const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
                 rest += l2_ex2((hl.x - Ms) + hl.y);
             }
-            if (g == 0 && hD.x > -INFINITY) {
+            if (hD.x > -INFINITY) {
                 const float2 c = cdt[abs((int)xij.y - (int)xij.x)];
                 rest += l2_ex2(((hD.x - c.x) - Ms) + (hD.y - c.y));
             }
             kahan_add(sm, cm, rest);
             tot = sm - cm;
         }
-        for (int o = 1; o < G; o <<= 1) tot += __shfl_xor_sync(gmask, tot, o);
         float shift = Ms;
         if (live && !(tot >= 0x1p-100f && tot <= 0x1p100f)) {
             // exact maximum of the terms; an integer shift (on every grid) at or
             // above it keeps every term at most 1 and the largest above 1/2
             float mx = -INFINITY;
-            for (int y = g; y < n_in; y += G) {
+#pragma unroll 1
+            for (int y = 0; y < n_in; ++y) {
                 const float4 r = rec_in[y];
                 const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
                 const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
                 mx = fmaxf(mx, fmaf(ns.x, D, r.x));
             }
-            if (g == 0 && hD.x > -INFINITY) mx = fmaxf(mx, hD.x - cdt[abs((int)xij.y - (int)xij.x)].x);
-            for (int o = 1; o < G; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(gmask, mx, o));
+            if (hD.x > -INFINITY) mx = fmaxf(mx, hD.x - cdt[abs((int)xij.y - (int)xij.x)].x);
             shift = ceilf(mx);
             float sm = 0.f, cm = 0.f;
-            for (int y = g; y < n_in; y += G) {
+#pragma unroll 1
+            for (int y = 0; y < n_in; ++y) {
                 const float4 r = rec_in[y];
                 const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
                 const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
                 const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
                 kahan_add(sm, cm, l2_ex2((hl.x - shift) + hl.y));
             }
-            if (g == 0 && hD.x > -INFINITY) {
+            if (hD.x > -INFINITY) {
                 const float2 c = cdt[abs((int)xij.y - (int)xij.x)];
                 kahan_add(sm, cm, l2_ex2(((hD.x - c.x) - shift) + (hD.y - c.y)));
             }
             tot = sm - cm;
-            for (int o = 1; o < G; o <<= 1) tot += __shfl_xor_sync(gmask, tot, o);
         }
-        if (live && g == 0) {
+        if (live) {
             float2 pn;
             if (l2_update(tot, shift, Ms, po, smp<float>(out.w)[e], want_err, K, errq, errbad, pn)) {
                 out_pot[e] = pn;
@@ -1051,9 +1050,10 @@ __global__ void sk_lse2_need_kernel(SkWS w, int* max_need, int form) {
         ncB += q.cpb[i + 1] > q.cpb[i];
     }
     const int nA = q.ic[IC_NA], nB = q.ic[IC_NB];
-    const size_t need = l2_need(nA, nB, nrA, nrB, w.d, l2_pw_half(nB, nrB, nA, ncA, form, w.p == 2.0),
-                                l2_pw_half(nA, nrA, nB, ncB, form, w.p == 2.0));
+    const bool pwU = l2_pw_half(nB, nrB, nA, ncA, form, w.p == 2.0), pwV = l2_pw_half(nA, nrA, nB, ncB, form, w.p == 2.0);
+    const size_t need = l2_need(nA, nB, nrA, nrB, w.d, pwU, pwV);
     atomicMax(max_need, (int)(need > 0x7fffffff ? 0x7fffffff : need));
+    if (!(pwU && pwV)) atomicAdd(max_need + 1, 1);
 }
 
 cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, int form, cudaStream_t s) {
