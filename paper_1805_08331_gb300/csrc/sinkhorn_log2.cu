@@ -245,34 +245,74 @@ struct L2Consts {
     int d;
     float gsc, ginv, lim;
     float escale;    // 2^40 / total mass (marginal-error terms in fixed point)
-    float s1, s2;    // pairwise form (p = 2): c_xy/gamma in log2 units = (s1 + s2) D, D = |x - y|^2 in cells
-    bool pw_ok;      // the pairwise form is exact at this gamma (p = 2)
+    // pairwise form (p = 2): c_xy/gamma in log2 units = s D, D = |x - y|^2 in
+    // cells, s = log2(e) / (gamma d^2); it runs in units of kap log2 with
+    // sp = s / kap = n1 2^-G on the grid (see l2_pw_consts)
+    float sp, kap, rho_h, rho_l;   // sp; kap; 1/kap - 1 as a two-float sum
+    bool pw_ok;      // the pairwise form is available at this gamma
     int form;        // 0 automatic, 1 separable only, 2 pairwise wherever pw_ok
 };
 
-// Pairwise-form constants at this gamma (p = 2): c_xy/gamma in log2 units is
-// s D with D = (i-k)^2 + (j-l)^2 <= 2 (d-1)^2, an integer exact in FP32, and
-// s = log2(e) / (gamma d^2).  s = s1 + s2 with s1 on the finest grid 2^-Gs
-// (Gs >= G) such that s1 D is exact and every hi word (h_y - Ms) - s1 D lies
-// below 2^(24-Gs) (potentials below 2^(21-G), log2 weights below 64), so the
-// hi words are exact; s2 D joins the rest word.  pw_ok = false otherwise.
-__device__ __forceinline__ void l2_pw_consts(L2Consts& K, double gamma, int d, int gbits, double pw) {
-    K.pw_ok = false;
-    K.s1 = 0.f;
-    K.s2 = 0.f;
-    if (pw != 2.0) return;
+// Pairwise-form constants at this gamma (p = 2).  The form sums in scaled
+// units: a log2-unit value v is v' = v / kap, with kap = s / sp and sp = n1 2^-G
+// the grid value nearest s (n1 >= 4, so kap lies in [7/8, 9/8]).  In those
+// units a term's exponent is
+//   kap ( (h'.hi - sp D - Ms') + h'.lo ),   D = (i-k)^2 + (j-l)^2,
+// and h'.hi - sp D - Ms' = A_y + B_x + 2 sp (i k + j l) with A_y = h'.hi -
+// sp (k^2 + l^2) per input cell and B_x = -sp (i^2 + j^2) - Ms' per output
+// cell: every product and partial sum is a multiple of 2^-G below 2^(24-G)
+// (checked here), hence exact in FP32, and kap multiplies only the small
+// result.  pw_ok = false (the separable form runs) when no such n1 exists.
+// Grid of the (hi, lo) words at the target gamma: 2^-G with 2^(23-G) >= 8
+// (max cost/gamma + 64) in log2 units; -1 when G would fall below 4.
+__host__ __device__ inline int l2_grid_bits(double gamma) {
+    const double cmax = 2.0 / gamma * 1.4426950408889634 + 64.0;
+    int e = 0;
+    while (ldexp(1.0, e) < 8.0 * cmax && e < 64) ++e;
+    const int g = 23 - e;
+    return g >= 4 ? (g > 12 ? 12 : g) : -1;
+}
+
+struct L2PwC {
+    double sp, kap, rho;
+    bool ok;
+};
+__host__ __device__ inline L2PwC l2_pw_calc(double gamma, int d, int gbits, double pw) {
+    L2PwC c{0.0, 1.0, 0.0, false};
+    if (pw != 2.0 || gbits < 0) return c;
     const double s = 1.4426950408889634 / (gamma * (double)d * (double)d);
-    const double dmax = 2.0 * (double)(d - 1) * (double)(d - 1);
-    const double bhi = ldexp(1.0, 22 - gbits) + 64.0 + s * dmax;
-    for (int gs = gbits + 8; gs >= gbits; --gs) {
-        const double n1 = rint(ldexp(s, gs));
-        if (ldexp(1.0, 24 - gs) >= bhi && n1 * dmax < 16777216.0) {
-            K.s1 = (float)ldexp(n1, -gs);
-            K.s2 = (float)(s - ldexp(n1, -gs));
-            K.pw_ok = true;
-            return;
-        }
-    }
+    const double n1 = rint(ldexp(s, gbits));
+    if (n1 < 4.0) return c;
+    c.sp = ldexp(n1, -gbits);
+    c.kap = (double)(float)(s / c.sp);   // the FP32 value the kernel multiplies by
+    c.rho = 1.0 / c.kap - 1.0;
+    const double q = (double)(d - 1) * (double)(d - 1), dmax = 2.0 * q;
+    // |h'| and |Ms'| (potentials below 2^(21-G), log2 weights below 64) plus the
+    // cost words of every partial sum of A_y + B_x + 2 sp (j l) + 2 sp (i k)
+    const double bound = (ldexp(1.0, 22 - gbits) + 128.0) * (1.0 + fabs(c.rho)) + 3.0 * c.sp * dmax;
+    c.ok = bound < ldexp(1.0, 24 - gbits) && 2.0 * n1 * q < 16777216.0 && n1 * dmax < 16777216.0;
+    return c;
+}
+__device__ __forceinline__ void l2_pw_consts(L2Consts& K, double gamma, int d, int gbits, double pw) {
+    const L2PwC c = l2_pw_calc(gamma, d, gbits, pw);
+    K.pw_ok = c.ok;
+    K.sp = (float)c.sp;
+    K.kap = (float)c.kap;
+    K.rho_h = (float)c.rho;
+    K.rho_l = (float)(c.rho - (double)(float)c.rho);
+}
+
+// The pairwise record of an input cell (row k, column l) from its h = (hi, lo)
+// in log2 units: h' = h / kap = h (1 + rho) split into h'.hi on the grid and
+// h'.lo (two-float products: hi rho = p + pe exactly), then
+// (A = h'.hi - sp (k^2 + l^2), kap h'.lo, k, l).
+__device__ __forceinline__ float4 l2_pw_record(float2 h, float k, float l, const L2Consts& K) {
+    const float p = h.x * K.rho_h;
+    const float pe = fmaf(h.x, K.rho_h, -p);
+    const float ph = l2_round(p, K.gsc, K.ginv);
+    const float hi = h.x + ph;
+    const float lo = (p - ph) + (pe + fmaf(h.x, K.rho_l, fmaf(h.y, K.rho_h, h.y)));
+    return make_float4(fmaf(-K.sp, fmaf(k, k, l * l), hi), K.kap * lo, k, l);
 }
 
 // Packed FP32 pair arithmetic (two lanes of one 64-bit register pair).
@@ -576,7 +616,7 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
                         const float2 lw = sdp<float2, GM>(gb, out.lw)[qo];
                         const float2 hn = make_float2(lw.x + pn.x, lw.y + pn.y);
                         sdp<float2, GM>(gb, out.hin)[qo] = hn;
-                        if (!GM && K.pw_ok) *smp<float2>(out.rec + 16 * qo) = hn;
+                        if (!GM && K.pw_ok) smp<float4>(out.rec)[qo] = l2_pw_record(hn, (float)i, (float)j, K);
                     } else {
                         atomicOr(range_flag, 1);
                     }
@@ -588,17 +628,26 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
     if (out_nch == 0) __syncthreads();
 }
 
+// One pairwise term in the scaled units of l2_pw_consts: r = (A_y, kap h'.lo,
+// k, l); B = B_x, a = 2 sp i, b = 2 sp j.  The hi word A_y + B_x + b l + a k
+// is exact; kap multiplies it and adds kap h'.lo in one rounding.
+__device__ __forceinline__ float l2_pw_term(const float4& r, float B, float a, float b, float kap) {
+    return l2_ex2(fmaf(kap, fmaf(a, r.z, fmaf(b, r.w, r.x + B)), r.y));
+}
+
 // Pairwise form of a half-step (p = 2, on chip): the same log-sum-exp as the
 // separable form, summed over the input support directly,
 //   out_x = -LSE( { h_y - s D_xy : y in supp(in) } u { h_D - cD_x/gamma } ),
-// with the shift Ms = -(previous out_x) and the exact hi words of
-// l2_pw_consts: per term two packed differences give (i-k, j-l), D is exact,
-// one packed FMA gives (h_y.hi - s1 D, h_y.lo - s2 D), then ex2.  One lane per
-// output cell runs over all input cells in order (every lane of a warp reads
-// the same record: one broadcast load); it adds blocks of eight terms (then
-// one of four), left to right, and sums the blocks compensated (Kahan), then
-// the last records and the Delta term.  The partition does not depend on the
-// CTA width, so neither does any result.  (Measured slower on the benchmark
+// in the scaled units of l2_pw_consts: per output cell, Ms' = the grid value
+// nearest Ms / kap (Ms = -(previous out_x)), B_x = -sp (i^2 + j^2) - Ms', and
+// delta = kap Ms' - Ms; per term one shared record, FADD + 2 FFMA (the exact hi
+// word), FFMA (kap hi + kap lo) and ex2: the terms are shifted by kap Ms' = Ms +
+// delta, so tot = (their sum) 2^delta + (the Delta term shifted by Ms).  One
+// lane per output cell runs over all input cells in order (every lane of a
+// warp reads the same record: one broadcast load); it adds blocks of eight
+// terms (then one of four), left to right, and sums the blocks compensated
+// (Kahan), then the last records.  The partition does not depend on the CTA
+// width, so neither does any result.  (Measured slower on the benchmark
 // batch: several lanes per cell over strided parts of the input, 10 %; two
 // cells per lane in packed arithmetic, 25 %: half the warps busy.)
 template <int NT>
@@ -608,105 +657,84 @@ static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bo
     const int t = threadIdx.x;
     const int n_in = in.n, m = out.n;
     const float4* rec_in = smp<float4>(in.rec);
-    const float4* rec_out = smp<float4>(out.rec);
+    float4* rec_out = smp<float4>(out.rec);
     float2* out_pot = smp<float2>(out.pot);
     const float2* cdt = smp<float2>(K.cdt);
     const float2 hD = in.hinD;   // input Delta term (not written in this half-step)
-    const float2 ns = make_float2(-K.s1, -K.s2);
+    const float kap = K.kap, sp = K.sp;
     for (int e0 = 0; e0 < m; e0 += NT) {
         const int e = e0 + t;
-        const bool live = e < m;
-        float2 xij = make_float2(0.f, 0.f), po = make_float2(0.f, 0.f);
-        if (live) {
+        if (e >= m) continue;
+        float sum, Mp;
+        {
+            // the sum over the records, shifted by kap Ms' (Ms' on the grid);
+            // only what the loop needs is live across it
             const float4 rx = rec_out[e];
-            xij = make_float2(rx.z, rx.w);
-            po = out_pot[e];
-        }
-        const float Ms = -po.x;
-        float tot = 0.f;
-        if (live) {
+            const float Ms = -out_pot[e].x;
+            Mp = Ms + l2_round(Ms * K.rho_h, K.gsc, K.ginv);
+            const float a = 2.f * sp * rx.z, b = 2.f * sp * rx.w;
+            const float B = fmaf(-sp, fmaf(rx.z, rx.z, rx.w * rx.w), -Mp);
             float sm = 0.f, cm = 0.f;
             int y = 0;
             for (; y + 7 < n_in; y += 8) {
                 float ev[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float4 r = rec_in[y + u];
-                    const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
-                    const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
-                    const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
-                    ev[u] = l2_ex2((hl.x - Ms) + hl.y);
-                }
+                for (int u = 0; u < 8; ++u) ev[u] = l2_pw_term(rec_in[y + u], B, a, b, kap);
                 kahan_add(sm, cm, ((ev[0] + ev[1]) + (ev[2] + ev[3])) + ((ev[4] + ev[5]) + (ev[6] + ev[7])));
             }
             for (; y + 3 < n_in; y += 4) {
                 float ev[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float4 r = rec_in[y + u];
-                    const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
-                    const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
-                    const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
-                    ev[u] = l2_ex2((hl.x - Ms) + hl.y);
-                }
+                for (int u = 0; u < 4; ++u) ev[u] = l2_pw_term(rec_in[y + u], B, a, b, kap);
                 kahan_add(sm, cm, (ev[0] + ev[1]) + (ev[2] + ev[3]));
             }
             float rest = 0.f;
 #pragma unroll 1
-            for (; y < n_in; ++y) {
-                const float4 r = rec_in[y];
-                const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
-                const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
-                const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
-                rest += l2_ex2((hl.x - Ms) + hl.y);
-            }
-            if (hD.x > -INFINITY) {
-                const float2 c = cdt[abs((int)xij.y - (int)xij.x)];
-                rest += l2_ex2(((hD.x - c.x) - Ms) + (hD.y - c.y));
-            }
+            for (; y < n_in; ++y) rest += l2_pw_term(rec_in[y], B, a, b, kap);
             kahan_add(sm, cm, rest);
-            tot = sm - cm;
+            sum = sm - cm;
         }
+        const float4 rx = rec_out[e];
+        const float xi = rx.z, xj = rx.w;
+        const float2 po = out_pot[e];
+        const float Ms = -po.x;
+        const float2 cD = cdt[abs((int)xj - (int)xi)];
+        // the records' terms are 2^(x - delta) (shift kap Ms' = Ms + delta, x the
+        // exponent shifted by Ms): their sum times 2^delta, plus the Delta term
+        float tot = fmaf(sum, exp2f(fmaf(kap, Mp, -Ms)),
+                         hD.x > -INFINITY ? l2_ex2(((hD.x - cD.x) - Ms) + (hD.y - cD.y)) : 0.f);
         float shift = Ms;
-        if (live && !(tot >= 0x1p-100f && tot <= 0x1p100f)) {
-            // exact maximum of the terms; an integer shift (on every grid) at or
-            // above it keeps every term at most 1 and the largest above 1/2
+        if (!(tot >= 0x1p-100f && tot <= 0x1p100f)) {
+            // exact maximum of the terms (hi words, scaled units, shift 0); an
+            // integer shift at or above kap times it keeps every term at most
+            // about 1 and the largest near 1
+            const float a = 2.f * sp * xi, b = 2.f * sp * xj;
+            const float B0 = -sp * fmaf(xi, xi, xj * xj);
             float mx = -INFINITY;
 #pragma unroll 1
             for (int y = 0; y < n_in; ++y) {
                 const float4 r = rec_in[y];
-                const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
-                const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
-                mx = fmaxf(mx, fmaf(ns.x, D, r.x));
+                mx = fmaxf(mx, kap * fmaf(a, r.z, fmaf(b, r.w, r.x + B0)));
             }
-            if (hD.x > -INFINITY) mx = fmaxf(mx, hD.x - cdt[abs((int)xij.y - (int)xij.x)].x);
+            if (hD.x > -INFINITY) mx = fmaxf(mx, hD.x - cD.x);
             shift = ceilf(mx);
+            const float Mf = shift + l2_round(shift * K.rho_h, K.gsc, K.ginv);
+            const float B = fmaf(-sp, fmaf(xi, xi, xj * xj), -Mf);
             float sm = 0.f, cm = 0.f;
 #pragma unroll 1
-            for (int y = 0; y < n_in; ++y) {
-                const float4 r = rec_in[y];
-                const float2 dd = f2_sub(xij, make_float2(r.z, r.w));
-                const float D = fmaf(dd.x, dd.x, dd.y * dd.y);
-                const float2 hl = f2_fma(ns, make_float2(D, D), make_float2(r.x, r.y));
-                kahan_add(sm, cm, l2_ex2((hl.x - shift) + hl.y));
-            }
-            if (hD.x > -INFINITY) {
-                const float2 c = cdt[abs((int)xij.y - (int)xij.x)];
-                kahan_add(sm, cm, l2_ex2(((hD.x - c.x) - shift) + (hD.y - c.y)));
-            }
-            tot = sm - cm;
+            for (int y = 0; y < n_in; ++y) kahan_add(sm, cm, l2_pw_term(rec_in[y], B, a, b, kap));
+            tot = fmaf(sm - cm, exp2f(fmaf(kap, Mf, -shift)),
+                       hD.x > -INFINITY ? l2_ex2(((hD.x - cD.x) - shift) + (hD.y - cD.y)) : 0.f);
         }
-        if (live) {
-            float2 pn;
-            if (l2_update(tot, shift, Ms, po, smp<float>(out.w)[e], want_err, K, errq, errbad, pn)) {
-                out_pot[e] = pn;
-                const float2 lw = smp<float2>(out.lw)[e];
-                const float2 hn = make_float2(lw.x + pn.x, lw.y + pn.y);
-                smp<float2>(out.hin)[e] = hn;
-                *smp<float2>(out.rec + 16 * e) = hn;
-            } else {
-                atomicOr(range_flag, 1);
-            }
+        float2 pn;
+        if (l2_update(tot, shift, Ms, po, smp<float>(out.w)[e], want_err, K, errq, errbad, pn)) {
+            out_pot[e] = pn;
+            const float2 lw = smp<float2>(out.lw)[e];
+            const float2 hn = make_float2(lw.x + pn.x, lw.y + pn.y);
+            smp<float2>(out.hin)[e] = hn;
+            rec_out[e] = l2_pw_record(hn, xi, xj, K);
+        } else {
+            atomicOr(range_flag, 1);
         }
     }
     __syncthreads();
@@ -734,7 +762,10 @@ static __device__ void l2_next_stage(L2Side* S, const L2Consts& K, double gamma_
             xpot[e] = pn;
             const float2 hn = make_float2(xlw[e].x + pn.x, xlw[e].y + pn.y);
             xhin[e] = hn;
-            if (!GM && K.pw_ok) *smp<float2>(X.rec + 16 * e) = hn;
+            if (!GM && K.pw_ok) {
+                float4* xr = smp<float4>(X.rec) + e;
+                *xr = l2_pw_record(hn, xr->z, xr->w, K);
+            }
         }
     }
     __syncthreads();   // every thread has read the sides' Delta state (hinD in the half-steps) before t == 0 writes it
@@ -814,8 +845,10 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     if constexpr (!GM) {
         l2_compact(q.cpa, d, nullptr, &cnt[2], nullptr, wcnt);
         l2_compact(q.cpb, d, nullptr, &cnt[3], nullptr, wcnt);
-        pwU = l2_pw_half(nB, nrB, nA, cnt[2], r.form, W.p == 2.0);
-        pwV = l2_pw_half(nA, nrA, nB, cnt[3], r.form, W.p == 2.0);
+        // the pairwise form at this pair's starting gamma (later stages keep it)
+        const bool p2 = l2_pw_calc(gamma_k, d, gbits, W.p).ok;
+        pwU = l2_pw_half(nB, nrB, nA, cnt[2], r.form, p2);
+        pwV = l2_pw_half(nA, nrA, nB, cnt[3], r.form, p2);
     }
     if (t == 0) {
         if (GM)
@@ -870,9 +903,16 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     const int nrmax = nrA > nrB ? nrA : nrB;
     K.L1 = take((pwU && pwV) ? 0 : 8 * (size_t)L2_CW * nrmax);
     __syncthreads();
-    // ---- load
     const double gsc = ldexp(1.0, gbits);
     const double LOG2E = 1.4426950408889634;
+    K.d = d;
+    K.gsc = (float)gsc; K.ginv = (float)(1.0 / gsc);
+    K.lim = (float)ldexp(1.0, 21 - gbits);   // |potential| bound keeping every sum of grid words exact
+    K.escale = q.sc[SC_TOTAL] > 0 ? (float)(ldexp(1.0, 40) / q.sc[SC_TOTAL]) : 0.f;
+    K.form = r.form;
+    l2_pw_consts(K, gamma_k, d, gbits, W.p);
+    K.pw_ok = K.pw_ok && (pwU || pwV);
+    // ---- load
     {
         const int* lists[2] = {q.sa, q.sb};
         const double* lw[2] = {q.la, q.lb};
@@ -899,8 +939,8 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
                 const float2 p2 = l2_split(pot[s][c] * LOG2E, gsc);
                 xlw[e] = l2; xpot[e] = p2;
                 xhin[e] = make_float2(l2.x + p2.x, l2.y + p2.y);
-                if (!GM && (pwU || pwV))
-                    smp<float4>(X.rec)[e] = make_float4(l2.x + p2.x, l2.y + p2.y, (float)i, (float)j);
+                if (!GM && K.pw_ok)
+                    smp<float4>(X.rec)[e] = l2_pw_record(make_float2(l2.x + p2.x, l2.y + p2.y), (float)i, (float)j, K);
                 xw[e] = wt[s][c];
             }
             for (int i = t; i <= d; i += NT) xrp[i] = rps[s][i];
@@ -933,13 +973,6 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     __syncthreads();
     l2_chunks<GM>(S[0], wcnt, gb);
     l2_chunks<GM>(S[1], wcnt, gb);
-    K.d = d;
-    K.gsc = (float)gsc; K.ginv = (float)(1.0 / gsc);
-    K.lim = (float)ldexp(1.0, 21 - gbits);   // |potential| bound keeping every sum of grid words exact
-    K.escale = q.sc[SC_TOTAL] > 0 ? (float)(ldexp(1.0, 40) / q.sc[SC_TOTAL]) : 0.f;
-    K.form = r.form;
-    l2_pw_consts(K, gamma_k, d, gbits, W.p);
-    K.pw_ok = K.pw_ok && (pwU || pwV);
     const float tolf = (float)r.tol, stage_tolf = (float)r.stage_tol;
     int iters = q.ic[IC_ITERS];
     float errf = (float)q.sc[SC_ERR];
@@ -975,12 +1008,16 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
         if (!isfinite(errf)) { status = ST_RANGE; break; }
         if (stage_done) {
             --stage;
-            l2_next_stage<NT, GM>(S, K, ldexp(W.gamma, 2 * stage), W.p, d, &range_flag, gb);
             {
+                // the pairwise constants of the new gamma first: the stage step
+                // rebuilds the records with them (a pair that had the pairwise
+                // form keeps it: smaller gamma only moves n1 up)
                 const bool keep = K.pw_ok;
                 l2_pw_consts(K, ldexp(W.gamma, 2 * stage), d, gbits, W.p);
+                if (keep && !K.pw_ok && t == 0) range_flag = 1;   // not reached; the FP64 kernel would take over
                 K.pw_ok = K.pw_ok && keep;
             }
+            l2_next_stage<NT, GM>(S, K, ldexp(W.gamma, 2 * stage), W.p, d, &range_flag, gb);
             if (range_flag) { moved = true; break; }
         }
         if (leave) break;   // status stays ST_ACTIVE: relaunched in a wider CTA
@@ -1050,7 +1087,9 @@ __global__ void sk_lse2_need_kernel(SkWS w, int* max_need, int form) {
         ncB += q.cpb[i + 1] > q.cpb[i];
     }
     const int nA = q.ic[IC_NA], nB = q.ic[IC_NB];
-    const bool pwU = l2_pw_half(nB, nrB, nA, ncA, form, w.p == 2.0), pwV = l2_pw_half(nA, nrA, nB, ncB, form, w.p == 2.0);
+    // the pairwise form at this pair's current gamma (later stages keep it)
+    const bool p2 = l2_pw_calc(ldexp(w.gamma, 2 * q.ic[IC_STAGE]), w.d, l2_grid_bits(w.gamma), w.p).ok;
+    const bool pwU = l2_pw_half(nB, nrB, nA, ncA, form, p2), pwV = l2_pw_half(nA, nrA, nB, ncB, form, p2);
     const size_t need = l2_need(nA, nB, nrA, nrB, w.d, pwU, pwV);
     atomicMax(max_need, (int)(need > 0x7fffffff ? 0x7fffffff : need));
     if (!(pwU && pwV)) atomicAdd(max_need + 1, 1);
@@ -1069,13 +1108,7 @@ cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, int form, cudaStre
 // margin for log-weights, which bounds every argument the kernel forms.
 // Returns -1 when gamma is too small for a grid of at least 2^-4 (the caller
 // then uses the FP64-argument kernels).
-int sk_lse2_grid_bits(double gamma) {
-    const double cmax = 2.0 / gamma * 1.4426950408889634 + 64.0;
-    int e = 0;
-    while (std::ldexp(1.0, e) < 8.0 * cmax) ++e;
-    const int g = 23 - e;
-    return g >= 4 ? (g > 12 ? 12 : g) : -1;
-}
+int sk_lse2_grid_bits(double gamma) { return l2_grid_bits(gamma); }
 
 size_t sk_lse2_smem_cap() {
     int dev = 0, cap = 0;
