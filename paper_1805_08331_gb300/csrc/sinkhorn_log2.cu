@@ -380,11 +380,11 @@ __device__ __forceinline__ bool l2_update(float tot, float shift, float Ms, floa
 
 // Delta output of a half-step, shifted by its previous value: partial sums
 // over a fixed L2_DLANES-lane partition of the input cells, one barrier, then
-// thread 0 finishes the sum and updates out.potD (the other threads go on).
+// thread `fin` finishes the sum and updates out.potD (the other threads go on).
 template <int NT, bool GM>
 static __device__ __forceinline__ void l2_delta_out(L2Side& in, L2Side& out, const L2Consts& K, bool want_err,
                                                     long long& errq, bool& errbad, float* redD, int* range_flag,
-                                                    unsigned char* gb) {
+                                                    unsigned char* gb, int fin = 0) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int in_n = in.n;
     const float2* in_hin = sdp<float2, GM>(gb, in.hin);
@@ -424,7 +424,7 @@ static __device__ __forceinline__ void l2_delta_out(L2Side& in, L2Side& out, con
         }
     }
     __syncthreads();
-    if (t == 0 && doD) {
+    if (t == fin && doD) {
         float tot = 0.f;
         for (int q = 0; q < L2_DLANES / 32; ++q) tot += redD[q];
         const float2 hD = in.hinD;
@@ -653,9 +653,12 @@ __device__ __forceinline__ float l2_pw_term(const float4& r, float B, float a, f
 template <int NT>
 static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bool want_err, long long& errq,
                                   bool& errbad, float* redD, int* range_flag) {
-    l2_delta_out<NT, false>(in, out, K, want_err, errq, errbad, redD, range_flag, nullptr);
     const int t = threadIdx.x;
     const int n_in = in.n, m = out.n;
+    // the Delta output's serial finish goes to the first warp without an
+    // output cell (if any), so that no warp with cells starts them late
+    const int idle = ((m + 31) >> 5) << 5;   // first thread of the first warp without a cell
+    l2_delta_out<NT, false>(in, out, K, want_err, errq, errbad, redD, range_flag, nullptr, idle < NT ? idle : 0);
     const float4* rec_in = smp<float4>(in.rec);
     float4* rec_out = smp<float4>(out.rec);
     float2* out_pot = smp<float2>(out.pot);
