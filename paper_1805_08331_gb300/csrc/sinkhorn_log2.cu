@@ -378,6 +378,43 @@ __device__ __forceinline__ bool l2_update(float tot, float shift, float Ms, floa
     return fabsf(pn.x) < K.lim;
 }
 
+// End of a Delta-output sum: tot = the input cells' terms shifted by the
+// previous value MsD; adds the input Delta term, recomputes with the exact
+// maximum when the sum left [2^-100, 2^100], and updates out.potD.
+template <bool GM>
+static __device__ __forceinline__ void l2_delta_finish(L2Side& in, L2Side& out, const L2Consts& K, float tot,
+                                                       bool want_err, long long& errq, bool& errbad, int* range_flag,
+                                                       unsigned char* gb) {
+    const int in_n = in.n;
+    const float2* in_hin = sdp<float2, GM>(gb, in.hin);
+    const short* in_row = sdp<short, GM>(gb, in.row);
+    const short* in_col = sdp<short, GM>(gb, in.col);
+    const float2* cdt = smp<float2>(K.cdt);
+    const float MsD = -out.potD.x;
+    const float2 hD = in.hinD;
+    if (hD.x > -INFINITY) tot += exp2f((hD.x - MsD) + hD.y);
+    float shift = MsD;
+    if (!(tot >= 0x1p-100f && tot <= 0x1p100f)) {
+        float mx = hD.x;
+        for (int q = 0; q < in_n; ++q)
+            mx = fmaxf(mx, in_hin[q].x - cdt[abs((int)in_col[q] - (int)in_row[q])].x);
+        shift = mx;
+        tot = (hD.x > -INFINITY) ? exp2f((hD.x - shift) + hD.y) : 0.f;
+        for (int q = 0; q < in_n; ++q) {
+            const float2 h = in_hin[q];
+            const float2 c = cdt[abs((int)in_col[q] - (int)in_row[q])];
+            tot += exp2f(((h.x - c.x) - shift) + (h.y - c.y));
+        }
+    }
+    float2 pn;
+    if (l2_update(tot, shift, MsD, out.potD, out.wD, want_err, K, errq, errbad, pn)) {
+        out.potD = pn;
+        out.hinD = make_float2(out.lwD.x + pn.x, out.lwD.y + pn.y);
+    } else {
+        atomicOr(range_flag, 1);
+    }
+}
+
 // Delta output of a half-step, shifted by its previous value: partial sums
 // over a fixed L2_DLANES-lane partition of the input cells, one barrier, then
 // thread `fin` finishes the sum and updates out.potD (the other threads go on).
@@ -427,29 +464,32 @@ static __device__ __forceinline__ void l2_delta_out(L2Side& in, L2Side& out, con
     if (t == fin && doD) {
         float tot = 0.f;
         for (int q = 0; q < L2_DLANES / 32; ++q) tot += redD[q];
-        const float2 hD = in.hinD;
-        if (hD.x > -INFINITY) tot += exp2f((hD.x - MsD) + hD.y);
-        float shift = MsD;
-        if (!(tot >= 0x1p-100f && tot <= 0x1p100f)) {
-            float mx = hD.x;
-            for (int q = 0; q < in_n; ++q)
-                mx = fmaxf(mx, in_hin[q].x - cdt[abs((int)in_col[q] - (int)in_row[q])].x);
-            shift = mx;
-            tot = (hD.x > -INFINITY) ? exp2f((hD.x - shift) + hD.y) : 0.f;
-            for (int q = 0; q < in_n; ++q) {
-                const float2 h = in_hin[q];
-                const float2 c = cdt[abs((int)in_col[q] - (int)in_row[q])];
-                tot += exp2f(((h.x - c.x) - shift) + (h.y - c.y));
-            }
-        }
-        float2 pn;
-        if (l2_update(tot, shift, MsD, out.potD, out.wD, want_err, K, errq, errbad, pn)) {
-            out.potD = pn;
-            out.hinD = make_float2(out.lwD.x + pn.x, out.lwD.y + pn.y);
-        } else {
-            atomicOr(range_flag, 1);
-        }
+        l2_delta_finish<GM>(in, out, K, tot, want_err, errq, errbad, range_flag, gb);
     }
+}
+
+// Delta output of a pairwise half-step by one warp, with no block barrier:
+// lane l sums the input cells l, l + 32, ... in order, a fixed shuffle tree
+// adds the lanes, and lane 0 finishes.  The partition is the same whichever
+// warp runs it and at every CTA width.  out.potD is read by the next
+// half-step only, behind this half-step's closing barrier.
+static __device__ __forceinline__ void l2_delta_warp(L2Side& in, L2Side& out, const L2Consts& K, bool want_err,
+                                                     long long& errq, bool& errbad, int* range_flag) {
+    if (!(out.wD > 0.f)) return;
+    const int lane = threadIdx.x & 31, in_n = in.n;
+    const float2* in_hin = smp<float2>(in.hin);
+    const short* in_row = smp<short>(in.row);
+    const short* in_col = smp<short>(in.col);
+    const float2* cdt = smp<float2>(K.cdt);
+    const float MsD = -out.potD.x;
+    float sD = 0.f;
+    for (int q = lane; q < in_n; q += 32) {
+        const float2 h = in_hin[q];
+        const float2 c = cdt[abs((int)in_col[q] - (int)in_row[q])];
+        sD += l2_ex2(((h.x - c.x) - MsD) + (h.y - c.y));
+    }
+    sD = warp_sum(sD);
+    if (lane == 0) l2_delta_finish<false>(in, out, K, sD, want_err, errq, errbad, range_flag, nullptr);
 }
 
 // One half-step: out.pot <- -LSE over the input side.  Adds the marginal-error
@@ -652,13 +692,15 @@ __device__ __forceinline__ float l2_pw_term(const float4& r, float B, float a, f
 // cells per lane in packed arithmetic, 25 %: half the warps busy.)
 template <int NT>
 static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bool want_err, long long& errq,
-                                  bool& errbad, float* redD, int* range_flag) {
+                                  bool& errbad, int* range_flag, bool end_sync) {
     const int t = threadIdx.x;
     const int n_in = in.n, m = out.n;
-    // the Delta output's serial finish goes to the first warp without an
-    // output cell (if any), so that no warp with cells starts them late
-    const int idle = ((m + 31) >> 5) << 5;   // first thread of the first warp without a cell
-    l2_delta_out<NT, false>(in, out, K, want_err, errq, errbad, redD, range_flag, nullptr, idle < NT ? idle : 0);
+    // the Delta output: one warp, no block barrier; the first warp without an
+    // output cell if there is one, else the last warp (fewest cells in the
+    // last pass)
+    const int idle = (m + 31) >> 5;
+    if ((t >> 5) == (idle < NT / 32 ? idle : NT / 32 - 1))
+        l2_delta_warp(in, out, K, want_err, errq, errbad, range_flag);
     const float4* rec_in = smp<float4>(in.rec);
     float4* rec_out = smp<float4>(out.rec);
     float2* out_pot = smp<float2>(out.pot);
@@ -740,7 +782,9 @@ static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bo
             atomicOr(range_flag, 1);
         }
     }
-    __syncthreads();
+    // the closing barrier (the caller's error reduction provides it after the
+    // v-update)
+    if (end_sync) __syncthreads();
 }
 
 // gamma-continuation step inside the launch: gamma -> gamma / 4.  Potentials
@@ -989,14 +1033,16 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
 #pragma unroll 1
         for (int hs = 0; hs < 2; ++hs) {
             if (!GM && K.pw_ok && (hs == 0 ? pwU : pwV))
-                l2_half_pw<NT>(S[1 - hs], S[hs], K, hs == 1, errq, errbad, redD, &range_flag);
+                l2_half_pw<NT>(S[1 - hs], S[hs], K, hs == 1, errq, errbad, &range_flag, hs == 0);
             else
                 l2_half<NT, GM>(S[1 - hs], S[hs], K, hs == 1, errq, errbad, redD, &range_flag, gb);
         }
         errq = warp_sum(errq);
         if (lane == 0) redE[wid] = errq;
         // written next to redE and read after the same barrier (the next write
-        // is behind the barriers of the next iteration's half-steps)
+        // is behind the barriers of the next iteration's half-steps); the
+        // barrier also closes a pairwise v-update, whose results the next
+        // iteration reads
         if (t == 0) leave = can_leave && (it & 15) == 15 && *(volatile int*)&counter[4] >= r.exit_at;
         const int bad = __syncthreads_or(errbad);
         long long e = 0;
