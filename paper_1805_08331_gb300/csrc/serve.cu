@@ -154,7 +154,7 @@ struct Pool {
     int d = 0, dp = 0, S = 0;
     void* ws = nullptr;
     SkWS w{};
-    int* counter = nullptr;            // 4 device ints inside ws
+    int* counter = nullptr;            // 8 device ints inside ws
     double *WA = nullptr, *WB = nullptr, *ginit = nullptr, *gout = nullptr, *cost = nullptr;
     int32_t *iters = nullptr, *status = nullptr;
     float* err = nullptr;

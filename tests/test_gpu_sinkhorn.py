@@ -162,6 +162,21 @@ def test_lse_forms_converged_against_oracle(ctx, d, gamma, nmin, nmax):
     assert (np.abs(res[1]["cost"] - res[2]["cost"]) / ref["cost"]).max() <= 5e-6
 
 
+def test_pair_alone_equals_pair_in_a_batch(ctx):
+    """A pair's result does not depend on the batch around it: solved alone it
+    equals the same pair solved inside a batch of 600 bit for bit (the batch
+    orders its CTAs by support size and runs them side by side on the SMs)."""
+    d, gamma = 128, 1e-3
+    b, t, o = inputs.random_diagrams(1200, nmin=50, nmax=500, seed=21)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    big = _solve(ctx, hA, hB, d, gamma, 3000, 1e-6, want_potentials=True)
+    for p in (0, 7, 599):
+        one = _solve(ctx, hA[p:p + 1], hB[p:p + 1], d, gamma, 3000, 1e-6, want_potentials=True)
+        for k in ("cost", "iters", "err", "status", "f", "g"):
+            assert np.array_equal(one[k][0], big[k][p]), (p, k)
+
+
 def test_automatic_form_follows_the_rule(ctx):
     """Form 0 chooses per half-step: on sparse diagrams at d = 128 (every
     half-step pairwise by the rule) it equals form 2 bit for bit; on dense
