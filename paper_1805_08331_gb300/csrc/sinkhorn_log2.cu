@@ -109,8 +109,28 @@ __host__ __device__ __forceinline__ bool l2_pw_half(int n_in, int nr_in, int n_o
 // Shared-memory bytes of a pair in the on-chip variant (the host sizes the
 // launch with the maximum over the pairs); pwU / pwV: the forms of its
 // u- and v-updates.
-__host__ __device__ __forceinline__ size_t l2_need(int nA, int nB, int nrA, int nrB, int d, bool pwU, bool pwV) {
-    return l2_side_bytes(nA, nB, d, pwU || pwV) + l2_table_bytes(nrA > nrB ? nrA : nrB, d, !(pwU && pwV));
+// rec: the pair may take the pairwise form at some stage (records); sep: it
+// may take the separable form at some stage (stage buffer).
+__host__ __device__ __forceinline__ size_t l2_need(int nA, int nB, int nrA, int nrB, int d, bool rec, bool sep) {
+    return l2_side_bytes(nA, nB, d, rec) + l2_table_bytes(nrA > nrB ? nrA : nrB, d, sep);
+}
+
+// Forms of a pair's half-steps.  rule*: the form rule says pairwise (with
+// exact scaled units assumed); pw*: pairwise at the starting stage (scaled
+// units exist at its gamma); rec: records are needed at some stage (scaled
+// units at the target gamma: a smaller gamma only raises n1).
+struct L2Forms {
+    bool ruleU, ruleV, pwU, pwV, rec;
+};
+__host__ __device__ inline L2Forms l2_forms(int nA, int nB, int nrA, int nrB, int ncA, int ncB, int form,
+                                           bool p2_start, bool p2_target) {
+    L2Forms f;
+    f.ruleU = l2_pw_half(nB, nrB, nA, ncA, form, p2_target);
+    f.ruleV = l2_pw_half(nA, nrA, nB, ncB, form, p2_target);
+    f.pwU = f.ruleU && p2_start;
+    f.pwV = f.ruleV && p2_start;
+    f.rec = f.ruleU || f.ruleV;
+    return f;
 }
 
 // (hi, lo) split of an FP64 value on the 2^-G grid (gsc = 2^G).
@@ -255,7 +275,7 @@ struct L2Consts {
 
 // Pairwise-form constants at this gamma (p = 2).  The form sums in scaled
 // units: a log2-unit value v is v' = v / kap, with kap = s / sp and sp = n1 2^-G
-// the grid value nearest s (n1 >= 4, so kap lies in [7/8, 9/8]).  In those
+// the grid value nearest s (n1 >= 1, so kap lies in [1/2, 3/2]).  In those
 // units a term's exponent is
 //   kap ( (h'.hi - sp D - Ms') + h'.lo ),   D = (i-k)^2 + (j-l)^2,
 // and h'.hi - sp D - Ms' = A_y + B_x + 2 sp (i k + j l) with A_y = h'.hi -
@@ -282,7 +302,7 @@ __host__ __device__ inline L2PwC l2_pw_calc(double gamma, int d, int gbits, doub
     if (pw != 2.0 || gbits < 0) return c;
     const double s = 1.4426950408889634 / (gamma * (double)d * (double)d);
     const double n1 = rint(ldexp(s, gbits));
-    if (n1 < 4.0) return c;
+    if (n1 < 1.0) return c;
     c.sp = ldexp(n1, -gbits);
     c.kap = (double)(float)(s / c.sp);   // the FP32 value the kernel multiplies by
     c.rho = 1.0 / c.kap - 1.0;
@@ -809,10 +829,8 @@ static __device__ void l2_next_stage(L2Side* S, const L2Consts& K, double gamma_
             xpot[e] = pn;
             const float2 hn = make_float2(xlw[e].x + pn.x, xlw[e].y + pn.y);
             xhin[e] = hn;
-            if (!GM && K.pw_ok) {
-                float4* xr = smp<float4>(X.rec) + e;
-                *xr = l2_pw_record(hn, xr->z, xr->w, K);
-            }
+            if (!GM && K.pw_ok)   // (records may not exist yet: the coordinates come from the cell lists)
+                smp<float4>(X.rec)[e] = l2_pw_record(hn, (float)smp<short>(X.row)[e], (float)smp<short>(X.col)[e], K);
         }
     }
     __syncthreads();   // every thread has read the sides' Delta state (hinD in the half-steps) before t == 0 writes it
@@ -871,6 +889,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     __shared__ int wcnt[NW > L2_MAXCH ? NW : L2_MAXCH];
     __shared__ int cnt[4];
     __shared__ int range_flag, fits, leave;
+    __shared__ L2Forms Fsh;   // the pair's forms (read at each half-step; not kept in registers)
     const bool can_leave = !GM && r.exit_at > 0;
     // the launch order maps this CTA to a pair, and, in a launch over several
     // workspaces (pairs of several grid sizes), to its workspace: code =
@@ -888,21 +907,24 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     l2_compact(q.rpb, d, nullptr, &cnt[1], nullptr, wcnt);
     const int nrA = cnt[0], nrB = cnt[1];
     // the form of each half-step (the pairwise form runs on chip only)
-    bool pwU = false, pwV = false;
+    // (a pair that starts at a continuation stage without exact scaled units
+    // takes the separable form there and switches at the first stage that has
+    // them)
+    L2Forms fm{false, false, false, false, false};
     if constexpr (!GM) {
         l2_compact(q.cpa, d, nullptr, &cnt[2], nullptr, wcnt);
         l2_compact(q.cpb, d, nullptr, &cnt[3], nullptr, wcnt);
-        // the pairwise form at this pair's starting gamma (later stages keep it)
-        const bool p2 = l2_pw_calc(gamma_k, d, gbits, W.p).ok;
-        pwU = l2_pw_half(nB, nrB, nA, cnt[2], r.form, p2);
-        pwV = l2_pw_half(nA, nrA, nB, cnt[3], r.form, p2);
+        fm = l2_forms(nA, nB, nrA, nrB, cnt[2], cnt[3], r.form, l2_pw_calc(gamma_k, d, gbits, W.p).ok,
+                      l2_pw_calc(W.gamma, d, gbits, W.p).ok);
     }
+    const bool pwU = fm.pwU, pwV = fm.pwV;   // at the starting stage (set-up only)
     if (t == 0) {
+        Fsh = fm;
         if (GM)
             fits = l2_side_bytes(nA, nB, d, false) <= gcap &&
                    l2_table_bytes(nrA > nrB ? nrA : nrB, d) <= (size_t)smem_cap;
         else
-            fits = l2_need(nA, nB, nrA, nrB, d, pwU, pwV) <= (size_t)smem_cap;
+            fits = l2_need(nA, nB, nrA, nrB, d, fm.rec, !(pwU && pwV)) <= (size_t)smem_cap;
         fits = fits && nA < 32768 && nB < 32768;   // cell indices are 16-bit (chl, packed row ranges)
     }
     __syncthreads();
@@ -931,7 +953,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     const int ns[2] = {nA, nB};
     for (int s = 0; s < 2; ++s) {
         const int n = ns[s];
-        const uint32_t o_lw = take(24 * (size_t)n), o_rec = take((pwU || pwV) ? 16 * (size_t)n : 0),
+        const uint32_t o_lw = take(24 * (size_t)n), o_rec = take(fm.rec ? 16 * (size_t)n : 0),
                        o_w = take(4 * (size_t)n), o_rp = take(4 * (size_t)(d + 1));
         const uint32_t o_row = take(6 * (size_t)n), o_rows = take(6 * (size_t)d);
         if (t == 0) {
@@ -1032,7 +1054,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
         // of the half-step code serves both (instruction cache)
 #pragma unroll 1
         for (int hs = 0; hs < 2; ++hs) {
-            if (!GM && K.pw_ok && (hs == 0 ? pwU : pwV))
+            if (!GM && K.pw_ok && (hs == 0 ? Fsh.pwU : Fsh.pwV))
                 l2_half_pw<NT>(S[1 - hs], S[hs], K, hs == 1, errq, errbad, &range_flag, hs == 0);
             else
                 l2_half<NT, GM>(S[1 - hs], S[hs], K, hs == 1, errq, errbad, redD, &range_flag, gb);
@@ -1059,12 +1081,19 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
             --stage;
             {
                 // the pairwise constants of the new gamma first: the stage step
-                // rebuilds the records with them (a pair that had the pairwise
-                // form keeps it: smaller gamma only moves n1 up)
-                const bool keep = K.pw_ok;
+                // rebuilds the records with them.  A pair takes the pairwise
+                // form from the first stage with exact scaled units on (a
+                // smaller gamma only raises n1, so it never turns off)
+                const bool was = K.pw_ok;
+                const L2Forms f = Fsh;
                 l2_pw_consts(K, ldexp(W.gamma, 2 * stage), d, gbits, W.p);
-                if (keep && !K.pw_ok && t == 0) range_flag = 1;   // not reached; the FP64 kernel would take over
-                K.pw_ok = K.pw_ok && keep;
+                K.pw_ok = K.pw_ok && f.rec;
+                __syncthreads();   // every thread has read Fsh
+                if (t == 0) {
+                    if (was && !K.pw_ok) range_flag = 1;   // not reached; the FP64 kernel would take over
+                    Fsh.pwU = f.ruleU && K.pw_ok;
+                    Fsh.pwV = f.ruleV && K.pw_ok;
+                }
             }
             l2_next_stage<NT, GM>(S, K, ldexp(W.gamma, 2 * stage), W.p, d, &range_flag, gb);
             if (range_flag) { moved = true; break; }
@@ -1136,12 +1165,13 @@ __global__ void sk_lse2_need_kernel(SkWS w, int* max_need, int form) {
         ncB += q.cpb[i + 1] > q.cpb[i];
     }
     const int nA = q.ic[IC_NA], nB = q.ic[IC_NB];
-    // the pairwise form at this pair's current gamma (later stages keep it)
-    const bool p2 = l2_pw_calc(ldexp(w.gamma, 2 * q.ic[IC_STAGE]), w.d, l2_grid_bits(w.gamma), w.p).ok;
-    const bool pwU = l2_pw_half(nB, nrB, nA, ncA, form, p2), pwV = l2_pw_half(nA, nrA, nB, ncB, form, p2);
-    const size_t need = l2_need(nA, nB, nrA, nrB, w.d, pwU, pwV);
+    const int gb = l2_grid_bits(w.gamma);
+    const L2Forms fm = l2_forms(nA, nB, nrA, nrB, ncA, ncB, form,
+                                l2_pw_calc(ldexp(w.gamma, 2 * q.ic[IC_STAGE]), w.d, gb, w.p).ok,
+                                l2_pw_calc(w.gamma, w.d, gb, w.p).ok);
+    const size_t need = l2_need(nA, nB, nrA, nrB, w.d, fm.rec, !(fm.pwU && fm.pwV));
     atomicMax(max_need, (int)(need > 0x7fffffff ? 0x7fffffff : need));
-    if (!(pwU && pwV)) atomicAdd(max_need + 1, 1);
+    if (!(fm.pwU && fm.pwV)) atomicAdd(max_need + 1, 1);
 }
 
 cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, int form, cudaStream_t s) {
