@@ -122,14 +122,20 @@ __host__ __device__ __forceinline__ size_t l2_need(int nA, int nB, int nrA, int 
 struct L2Forms {
     bool ruleU, ruleV, pwU, pwV, rec;
 };
-__host__ __device__ inline L2Forms l2_forms(int nA, int nB, int nrA, int nrB, int ncA, int ncB, int form,
-                                           bool p2_start, bool p2_target) {
+// cap: the shared memory a CTA may use; a pair that fits on chip only without
+// the pairwise records (16 bytes per cell) takes the separable form rather
+// than the global-memory tier.
+__host__ __device__ inline L2Forms l2_forms(int nA, int nB, int nrA, int nrB, int ncA, int ncB, int d, int form,
+                                           bool p2_start, bool p2_target, size_t cap) {
     L2Forms f;
     f.ruleU = l2_pw_half(nB, nrB, nA, ncA, form, p2_target);
     f.ruleV = l2_pw_half(nA, nrA, nB, ncB, form, p2_target);
     f.pwU = f.ruleU && p2_start;
     f.pwV = f.ruleV && p2_start;
     f.rec = f.ruleU || f.ruleV;
+    if (f.rec && l2_need(nA, nB, nrA, nrB, d, true, !(f.pwU && f.pwV)) > cap &&
+        l2_need(nA, nB, nrA, nrB, d, false, true) <= cap)
+        f = L2Forms{false, false, false, false, false};
     return f;
 }
 
@@ -914,8 +920,8 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     if constexpr (!GM) {
         l2_compact(q.cpa, d, nullptr, &cnt[2], nullptr, wcnt);
         l2_compact(q.cpb, d, nullptr, &cnt[3], nullptr, wcnt);
-        fm = l2_forms(nA, nB, nrA, nrB, cnt[2], cnt[3], r.form, l2_pw_calc(gamma_k, d, gbits, W.p).ok,
-                      l2_pw_calc(W.gamma, d, gbits, W.p).ok);
+        fm = l2_forms(nA, nB, nrA, nrB, cnt[2], cnt[3], d, r.form, l2_pw_calc(gamma_k, d, gbits, W.p).ok,
+                      l2_pw_calc(W.gamma, d, gbits, W.p).ok, (size_t)smem_cap);
     }
     const bool pwU = fm.pwU, pwV = fm.pwV;   // at the starting stage (set-up only)
     if (t == 0) {
@@ -1152,7 +1158,7 @@ cudaError_t sk_launch_set_stage(const SkWS& w, int K, cudaStream_t s) {
 }
 
 // Maximum shared-memory need over the active on-chip pairs (one thread per pair).
-__global__ void sk_lse2_need_kernel(SkWS w, int* max_need, int form) {
+__global__ void sk_lse2_need_kernel(SkWS w, int* max_need, int form, size_t cap) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= w.P) return;
     PairPtrs q = pair_ptrs(w, p);
@@ -1166,17 +1172,18 @@ __global__ void sk_lse2_need_kernel(SkWS w, int* max_need, int form) {
     }
     const int nA = q.ic[IC_NA], nB = q.ic[IC_NB];
     const int gb = l2_grid_bits(w.gamma);
-    const L2Forms fm = l2_forms(nA, nB, nrA, nrB, ncA, ncB, form,
+    const L2Forms fm = l2_forms(nA, nB, nrA, nrB, ncA, ncB, w.d, form,
                                 l2_pw_calc(ldexp(w.gamma, 2 * q.ic[IC_STAGE]), w.d, gb, w.p).ok,
-                                l2_pw_calc(w.gamma, w.d, gb, w.p).ok);
+                                l2_pw_calc(w.gamma, w.d, gb, w.p).ok, cap);
     const size_t need = l2_need(nA, nB, nrA, nrB, w.d, fm.rec, !(fm.pwU && fm.pwV));
     atomicMax(max_need, (int)(need > 0x7fffffff ? 0x7fffffff : need));
     if (!(fm.pwU && fm.pwV)) atomicAdd(max_need + 1, 1);
 }
 
+size_t sk_lse2_smem_cap();
 cudaError_t sk_launch_lse2_need(const SkWS& w, int* max_need, int form, cudaStream_t s) {
     if (w.P == 0) return cudaSuccess;
-    sk_lse2_need_kernel<<<(w.P + 255) / 256, 256, 0, s>>>(w, max_need, form);
+    sk_lse2_need_kernel<<<(w.P + 255) / 256, 256, 0, s>>>(w, max_need, form, sk_lse2_smem_cap());
     return cudaGetLastError();
 }
 
