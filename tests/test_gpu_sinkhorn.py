@@ -177,6 +177,24 @@ def test_pair_alone_equals_pair_in_a_batch(ctx):
             assert np.array_equal(one[k][0], big[k][p]), (p, k)
 
 
+def test_pair_too_large_for_records_takes_the_separable_form(ctx):
+    """A pair that fits in shared memory only without the pairwise records (a
+    dense d = 100 histogram, ~4400 cells, against a small diagram) takes the
+    separable form on chip in the automatic rule: bit for bit the result of
+    form 1, and the oracle's cost after 100 fixed iterations."""
+    d, gamma, T = 100, 5e-3, 100
+    b1, t1, o1 = inputs.random_diagrams(1, nmin=40000, nmax=40000, seed=31)
+    b2, t2, o2 = inputs.random_diagrams(1, nmin=150, nmax=150, seed=32)
+    hA, _ = oracle.rasterize(b1, t1, o1, d)
+    hB, _ = oracle.rasterize(b2, t2, o2, d)
+    assert (hA > 0).sum() > 4000
+    r0, r1 = (_solve(ctx, hA, hB, d, gamma, T, 0.0, prm={"lse_form": f}, want_potentials=True) for f in (0, 1))
+    for k in ("cost", "f", "g", "err"):
+        assert np.array_equal(r0[k], r1[k]), k
+    ref = oracle.sinkhorn_pd(d, gamma, hA[0], hB[0], T, 0.0)
+    assert abs(r0["cost"][0] - ref["cost"]) <= 1e-6 * ref["cost"]
+
+
 def test_automatic_form_follows_the_rule(ctx):
     """Form 0 chooses per half-step: on sparse diagrams at d = 128 (every
     half-step pairwise by the rule) it equals form 2 bit for bit; on dense
