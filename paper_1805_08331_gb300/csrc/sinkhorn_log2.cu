@@ -58,7 +58,9 @@ struct L2Side {
     uint32_t lw;      // float2 [n] log2 weight (hi, lo)
     uint32_t pot;     // float2 [n] potential/gamma in log2 units (hi, lo)
     uint32_t hin;     // float2 [n] lw + pot, the side's h when it is the input
-    uint32_t rec;     // float4 [n] (hin.x, hin.y, row, column): a cell as the pairwise form reads it
+    uint32_t rec;     // pairwise records, two cells per 32 bytes (l2_rec_*): float4 [np] (A_2p, A_2p+1,
+                      //        kap lo_2p, kap lo_2p+1), then float4 [np] (k_2p, k_2p+1, l_2p, l_2p+1),
+                      //        np = ceil(n / 2); an odd n's last slot holds A = -inf (a zero term)
     uint32_t w;       // float  [n] weight (marginal error)
     uint32_t rp;      // int    [d+1] row pointers into the support while loading; then, per
                       //        non-empty row r: first cell | one-past-last cell << 16
@@ -81,7 +83,7 @@ __host__ __device__ __forceinline__ size_t l2_side_bytes(int nA, int nB, int d, 
     const int ns[2] = {nA, nB};
     for (int s = 0; s < 2; ++s) {
         const size_t n = (size_t)ns[s];
-        b += l2_al(24 * n) + (rec ? l2_al(16 * n) : 0) + l2_al(4 * n) + l2_al(4 * (size_t)(d + 1)) + l2_al(6 * n) +
+        b += l2_al(24 * n) + (rec ? l2_al(32 * ((n + 1) / 2)) : 0) + l2_al(4 * n) + l2_al(4 * (size_t)(d + 1)) + l2_al(6 * n) +
              l2_al(6 * (size_t)d);
     }
     return b;
@@ -331,14 +333,37 @@ __device__ __forceinline__ void l2_pw_consts(L2Consts& K, double gamma, int d, i
 // The pairwise record of an input cell (row k, column l) from its h = (hi, lo)
 // in log2 units: h' = h / kap = h (1 + rho) split into h'.hi on the grid and
 // h'.lo (two-float products: hi rho = p + pe exactly), then
-// (A = h'.hi - sp (k^2 + l^2), kap h'.lo, k, l).
-__device__ __forceinline__ float4 l2_pw_record(float2 h, float k, float l, const L2Consts& K) {
+// (A = h'.hi - sp (k^2 + l^2), kap h'.lo).
+__device__ __forceinline__ float2 l2_pw_record(float2 h, float k, float l, const L2Consts& K) {
     const float p = h.x * K.rho_h;
     const float pe = fmaf(h.x, K.rho_h, -p);
     const float ph = l2_round(p, K.gsc, K.ginv);
     const float hi = h.x + ph;
     const float lo = (p - ph) + (pe + fmaf(h.x, K.rho_l, fmaf(h.y, K.rho_h, h.y)));
-    return make_float4(fmaf(-K.sp, fmaf(k, k, l * l), hi), K.kap * lo, k, l);
+    return make_float2(fmaf(-K.sp, fmaf(k, k, l * l), hi), K.kap * lo);
+}
+
+// Records of a side of n cells in pairs (the layout of L2Side::rec): cell e's
+// (A, kap lo) and its (row, column) sit in lanes e & 1 of the pair records
+// e >> 1, so that one packed f32x2 instruction works on two input cells.
+__device__ __forceinline__ void l2_rec_put(uint32_t rec, int e, float2 Akl) {
+    float* hi = smp<float>(rec + 16 * (e >> 1));
+    hi[e & 1] = Akl.x;
+    hi[2 + (e & 1)] = Akl.y;
+}
+__device__ __forceinline__ void l2_rec_coord(uint32_t rec, int n, int e, float k, float l) {
+    float* co = smp<float>(rec + 16 * (((n + 1) >> 1) + (e >> 1)));
+    co[e & 1] = k;
+    co[2 + (e & 1)] = l;
+}
+__device__ __forceinline__ float2 l2_rec_xy(uint32_t rec, int n, int e) {
+    const float* co = smp<float>(rec + 16 * (((n + 1) >> 1) + (e >> 1)));
+    return make_float2(co[e & 1], co[2 + (e & 1)]);
+}
+__device__ __forceinline__ float4 l2_rec_get(uint32_t rec, int n, int e) {   // (A, kap lo, k, l)
+    const float* hi = smp<float>(rec + 16 * (e >> 1));
+    const float2 xy = l2_rec_xy(rec, n, e);
+    return make_float4(hi[e & 1], hi[2 + (e & 1)], xy.x, xy.y);
 }
 
 // Packed FP32 pair arithmetic (two lanes of one 64-bit register pair).
@@ -346,6 +371,13 @@ __device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
     float2 r;
     asm("{.reg .b64 ra, rb, rr;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
         "sub.rn.f32x2 rr, ra, rb;\n\tmov.b64 {%0, %1}, rr;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 ra, rb, rr;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rr, ra, rb;\n\tmov.b64 {%0, %1}, rr;}"
         : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
     return r;
 }
@@ -682,7 +714,7 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
                         const float2 lw = sdp<float2, GM>(gb, out.lw)[qo];
                         const float2 hn = make_float2(lw.x + pn.x, lw.y + pn.y);
                         sdp<float2, GM>(gb, out.hin)[qo] = hn;
-                        if (!GM && K.pw_ok) smp<float4>(out.rec)[qo] = l2_pw_record(hn, (float)i, (float)j, K);
+                        if (!GM && K.pw_ok) l2_rec_put(out.rec, qo, l2_pw_record(hn, (float)i, (float)j, K));
                     } else {
                         atomicOr(range_flag, 1);
                     }
@@ -699,6 +731,17 @@ static __device__ void l2_half(L2Side& in, L2Side& out, const L2Consts& K, bool 
 // is exact; kap multiplies it and adds kap h'.lo in one rounding.
 __device__ __forceinline__ float l2_pw_term(const float4& r, float B, float a, float b, float kap) {
     return l2_ex2(fmaf(kap, fmaf(a, r.z, fmaf(b, r.w, r.x + B)), r.y));
+}
+// The same term for two input cells at once, from a pair record: hi = (A_0,
+// A_1, kap lo_0, kap lo_1), co = (k_0, k_1, l_0, l_1); every step is one packed
+// f32x2 instruction for both (each lane rounds as the scalar form does).
+__device__ __forceinline__ float2 l2_pw_term2(const float4& hi, const float4& co, float2 B2, float2 a2, float2 b2,
+                                              float2 k2) {
+    float2 t = f2_add(make_float2(hi.x, hi.y), B2);
+    t = f2_fma(b2, make_float2(co.z, co.w), t);
+    t = f2_fma(a2, make_float2(co.x, co.y), t);
+    t = f2_fma(k2, t, make_float2(hi.z, hi.w));
+    return make_float2(l2_ex2(t.x), l2_ex2(t.y));
 }
 
 // Pairwise form of a half-step (p = 2, on chip): the same log-sum-exp as the
@@ -727,8 +770,9 @@ static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bo
     const int idle = (m + 31) >> 5;
     if ((t >> 5) == (idle < NT / 32 ? idle : NT / 32 - 1))
         l2_delta_warp(in, out, K, want_err, errq, errbad, range_flag);
-    const float4* rec_in = smp<float4>(in.rec);
-    float4* rec_out = smp<float4>(out.rec);
+    const int np = (n_in + 1) >> 1;   // pair records of the input (an odd n's last slot is a zero term)
+    const float4* rhi = smp<float4>(in.rec);
+    const float4* rco = rhi + np;
     float2* out_pot = smp<float2>(out.pot);
     const float2* cdt = smp<float2>(K.cdt);
     const float2 hD = in.hinD;   // input Delta term (not written in this half-step)
@@ -738,35 +782,33 @@ static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bo
         if (e >= m) continue;
         float sum, Mp;
         {
-            // the sum over the records, shifted by kap Ms' (Ms' on the grid);
-            // only what the loop needs is live across it
-            const float4 rx = rec_out[e];
+            // the sum over the records, shifted by kap Ms' (Ms' on the grid),
+            // two input cells per packed instruction; only what the loop needs
+            // is live across it
+            const float2 xy = l2_rec_xy(out.rec, m, e);
             const float Ms = -out_pot[e].x;
             Mp = Ms + l2_round(Ms * K.rho_h, K.gsc, K.ginv);
-            const float a = 2.f * sp * rx.z, b = 2.f * sp * rx.w;
-            const float B = fmaf(-sp, fmaf(rx.z, rx.z, rx.w * rx.w), -Mp);
+            const float a = 2.f * sp * xy.x, b = 2.f * sp * xy.y;
+            const float B = fmaf(-sp, fmaf(xy.x, xy.x, xy.y * xy.y), -Mp);
+            const float2 B2 = make_float2(B, B), a2 = make_float2(a, a), b2 = make_float2(b, b),
+                         k2 = make_float2(kap, kap);
             float sm = 0.f, cm = 0.f;
-            int y = 0;
-            for (; y + 7 < n_in; y += 8) {
-                float ev[8];
+            int q = 0;
+            for (; q + 3 < np; q += 4) {
+                float2 ev[4];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) ev[u] = l2_pw_term(rec_in[y + u], B, a, b, kap);
-                kahan_add(sm, cm, ((ev[0] + ev[1]) + (ev[2] + ev[3])) + ((ev[4] + ev[5]) + (ev[6] + ev[7])));
+                for (int u = 0; u < 4; ++u) ev[u] = l2_pw_term2(rhi[q + u], rco[q + u], B2, a2, b2, k2);
+                const float2 s2 = f2_add(f2_add(ev[0], ev[1]), f2_add(ev[2], ev[3]));
+                kahan_add(sm, cm, s2.x + s2.y);
             }
-            for (; y + 3 < n_in; y += 4) {
-                float ev[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) ev[u] = l2_pw_term(rec_in[y + u], B, a, b, kap);
-                kahan_add(sm, cm, (ev[0] + ev[1]) + (ev[2] + ev[3]));
-            }
-            float rest = 0.f;
+            float2 rest = make_float2(0.f, 0.f);
 #pragma unroll 1
-            for (; y < n_in; ++y) rest += l2_pw_term(rec_in[y], B, a, b, kap);
-            kahan_add(sm, cm, rest);
+            for (; q < np; ++q) rest = f2_add(rest, l2_pw_term2(rhi[q], rco[q], B2, a2, b2, k2));
+            kahan_add(sm, cm, rest.x + rest.y);
             sum = sm - cm;
         }
-        const float4 rx = rec_out[e];
-        const float xi = rx.z, xj = rx.w;
+        const float2 xy = l2_rec_xy(out.rec, m, e);
+        const float xi = xy.x, xj = xy.y;
         const float2 po = out_pot[e];
         const float Ms = -po.x;
         const float2 cD = cdt[abs((int)xj - (int)xi)];
@@ -784,7 +826,7 @@ static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bo
             float mx = -INFINITY;
 #pragma unroll 1
             for (int y = 0; y < n_in; ++y) {
-                const float4 r = rec_in[y];
+                const float4 r = l2_rec_get(in.rec, n_in, y);
                 mx = fmaxf(mx, kap * fmaf(a, r.z, fmaf(b, r.w, r.x + B0)));
             }
             if (hD.x > -INFINITY) mx = fmaxf(mx, hD.x - cD.x);
@@ -793,7 +835,7 @@ static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bo
             const float B = fmaf(-sp, fmaf(xi, xi, xj * xj), -Mf);
             float sm = 0.f, cm = 0.f;
 #pragma unroll 1
-            for (int y = 0; y < n_in; ++y) kahan_add(sm, cm, l2_pw_term(rec_in[y], B, a, b, kap));
+            for (int y = 0; y < n_in; ++y) kahan_add(sm, cm, l2_pw_term(l2_rec_get(in.rec, n_in, y), B, a, b, kap));
             tot = fmaf(sm - cm, exp2f(fmaf(kap, Mf, -shift)),
                        hD.x > -INFINITY ? l2_ex2(((hD.x - cD.x) - shift) + (hD.y - cD.y)) : 0.f);
         }
@@ -803,7 +845,7 @@ static __device__ void l2_half_pw(L2Side& in, L2Side& out, const L2Consts& K, bo
             const float2 lw = smp<float2>(out.lw)[e];
             const float2 hn = make_float2(lw.x + pn.x, lw.y + pn.y);
             smp<float2>(out.hin)[e] = hn;
-            rec_out[e] = l2_pw_record(hn, xi, xj, K);
+            l2_rec_put(out.rec, e, l2_pw_record(hn, xi, xj, K));
         } else {
             atomicOr(range_flag, 1);
         }
@@ -836,7 +878,7 @@ static __device__ void l2_next_stage(L2Side* S, const L2Consts& K, double gamma_
             const float2 hn = make_float2(xlw[e].x + pn.x, xlw[e].y + pn.y);
             xhin[e] = hn;
             if (!GM && K.pw_ok)   // (records may not exist yet: the coordinates come from the cell lists)
-                smp<float4>(X.rec)[e] = l2_pw_record(hn, (float)smp<short>(X.row)[e], (float)smp<short>(X.col)[e], K);
+                l2_rec_put(X.rec, e, l2_pw_record(hn, (float)smp<short>(X.row)[e], (float)smp<short>(X.col)[e], K));
         }
     }
     __syncthreads();   // every thread has read the sides' Delta state (hinD in the half-steps) before t == 0 writes it
@@ -959,7 +1001,7 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
     const int ns[2] = {nA, nB};
     for (int s = 0; s < 2; ++s) {
         const int n = ns[s];
-        const uint32_t o_lw = take(24 * (size_t)n), o_rec = take(fm.rec ? 16 * (size_t)n : 0),
+        const uint32_t o_lw = take(24 * (size_t)n), o_rec = take(fm.rec ? 32 * (size_t)((n + 1) / 2) : 0),
                        o_w = take(4 * (size_t)n), o_rp = take(4 * (size_t)(d + 1));
         const uint32_t o_row = take(6 * (size_t)n), o_rows = take(6 * (size_t)d);
         if (t == 0) {
@@ -1014,9 +1056,14 @@ sk_lse2_kernel(SkWS w, SkRun r, int n_inner, int* counter, int smem_cap, size_t 
                 const float2 p2 = l2_split(pot[s][c] * LOG2E, gsc);
                 xlw[e] = l2; xpot[e] = p2;
                 xhin[e] = make_float2(l2.x + p2.x, l2.y + p2.y);
+                if (!GM && fm.rec) l2_rec_coord(X.rec, n, e, (float)i, (float)j);
                 if (!GM && K.pw_ok)
-                    smp<float4>(X.rec)[e] = l2_pw_record(make_float2(l2.x + p2.x, l2.y + p2.y), (float)i, (float)j, K);
+                    l2_rec_put(X.rec, e, l2_pw_record(make_float2(l2.x + p2.x, l2.y + p2.y), (float)i, (float)j, K));
                 xw[e] = wt[s][c];
+            }
+            if (!GM && fm.rec && (n & 1) && t == 0) {   // an odd side's last slot: a zero term
+                l2_rec_put(X.rec, n, make_float2(-INFINITY, 0.f));
+                l2_rec_coord(X.rec, n, n, 0.f, 0.f);
             }
             for (int i = t; i <= d; i += NT) xrp[i] = rps[s][i];
             l2_compact(rps[s], d, sdp<short, GM>(gb, X.rows), &cnt[2], nullptr, wcnt);
