@@ -135,8 +135,12 @@ typedef struct {
                           output's columns, stage 2 over the input's rows and the output's cells); 2 = pairwise
                           over the two supports, c_xy = |x - y|^2 / d^2 computed exactly per term, wherever
                           p = 2; 0 (default) = per half-step, pairwise while it has at most twice the separable
-                          form's terms (p = 2), else separable.  Both forms are exact sums of the same terms in
-                          FP32; results agree within rounding */
+                          form's terms (p = 2), else separable.  The pairwise form also needs its records
+                          (16 bytes per cell) to fit in shared memory beside the pair's other arrays (else
+                          the separable form runs on chip) and exact scaled units at the gamma of the stage
+                          (n1 = rint(log2(e) / (gamma d^2) 2^G) >= 1; a continuation stage without them runs
+                          separable, and the pair switches at the first stage that has them).  Both forms are
+                          exact sums of the same terms in FP32; results agree within rounding */
 } pd_sinkhorn_params;
 
 /* Fill *p with defaults for (gamma, d): max_iter 20000, tol 1e-6, PD_FP32,
