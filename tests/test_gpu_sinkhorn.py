@@ -388,21 +388,93 @@ def test_ground_cost_p_rejected_where_unsupported(ctx):
         api.pd_sinkhorn_bounds(ctx, hh, mm, hh, mm, prm)
 
 
-def test_pairs_index_and_edge_cases(ctx):
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_pairs_index_and_edge_cases(ctx, form):
+    """Pair indexing, empty diagrams, a one-cell diagram and a diagram on the
+    zero-cost diagonal cells (i = j), in every log-sum-exp form: the oracle's
+    converged cost; both empty gives 0, and against an empty diagram every
+    point goes to the diagonal bin."""
     d, gamma = 32, 1e-2
     b, t, o = inputs.random_diagrams(3, nmin=5, nmax=30, seed=3)
     h, _ = oracle.rasterize(b, t, o, d)
     empty = np.zeros((1, d, d), np.uint32)
     one = np.zeros((1, d, d), np.uint32); one[0, 3, 20] = 2
-    H = np.concatenate([h, empty, one])                 # 0..2 random, 3 empty, 4 one cell
-    pairs = np.array([[0, 1], [1, 0], [2, 2], [0, 3], [3, 0], [3, 3], [4, 1], [4, 4]], dtype=np.int32)
-    g = _solve(ctx, H, H, d, gamma, 5000, 1e-9, pairs=dev(pairs))
+    diag = np.zeros((1, d, d), np.uint32); diag[0, 5, 5] = 3; diag[0, 30, 30] = 1
+    H = np.concatenate([h, empty, one, diag])           # 0..2 random, 3 empty, 4 one cell, 5 diagonal cells
+    pairs = np.array([[0, 1], [1, 0], [2, 2], [0, 3], [3, 0], [3, 3], [4, 1], [4, 4], [5, 0], [5, 3], [4, 5]],
+                     dtype=np.int32)
+    g = _solve(ctx, H, H, d, gamma, 5000, 1e-9, pairs=dev(pairs), prm={"lse_form": form})
     for k, (i, j) in enumerate(pairs):
         r = oracle.sinkhorn_pd(d, gamma, H[i], H[j], 5000, 1e-9)
         assert abs(g["cost"][k] - r["cost"]) <= 2e-6 * max(r["cost"], 1e-12) + 1e-9, (k, g["cost"][k], r["cost"])
     assert g["cost"][5] == 0.0 and g["status"][5] == api.PD_OK      # both empty
     ii, jj = np.meshgrid(np.arange(d), np.arange(d), indexing="ij")
     assert g["cost"][3] == pytest.approx(float((h[0] * ((jj - ii) / d) ** 2 / 2).sum()), rel=1e-6)
+    assert g["cost"][9] <= 1e-12                                    # diagonal cells to the diagonal bin
+
+
+def _scaled_units(gamma, d):
+    """The pairwise form's scaled units, restated: grid bits G of the base-2
+    number format at gamma, n1 = rint(log2(e) / (gamma d^2) 2^G) and
+    kappa = log2(e) / (gamma d^2) / (n1 2^-G) (None where n1 < 1)."""
+    cmax = 2.0 / gamma * math.log2(math.e) + 64.0
+    e = 0
+    while 2.0 ** e < 8.0 * cmax:
+        e += 1
+    G = min(23 - e, 12)
+    s = math.log2(math.e) / (gamma * d * d)
+    n1 = round(s * 2.0 ** G)
+    return None if n1 < 1 else s / (n1 * 2.0 ** -G)
+
+
+@pytest.mark.parametrize("gamma", [0.242, 0.7, 1.0])
+def test_pairwise_form_at_the_ends_of_its_scaled_units(ctx, gamma):
+    """d = 128 at large gamma, where the scaled unit is one grid step (n1 = 1):
+    kappa = 1.49 (gamma 0.242) and 0.515 (gamma 0.7) sit at the two ends of
+    [1/2, 3/2], where the records' hi words carry the most rescaling; at
+    gamma = 1 n1 rounds to 0, so the pairwise form is not available and form 2
+    runs the separable form (bit for bit form 1).  Each matches the FP64
+    oracle after 100 fixed iterations: cost, marginals and potentials."""
+    d, T = 128, 100
+    kap = _scaled_units(gamma, d)
+    assert (kap is None) if gamma == 1.0 else (0.5 <= kap <= 1.5 and abs(kap - 1.0) > 0.45)
+    b, t, o = inputs.random_diagrams(6, nmin=50, nmax=500, seed=41)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    g = _solve(ctx, hA, hB, d, gamma, T, 0.0, prm={"lse_form": 2}, want_marginals=True, want_potentials=True)
+    assert np.all(g["iters"] == T)
+    for p in range(3):
+        r = oracle.sinkhorn_pd(d, gamma, hA[p], hB[p], T, 0.0)
+        a, bb = oracle.augment(hA[p], hB[p])
+        ma, mb = a > 0, bb > 0
+        assert abs(g["cost"][p] - r["cost"]) <= 1e-6 * r["cost"], (p, g["cost"][p], r["cost"])
+        assert np.allclose(g["row_marg"][p], r["rmarg"], rtol=5e-6, atol=1e-6)
+        assert np.allclose(g["col_marg"][p], r["cmarg"], rtol=5e-6, atol=1e-6)
+        assert np.allclose(g["f"][p][ma], r["f"][ma], rtol=0, atol=gamma * 2e-5)
+        assert np.allclose(g["g"][p][mb], r["g"][mb], rtol=0, atol=gamma * 2e-5)
+    if kap is None:
+        g1 = _solve(ctx, hA, hB, d, gamma, T, 0.0, prm={"lse_form": 1}, want_potentials=True)
+        for k in ("cost", "f", "g", "err"):
+            assert np.array_equal(g[k], g1[k]), k
+
+
+@pytest.mark.parametrize("d", [2, 7])
+@pytest.mark.parametrize("form", [1, 2])
+def test_smallest_and_odd_grids_every_form(ctx, d, form):
+    """The smallest grid (d = 2: three cells with j >= i) and an odd one,
+    iterated toward 1e-9 (at most 5000 iterations) on both sides in each form:
+    the oracle's costs."""
+    gamma = 1e-2
+    b, t, o = inputs.random_diagrams(8, nmin=5, nmax=60, seed=50 + d)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hA, hB = h[0::2], h[1::2]
+    ref = oracle.sinkhorn_pd_batch(d, gamma, hA, hB, 5000, 1e-9)
+    g = _solve(ctx, hA, hB, d, gamma, 5000, 1e-9, prm={"lse_form": form})
+    # a pair whose points all sit on the zero-cost cells (i = j) has a cost of
+    # ~1e-5 from the entropic spread alone: it is held to FP32 potentials'
+    # accuracy on the scale of its mass times one grid step's cost
+    floor = 1e-7 * (hA.reshape(len(hA), -1).sum(1) + hB.reshape(len(hB), -1).sum(1)) / d ** 2
+    assert np.all(np.abs(g["cost"] - ref["cost"]) <= 2e-6 * ref["cost"] + floor), (g["cost"], ref["cost"])
 
 
 def test_invalid_params(ctx):
