@@ -139,8 +139,12 @@ typedef struct {
                           (16 bytes per cell) to fit in shared memory beside the pair's other arrays (else
                           the separable form runs on chip) and exact scaled units at the gamma of the stage
                           (n1 = rint(log2(e) / (gamma d^2) 2^G) >= 1; a continuation stage without them runs
-                          separable, and the pair switches at the first stage that has them).  Both forms are
-                          exact sums of the same terms in FP32; results agree within rounding */
+                          separable, and the pair switches at the first stage that has them).  In
+                          pd_barycenter, pd_barycenter_grad, pd_kmeans and pd_kmeans_assign, whose results
+                          depend on the whole batch, form 0 runs a call in the separable form where the
+                          pairwise records would lower the on-chip CTAs per SM (a dense barycenter side at
+                          d = 64).  Both forms are exact sums of the same terms in FP32; results agree
+                          within rounding */
 } pd_sinkhorn_params;
 
 /* Fill *p with defaults for (gamma, d): max_iter 20000, tol 1e-6, PD_FP32,

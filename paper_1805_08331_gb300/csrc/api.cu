@@ -424,6 +424,29 @@ static cudaError_t lse_rounds_groups(pd_ctx* c, std::vector<SkWS>& gs, SkWS* dev
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
         smem = (size_t)hbuf[2];
         pw_all = hbuf[3] == 0;
+        if (r.batch_form && r.form == 0 && smem > 0) {
+            // the launch's shared memory is the largest pair's: where records
+            // push it past a CTA-per-SM step (at most 3 count), the pairwise
+            // half-steps run latency-bound in few warps; the whole call then
+            // takes the separable form (dense barycenter sides at d = 64)
+            if ((e = cudaMemsetAsync(counter + 2, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
+            for (int gi = 0; gi < G; ++gi)
+                if ((e = sk_launch_lse2_need(gs[gi], counter + 2, 1, s)) != cudaSuccess) return e;
+            if ((e = cudaMemcpyAsync(hbuf + 2, counter + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess)
+                return e;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            const size_t smem1 = (size_t)hbuf[2];
+            int dv = 0, per_sm = 0;
+            cudaGetDevice(&dv);
+            cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dv);
+            auto ctas = [&](size_t b) { return std::min(3, (int)((size_t)per_sm / (b + 2048))); };
+            if (ctas(smem1) > ctas(smem)) {
+                r.form = 1;
+                smem = smem1;
+                pw_all = false;
+            }
+        }
     }
     // CTA width of the base-2 kernel: 256 threads while there are several pairs
     // per SM, wider CTAs (more warps on one pair) once fewer pairs than SMs
@@ -954,6 +977,7 @@ extern "C" pd_status pd_barycenter(pd_ctx* c, const uint32_t* hist, const uint32
     CUDA_TRY(c, outer_owner_pairs(nullptr, N, B.pairs, s));
     SkRun r = make_run(prm);
     r.pot_support_only = 1;
+    r.batch_form = 1;
     const bool stop_rule = rel_energy_tol > 0;
     double e_prev = 0.0;
     int steps = 0;
@@ -1060,6 +1084,7 @@ extern "C" pd_status pd_barycenter_grad(pd_ctx* c, const uint32_t* hist, const u
     w.pairs = pairs;
     SkRun r = make_run(prm);
     r.pot_support_only = 1;
+    r.batch_form = 1;
     st = lse_solve(c, w, r, warm ? g : nullptr, cost, nullptr, nullptr, f, g, iters, err, status, counter, s);
     if (st != PD_OK) return st;
     CUDA_TRY(c, outer_bary_grad(z, f, g, owner, N, k, d, gsum, count, s));
@@ -1099,6 +1124,7 @@ extern "C" pd_status pd_kmeans_assign(pd_ctx* c, const uint32_t* hist, const uin
     w.histB = nullptr; w.massB = nullptr; w.wB = centroids;
     w.pairs = pairs;
     SkRun r = make_run(prm);
+    r.batch_form = 1;
     r.pot_support_only = 0;
     st = lse_solve(c, w, r, nullptr, cst, nullptr, nullptr, nullptr, nullptr, iters, err, status, counter, s);
     if (st != PD_OK) return st;
@@ -1167,6 +1193,7 @@ extern "C" pd_status pd_kmeans(pd_ctx* c, const uint32_t* hist, const uint32_t* 
     st = sinkhorn_ws(c, (int)std::max(NK, (size_t)N), prm, &w, &counter, s);
     if (st != PD_OK) return st;
     SkRun r = make_run(prm);
+    r.batch_form = 1;
     for (int rd = 0; rd < rounds; ++rd) {
         // assignment: pairs (a_n + R z_c, z_c + R a_n) for every n, c
         CUDA_TRY(c, outer_km_pairs(N, k, pairs, s));

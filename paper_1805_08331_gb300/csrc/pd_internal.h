@@ -106,6 +106,10 @@ struct SkRun {
     int kstages;
     double stage_tol;
     int form;             // base-2 kernel: 0 automatic, 1 separable only, 2 pairwise wherever p = 2
+    // form 0 in an outer loop (Alg. 2, k-means: results that depend on the
+    // whole batch): the separable form for the whole call where the pairwise
+    // records of the automatic forms would lower the on-chip CTAs per SM
+    int batch_form;
 };
 
 cudaError_t sk_launch_setup(const SkWS& w, const double* g_init, cudaStream_t s);

@@ -54,6 +54,38 @@ def test_sharpened_barycenter_matches_oracle(ctx, d, gamma, lam, steps, T):
     assert H <= H0 + 1e-9
 
 
+def test_outer_loop_takes_the_separable_form_where_records_cost_occupancy(ctx):
+    """Alg. 2 at d = 64: the barycenter side is dense (2080 cells), and with
+    the pairwise records the largest pair's shared memory leaves one CTA per
+    SM instead of two, so the automatic form runs the whole call separable:
+    bit for bit lse_form = 1, and the oracle's barycenter (same fixed inner
+    iterations).  At d = 32 the records cost no CTA per SM and the automatic
+    forms stay (the result differs from form 1 in its rounding)."""
+    d, gamma, lam, steps, T = 64, 5e-3, 5.0, 2, 150
+    b, t, o = inputs.random_diagrams(4, nmin=200, nmax=300, exp_mean=0.2, seed=64, log_uniform=False)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hist, mass = hists_to_gpu(h), dev(masses(h).view(np.int32))
+    z0, e0 = api.pd_barycenter(ctx, hist, mass, api.pd_sinkhorn_default_params(gamma, d, max_iter=T, tol=0.0), lam,
+                               steps)
+    z1, e1 = api.pd_barycenter(ctx, hist, mass, api.pd_sinkhorn_default_params(gamma, d, max_iter=T, tol=0.0,
+                                                                               lse_form=1), lam, steps)
+    torch.cuda.synchronize()
+    assert torch.equal(z0, z1) and torch.equal(e0, e1)
+    z_ref, e_ref = oracle.barycenter(d, gamma, h, lam, steps, T, 0.0)
+    z, e = z0.cpu().numpy(), e0.cpu().numpy()
+    assert np.allclose(e, e_ref, rtol=1e-6, atol=0)
+    assert np.allclose(z, z_ref, rtol=1e-5, atol=1e-9 * z_ref.max())
+    d = 32
+    b, t, o = inputs.random_diagrams(4, nmin=10, nmax=60, seed=32)
+    h, _ = oracle.rasterize(b, t, o, d)
+    hist, mass = hists_to_gpu(h), dev(masses(h).view(np.int32))
+    z0, _ = api.pd_barycenter(ctx, hist, mass, api.pd_sinkhorn_default_params(gamma, d, max_iter=T, tol=0.0), lam,
+                              steps)
+    z1, _ = api.pd_barycenter(ctx, hist, mass, api.pd_sinkhorn_default_params(gamma, d, max_iter=T, tol=0.0,
+                                                                              lse_form=1), lam, steps)
+    assert not torch.equal(z0, z1)
+
+
 def test_barycenter_energy_stop_matches_oracle(ctx):
     """The barycenter experiment's stop |E_t/E_{t-1} - 1| < tol (Sec. 5):
     the GPU run stops at the same step as the oracle's, with the same energies
@@ -199,8 +231,9 @@ def test_sharded_step_two_shards_match_one_gpu(ctx):
     """The exchange of the sharded step emulated on one GPU: the diagrams in two
     shards, each with its own pd_barycenter_grad and warm potentials, the two
     sums added (the all-reduce), one pd_barycenter_apply.  Each pair's solve is
-    the same in either batch (results do not depend on the batch), so z only
-    differs from pd_barycenter by the rounding of adding two partial sums."""
+    the same in either batch (at d = 32 no call switches to the separable form
+    for occupancy), so z only differs from pd_barycenter by the rounding of
+    adding two partial sums."""
     d, gamma, lam, steps = 32, 5e-3, 5.0, 4
     b, t, o = inputs.random_diagrams(7, nmin=10, nmax=60, seed=12)
     h, _ = oracle.rasterize(b, t, o, d)
