@@ -184,7 +184,7 @@ def mufu_peak_gexp(sm_mhz):
     return num_sms() * MUFU_PER_SM * sm_mhz * 1e6 / 1e9
 
 
-PW_RATIO = 2   # the iteration kernel's form rule (pairwise while <= 2x the separable terms)
+PW_RATIO = 5   # the iteration kernel's form rule (pairwise while <= 5x the separable terms)
 
 
 def lse_terms_per_iteration(hist, pairs, d, form=0, p2=True):

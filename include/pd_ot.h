@@ -134,7 +134,7 @@ typedef struct {
                           restricted to the supports): 1 = separable (stage 1 over the input's cells and the
                           output's columns, stage 2 over the input's rows and the output's cells); 2 = pairwise
                           over the two supports, c_xy = |x - y|^2 / d^2 computed exactly per term, wherever
-                          p = 2; 0 (default) = per half-step, pairwise while it has at most twice the separable
+                          p = 2; 0 (default) = per half-step, pairwise while it has at most 5 times the separable
                           form's terms (p = 2), else separable.  The pairwise form also needs its records
                           (16 bytes per cell) to fit in shared memory beside the pair's other arrays (else
                           the separable form runs on chip) and exact scaled units at the gamma of the stage

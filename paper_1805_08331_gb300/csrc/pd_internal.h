@@ -82,6 +82,9 @@ cudaError_t pd_launch_raster(const double* birth, const double* death, const int
                              int d, int64_t npts, uint32_t* hist, uint32_t* mass, int* bad,
                              cudaStream_t s);
 
+// internal value of SkRun::form (never accepted from pd_sinkhorn_params)
+constexpr int SK_FORM_AUTO2 = 3;
+
 struct SkRun {
     int max_iter;
     double tol;
@@ -105,7 +108,8 @@ struct SkRun {
     // once its error is <= stage_tol
     int kstages;
     double stage_tol;
-    int form;             // base-2 kernel: 0 automatic, 1 separable only, 2 pairwise wherever p = 2
+    int form;             // base-2 kernel: 0 automatic, 1 separable only, 2 pairwise wherever p = 2,
+                          // SK_FORM_AUTO2 automatic with the term ratio 2 (serving)
     // form 0 in an outer loop (Alg. 2, k-means: results that depend on the
     // whole batch): the separable form for the whole call where the pairwise
     // records of the automatic forms would lower the on-chip CTAs per SM

@@ -563,6 +563,7 @@ extern "C" pd_status pd_serve_create(pd_ctx* ctx, const pd_serve_config* cfg, pd
     sv->run.absorb_every = 64;
     sv->run.rel_thresh = -21.0;
     sv->run.pot_support_only = 1;
+    sv->run.form = SK_FORM_AUTO2;   // the pool's launch carries pairs of every size
     // slots per pool: explicit, or an equal share of the memory budget
     size_t budget = cfg->max_hbm_bytes;
     if (budget == 0) {

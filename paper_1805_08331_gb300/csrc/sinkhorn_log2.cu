@@ -96,17 +96,22 @@ __host__ __device__ __forceinline__ size_t l2_table_bytes(int nrmax, int d, bool
 
 // Form of a half-step (in = input side, out = output side).  Separable: stage
 // 1 has n_in x nc_out terms, stage 2 nr_in x n_out.  Pairwise (p = 2 only):
-// n_in x n_out terms, each about 2.5x cheaper (no tables, no stage buffer, two
-// barriers per half-step), so it is taken while it has at most L2_PW_RATIO
-// times the separable form's terms.  form: 0 automatic, 1 separable only, 2
-// pairwise wherever p = 2.
-#define L2_PW_RATIO 2
+// n_in x n_out terms, each cheaper (no tables, no stage buffer, two barriers
+// per half-step, one setup per output cell instead of one per stage-1 output),
+// so it is taken while it has at most L2_PW_RATIO times the separable form's
+// terms: 5, the measured break-even on batches of one support shape (random
+// cells, d = 32 to 128, 40 to 2080 cells a side).  form: 0 automatic, 1
+// separable only, 2 pairwise wherever p = 2, SK_FORM_AUTO2 automatic with the
+// ratio 2 (the serving pools: pairs of every size share a launch there, whose
+// shared memory the largest pair sets, and the pairwise form loses where few
+// CTAs fit on an SM).
+#define L2_PW_RATIO 5
 __host__ __device__ __forceinline__ bool l2_pw_half(int n_in, int nr_in, int n_out, int nc_out, int form, bool p2) {
     if (!p2 || form == 1) return false;
     if (form == 2) return true;
     const long long direct = (long long)n_in * n_out;
     const long long sep = (long long)n_in * nc_out + (long long)nr_in * n_out;
-    return direct <= L2_PW_RATIO * sep;
+    return direct <= (form == SK_FORM_AUTO2 ? 2 : L2_PW_RATIO) * sep;
 }
 // Shared-memory bytes of a pair in the on-chip variant (the host sizes the
 // launch with the maximum over the pairs); pwU / pwV: the forms of its
