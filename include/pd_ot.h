@@ -429,7 +429,11 @@ pd_status pd_kmeans(pd_ctx* ctx, const uint32_t* hist, const uint32_t* mass, int
  * Queries that arrive while others are on the GPU join at the next round.
  * Centroids stay resident in device memory; with warm_start, the solve of a
  * query against centroid c starts from the centroid-side potential g of the
- * last finished solve against c (its support entries and Delta).
+ * last finished solve against c (its support entries and Delta).  Each
+ * half-step takes the pairwise form while it has at most twice the separable
+ * form's terms (the batch calls allow 5 times): a pool's launch carries pairs
+ * of every size, the largest sets its shared memory, and the pairwise form
+ * loses where few CTAs fit on an SM.
  *
  * All entry points are thread-safe.  Points are host arrays, copied at submit.
  */
