@@ -171,12 +171,11 @@ def fp32_peak_tflops(sm_mhz):
 
 
 # DRAM bytes (read + write) of the base-2 iteration kernel per pair and
-# launch, from one ncu capture of the kernel with the pairwise form in scaled
-# units (512 pairs of this workload, one launch: 54.39 MB read + 0.46 MB
-# written).  The kernel keeps every pair's state on chip; these bytes are the
+# launch, from one ncu capture of the current kernel (paired pairwise records;
+# 512 pairs of this workload, one launch: 54.40 MB read + 0.32 MB written).  The kernel keeps every pair's state on chip; these bytes are the
 # launch's load and store of the potentials, weights and support lists,
 # whatever the number of iterations.
-LSE2_DRAM_BYTES_PER_PAIR_LAUNCH = (54.391040e6 + 0.459264e6) / 512
+LSE2_DRAM_BYTES_PER_PAIR_LAUNCH = (54.397696e6 + 0.320768e6) / 512
 
 
 def mufu_peak_gexp(sm_mhz):
